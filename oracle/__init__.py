@@ -1,0 +1,178 @@
+"""FP64 CPU oracle for the D2Q9I lattice-BGK update (PortLBM, Sec. 3.1-3.3).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and bench.py's
+CPU-baseline / reference leg may import this package; the product path
+(``paper_2607_20650_gb300``) never does. The arithmetic lives in
+``lbm_oracle.c`` (plain C, FP64, two-lattice pull, canonical layout
+h[i*N + n]); this module only compiles it and marshals numpy arrays.
+
+Every function here is pinned by ``tests/test_oracle_pins.py`` against closed
+forms, invariants or exact-rational brute force.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liblbm_oracle.so")
+
+# Edge conditions (same numbering as the C source).
+PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG = range(6)
+
+CX = np.array([-1, 0, 1, -1, 0, 1, -1, 0, 1])
+CY = np.array([-1, -1, -1, 0, 0, 0, 1, 1, 1])
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("tau", ctypes.c_double), ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+        ("ux_in", ctypes.c_double), ("uy_in", ctypes.c_double),
+        ("bc_w", ctypes.c_int32), ("bc_e", ctypes.c_int32),
+        ("bc_s", ctypes.c_int32), ("bc_n", ctypes.c_int32),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile lbm_oracle.c with gcc (OpenMP, no FP contraction) if stale."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           "-std=c11", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        d, u8 = P(ctypes.c_double), P(ctypes.c_uint8)
+        lib.oracle_equilibrium.argtypes = [ctypes.c_double] * 3 + [d]
+        lib.oracle_effective_solid.argtypes = [P(_Params), u8, u8]
+        lib.oracle_init.argtypes = [P(_Params), u8, d, d, d, d]
+        lib.oracle_step.argtypes = [P(_Params), u8, d, d, d, d, d]
+        lib.oracle_run.argtypes = [P(_Params), u8, d, ctypes.c_int64, d, d, d]
+        lib.oracle_run.restype = ctypes.c_int
+        lib.oracle_mass.argtypes = [P(_Params), u8, d]
+        lib.oracle_mass.restype = ctypes.c_double
+        lib.oracle_force.argtypes = [P(_Params), u8, u8, d, d]
+        lib.oracle_omp_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _u8(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+@dataclass
+class Case:
+    """One lattice: size, relaxation time, force, inlet velocity, edges."""
+    nx: int
+    ny: int
+    tau: float
+    fx: float = 0.0
+    fy: float = 0.0
+    ux_in: float = 0.0
+    uy_in: float = 0.0
+    bc_w: int = PERIODIC
+    bc_e: int = PERIODIC
+    bc_s: int = PERIODIC
+    bc_n: int = PERIODIC
+
+    def _c(self):
+        return _Params(self.nx, self.ny, self.tau, self.fx, self.fy, self.ux_in,
+                       self.uy_in, self.bc_w, self.bc_e, self.bc_s, self.bc_n)
+
+
+def omp_threads() -> int:
+    return int(_load().oracle_omp_threads())
+
+
+def equilibrium(drho: float, ux: float, uy: float) -> np.ndarray:
+    """h_i^eq = f_i^eq - w_i of Eq. (2) for rho = 1 + drho, velocity (ux, uy)."""
+    out = np.zeros(9)
+    _load().oracle_equilibrium(drho, ux, uy, _dp(out))
+    return out
+
+
+def effective_solid(case: Case, mask: np.ndarray) -> np.ndarray:
+    mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    out = np.zeros_like(mask)
+    _load().oracle_effective_solid(ctypes.byref(case._c()), _u8(mask), _u8(out))
+    return out
+
+
+class Lattice:
+    """Oracle state: canonical h[i, n] (shape 9 x N, FP64) + effective solid mask."""
+
+    def __init__(self, case: Case, mask: np.ndarray | None = None,
+                 rho=None, ux=None, uy=None):
+        self.case = case
+        N = case.nx * case.ny
+        if mask is None:
+            mask = np.zeros(N, np.uint8)
+        self.solid = effective_solid(case, mask)
+        self.h = np.zeros((9, N))
+        arr = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+               for a in (rho, ux, uy)]
+        _load().oracle_init(ctypes.byref(case._c()), _u8(self.solid),
+                            *[_dp(a) for a in arr], _dp(self.h))
+        self.rho = np.where(self.solid > 0, 1.0, 1.0 if arr[0] is None else arr[0])
+        self.ux = np.where(self.solid > 0, 0.0, 0.0 if arr[1] is None else arr[1])
+        self.uy = np.where(self.solid > 0, 0.0, 0.0 if arr[2] is None else arr[2])
+        self.steps = 0
+
+    def set_h(self, h: np.ndarray):
+        self.h = np.ascontiguousarray(h, dtype=np.float64).reshape(9, -1).copy()
+
+    def run(self, nsteps: int):
+        """nsteps updates; rho/ux/uy hold the moments of the last one."""
+        if nsteps <= 0:
+            return self
+        N = self.case.nx * self.case.ny
+        self.rho = np.empty(N)
+        self.ux = np.empty(N)
+        self.uy = np.empty(N)
+        rc = _load().oracle_run(ctypes.byref(self.case._c()), _u8(self.solid), _dp(self.h),
+                                int(nsteps), _dp(self.rho), _dp(self.ux), _dp(self.uy))
+        if rc != 0:
+            raise MemoryError("oracle_run: out of host memory")
+        self.steps += nsteps
+        return self
+
+    def mass(self) -> float:
+        return float(_load().oracle_mass(ctypes.byref(self.case._c()), _u8(self.solid),
+                                         _dp(self.h)))
+
+    def force(self, body: np.ndarray) -> np.ndarray:
+        body = np.ascontiguousarray(body, dtype=np.uint8).reshape(-1)
+        out = np.zeros(2)
+        _load().oracle_force(ctypes.byref(self.case._c()), _u8(self.solid), _u8(body),
+                             _dp(self.h), _dp(out))
+        return out
+
+    def field(self, a: np.ndarray) -> np.ndarray:
+        return a.reshape(self.case.ny, self.case.nx)
