@@ -1,0 +1,240 @@
+/*
+ * lbm.h -- C ABI of liblbm.so: the D2Q9I lattice-BGK stream-and-collide update
+ * on one GB300 (sm_103a), after PortLBM (arXiv 2607.20650).
+ *
+ * The method (Sec. 3.1): Eq. (1), the BGK lattice Boltzmann equation
+ *   f_i(r + c_i, t + 1) = f_i(r, t) - (1/tau) [f_i(r, t) - f_i^eq(r, t)],
+ * with the incompressible D2Q9I equilibrium of Eq. (2)
+ *   f_i^eq = w_i [rho + 3 v.c_i + 9/2 (v.c_i)^2 - 3/2 v^2],  v = sum_i f_i c_i,
+ * directions i = 0..8 = SW, S, SE, W, rest, E, NW, N, NE (Fig. 1), i.e.
+ * c_i = (i%3 - 1, i/3 - 1), opposite(i) = 8 - i. Half-way bounce-back at
+ * fluid-solid links; Sec. 3.1 boundary kinds plus the edge conditions below.
+ *
+ * Conventions shared by every call:
+ *  - Node index n = y*nx + x (x fastest), 0 <= x < nx, 0 <= y < ny.
+ *  - Populations are stored as deviations h_i = f_i - w_i from the rest
+ *    weights ("shifted" storage) in every precision.
+ *  - The stored state after k updates holds post-collision populations.
+ *    "Moments of update k" are rho and v computed inside update k from the
+ *    pulled pre-collision values, with v = sum_i f_i c_i + F/2 (Guo force).
+ *  - Ownership: the library never allocates device memory. The caller
+ *    passes one device workspace (size from lbm_workspace_bytes) and a CUDA
+ *    stream (cudaStream_t as void*, NULL = legacy default stream); all
+ *    device work is enqueued on that stream. Host arrays stay caller-owned;
+ *    the mask is copied during lbm_create. Host-side handles are malloc'ed
+ *    and freed by lbm_destroy / lbm_batch_destroy.
+ *  - Errors: every call returns an lbm_status; nothing throws or exits.
+ *    lbm_last_error() returns a thread-local message for the last failure.
+ *  - Nothing in this library spins on the device; the only waits are host
+ *    waits, and lbm_wait bounds them.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,        /* bad argument (message in lbm_last_error) */
+    LBM_ENOMEM = 2,        /* workspace too small, or host allocation failed */
+    LBM_ECUDA = 3,         /* a CUDA runtime call failed */
+    LBM_EDIVERGED = 4,     /* a non-finite density was seen since the last check */
+    LBM_ETIMEOUT = 5,      /* lbm_wait ran out of time; work is still in flight */
+    LBM_EUNSUPPORTED = 6   /* valid but not implemented combination */
+} lbm_status;
+
+/* Population layouts of Sec. 3.2 / Fig. 1 (addresses in elements, N = nx*ny):
+ *   STREAM    (SoA)   addr(n, i) = i*N + n
+ *   BUNDLE    (SoAoS) addr(n, i) = (i/3)*3N + 3n + i%3
+ *               bundles {SW,S,SE}, {W,rest,E}, {NW,N,NE}
+ *   COLLISION (AoS)   addr(n, i) = 9n + i                                    */
+typedef enum { LBM_LAYOUT_STREAM = 0, LBM_LAYOUT_BUNDLE = 1, LBM_LAYOUT_COLLISION = 2 } lbm_layout;
+
+/* Algorithms of Sec. 3.3:
+ *   LPTL linear pull, two lattices (1-D launch, block size from the runtime)
+ *   NPTL 2-D tiles (tile_x * tile_y nodes, padded grid), pull, two lattices
+ *   NPOL 2-D tiles, pull, one lattice: a node's pulled values are held in
+ *        registers, a block barrier precedes the in-place writes, and values
+ *        crossing tile edges travel through a buffer grid double-buffered by
+ *        step parity
+ *   NSOL 2-D tiles, swap streaming (one lattice, populations stored in
+ *        opposite slots), in-tile exchanges in shared memory, the same buffer
+ *        grid across tiles.
+ * All four produce bit-identical states at equal storage precision.          */
+typedef enum { LBM_LPTL = 0, LBM_NPTL = 1, LBM_NPOL = 2, LBM_NSOL = 3 } lbm_algo;
+
+/* Storage precision of h; arithmetic is FP64 for F64 and FP32 otherwise. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_storage;
+
+/* Rounding of the FP32 -> F16S/BF16S store: round-to-nearest-even, or
+ * stochastic rounding keyed on (seed, update index, n, i), so results do not
+ * depend on layout or algorithm. Ignored for F64 / F32.                      */
+typedef enum { LBM_ROUND_RNE = 0, LBM_ROUND_SR = 1 } lbm_rounding;
+
+/* Edge conditions. SOUTH/NORTH: PERIODIC (both), WALL, FREESLIP.
+ * WEST: PERIODIC (with EAST), WALL, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG.
+ * EAST: PERIODIC (with WEST), WALL, OUTFLOW_ZG.
+ *   WALL        half-way bounce-back one half cell outside the edge
+ *   FREESLIP    specular reflection: the value pulled across the edge is the
+ *               neighbour row's mirror population of the node's own row
+ *   INLET_ZOUHE incompressible Zou-He velocity inlet (u_in) in column 0
+ *   INLET_EQ    column 0 set to f^eq(rho = 1, u_in) (Sec. 3.1 Dirichlet)
+ *   OUTFLOW_ZG  zero gradient: the pulled source column is clamped         */
+typedef enum {
+    LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_FREESLIP = 2,
+    LBM_BC_INLET_ZOUHE = 3, LBM_BC_INLET_EQ = 4, LBM_BC_OUTFLOW_ZG = 5
+} lbm_bc;
+
+#define LBM_FLAG_NO_GRAPH 0x1u   /* lbm_step launches kernels one by one */
+
+typedef struct lbm_params {
+    int32_t nx, ny;          /* lattice size; nx*ny < 2^32 */
+    double tau;              /* relaxation time, > 1/2 (omega = 1/tau in FP64) */
+    double force[2];         /* Guo body force (lattice units) */
+    double u_in[2];          /* inlet velocity for INLET_* edges */
+    int32_t bc_west, bc_east, bc_south, bc_north;   /* lbm_bc */
+    int32_t layout;          /* lbm_layout */
+    int32_t algo;            /* lbm_algo */
+    int32_t storage;         /* lbm_storage */
+    int32_t rounding;        /* lbm_rounding */
+    uint64_t seed;           /* stochastic-rounding seed */
+    int32_t tile_x, tile_y;  /* NPTL/NPOL/NSOL tile; 0 = default; tile_x*tile_y <= 1024,
+                                tile_x a multiple of 32 */
+    uint32_t flags;          /* LBM_FLAG_* */
+} lbm_params;
+
+typedef struct lbm_lattice lbm_lattice;
+
+/* Bytes of device workspace lbm_create needs for these parameters. */
+lbm_status lbm_workspace_bytes(const lbm_params *p, size_t *bytes);
+
+/* Lay a lattice out in d_workspace (>= lbm_workspace_bytes, 256-byte aligned,
+ * caller-owned, must outlive the lattice). mask_host: N bytes, nonzero =
+ * solid node (copied). A fluid node whose eight neighbours are all solid
+ * or wall is treated as solid. State after create: rho = 1, v = 0. */
+lbm_status lbm_create(const lbm_params *p, const uint8_t *mask_host, void *d_workspace,
+                      size_t bytes, void *cuda_stream, lbm_lattice **out);
+
+/* Initial state f = f^eq(rho, v) on fluid nodes (Eq. (2)), evaluated in FP64
+ * and rounded once to the storage type. Host arrays of N doubles; NULL rho
+ * means 1, NULL ux/uy mean 0. Resets the update counter. Synchronous. */
+lbm_status lbm_init(lbm_lattice *L, const double *rho, const double *ux, const double *uy);
+
+/* Enqueue nsteps updates (Eq. (1)) on the stream; asynchronous. With
+ * want_moments != 0 the last update also stores its moments (rho, ux, uy) in
+ * the workspace for lbm_read_moments / lbm_moments_device. Uses cached CUDA
+ * graphs of whole step blocks unless LBM_FLAG_NO_GRAPH is set. */
+lbm_status lbm_step(lbm_lattice *L, int64_t nsteps, uint32_t want_moments);
+
+/* Synchronise the stream; LBM_EDIVERGED if a non-finite density was seen
+ * (the flag is then cleared). */
+lbm_status lbm_sync(lbm_lattice *L);
+
+/* Wait at most timeout_s seconds for all enqueued work; LBM_ETIMEOUT if it is
+ * still running (nothing is cancelled), otherwise as lbm_sync. */
+lbm_status lbm_wait(lbm_lattice *L, double timeout_s);
+
+/* Moments of the last update that stored them (or of lbm_init), as host
+ * doubles, N each (solid nodes: rho = 1, v = 0). Synchronous. */
+lbm_status lbm_read_moments(lbm_lattice *L, double *rho, double *ux, double *uy);
+
+/* Same moments as FP32 device arrays (N each), enqueued on the stream. */
+lbm_status lbm_moments_device(lbm_lattice *L, float *d_rho, float *d_ux, float *d_uy);
+
+/* Total mass sum over fluid nodes of rho = 1 + sum_i h_i of the stored state,
+ * reduced in FP64 on the GPU in a fixed order. Synchronous. */
+lbm_status lbm_mass(lbm_lattice *L, double *out);
+
+/* Momentum-exchange force on the body: sum over links from a fluid node x to
+ * a node x + c_i with d_body[x + c_i] != 0 of 2 c_i f*_i(x), f* = w + h the
+ * stored post-collision populations; FP64 on the GPU, fixed order.
+ * d_body: device array of N bytes (NULL = every solid node). Synchronous. */
+lbm_status lbm_force(lbm_lattice *L, const uint8_t *d_body, double out[2]);
+
+/* Copy the state to / from host memory in canonical order h[i*N + n],
+ * as = LBM_F64 (double) or LBM_F32 (float). Writes round to the storage
+ * type (via FP32 for F16S/BF16S, nearest-even). Synchronous. */
+lbm_status lbm_read_populations(lbm_lattice *L, void *host, int32_t as);
+lbm_status lbm_write_populations(lbm_lattice *L, const void *host, int32_t as);
+
+typedef struct lbm_info {
+    int64_t cells, fluid_cells;
+    int64_t steps;                 /* updates done since lbm_init */
+    int32_t tile_x, tile_y;        /* tile used (LPTL: block size, 1) */
+    int32_t reserved;
+    double bytes_per_update;       /* algorithmic DRAM bytes of one update */
+    size_t workspace_bytes;
+} lbm_info;
+lbm_status lbm_get_info(lbm_lattice *L, lbm_info *out);
+
+void lbm_destroy(lbm_lattice *L);
+const char *lbm_last_error(void);
+
+/* Element offset of population i of node n in a layout (host-side copy of
+ * the device index map, for checks). Returns -1 on bad arguments. */
+int64_t lbm_layout_index(int32_t layout, int64_t N, int64_t n, int32_t i);
+
+/* Store codec on device arrays, enqueued on stream: d_in[k] (FP32) is
+ * rounded to storage (F16S or BF16S) as population i = k % 9 of node
+ * n = k / 9 at update index t (the keys of LBM_ROUND_SR), written to d_out
+ * (2 bytes each), then decoded back to FP32 in d_back (may be NULL). */
+lbm_status lbm_quantize(int32_t storage, int32_t rounding, uint64_t seed, int64_t t,
+                        const float *d_in, void *d_out, float *d_back, int64_t count,
+                        void *cuda_stream);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent lattices advanced together, one persistent launch per
+ * update over a packed list of tiles of every case, captured into CUDA
+ * graphs. Per case: its own size, tau, force, inlet, edges and mask; layout,
+ * algorithm and tile may be given or left to the autotuner (-1 / 0).
+ * Results per case are bit-identical to a single-lattice run.               */
+typedef struct lbm_batch lbm_batch;
+
+#define LBM_AUTO (-1)
+
+/* Measured cost table for the autotuner, filled by lbm_tune (or zeroed to
+ * use the built-in model). ns_per_cell[storage-independent layout][algo],
+ * ns_per_tile: per-tile overhead. */
+typedef struct lbm_tuning {
+    double ns_per_cell[3][4];
+    double ns_per_tile;
+    int32_t valid;
+    int32_t reserved;
+} lbm_tuning;
+
+/* Time every (layout, algo) on a probe lattice in the caller's workspace
+ * (size from lbm_workspace_bytes of probe with layout = COLLISION, algo =
+ * LPTL is enough for all) and fill *out. Synchronous. */
+lbm_status lbm_tune(const lbm_params *probe, const uint8_t *mask_host, void *d_workspace,
+                    size_t bytes, void *cuda_stream, lbm_tuning *out);
+
+/* Resolve LBM_AUTO layout/algo and 0 tiles of every case with the
+ * autotuner (tuning may be NULL: built-in model); params is updated in
+ * place. All cases must share storage type. */
+lbm_status lbm_batch_plan(int32_t ncases, lbm_params *params, const lbm_tuning *tuning);
+
+lbm_status lbm_batch_workspace_bytes(int32_t ncases, const lbm_params *params, size_t *bytes);
+lbm_status lbm_batch_create(int32_t ncases, const lbm_params *params,
+                            const uint8_t *const *masks_host, void *d_workspace, size_t bytes,
+                            void *cuda_stream, lbm_batch **out);
+/* Initial equilibrium of case c from host arrays (NULL = rho 1 / v 0). */
+lbm_status lbm_batch_init(lbm_batch *B, int32_t c, const double *rho, const double *ux,
+                          const double *uy);
+lbm_status lbm_batch_step(lbm_batch *B, int64_t nsteps, uint32_t want_moments);
+lbm_status lbm_batch_sync(lbm_batch *B);
+lbm_status lbm_batch_read_moments(lbm_batch *B, int32_t c, double *rho, double *ux, double *uy);
+lbm_status lbm_batch_read_populations(lbm_batch *B, int32_t c, void *host, int32_t as);
+/* Number of tiles in the packed work list and the persistent grid size. */
+lbm_status lbm_batch_get_info(lbm_batch *B, int64_t *tiles, int32_t *grid, int64_t *cells);
+void lbm_batch_destroy(lbm_batch *B);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

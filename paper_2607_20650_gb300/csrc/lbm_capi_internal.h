@@ -1,0 +1,32 @@
+// Host helpers shared by the single-lattice and batch parts of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+constexpr int kMaxTileThreadsHost = 512;
+
+// Workspace layout of one lattice (byte offsets, 256-byte aligned).
+struct Plan {
+    int64_t N = 0;
+    int two = 1;                 // two-lattice algorithm
+    int tx = 0, ty = 1, ntx = 0, nty = 0;
+    size_t pop[2] = {0, 0};
+    size_t halo = 0;
+    int64_t halo_parity_elems = 0;
+    size_t links = 0, mom = 0, mom_bytes = 0, partials = 0, misc = 0, total = 0;
+};
+
+lbm_status lbm_fail(lbm_status s, const char *fmt, ...);
+lbm_status lbm_cuda_fail(cudaError_t e, const char *where);
+lbm_status lbm_check_params(const lbm_params *p);
+lbm_status lbm_plan(const lbm_params *p, Plan *pl);
+const lbm::Ops *ops_for_storage(int storage);
+void lbm_fill_args(const lbm_params *p, const Plan &pl, char *ws, const lbm::Ops *ops, lbm::HostArgs *h);
+int64_t layout_addr(int layout, int64_t N, int64_t n, int i);
+lbm_status lbm_pops_to_host(const unsigned char *raw, int storage, int layout, int rev, int64_t N,
+                            void *host, int32_t as);

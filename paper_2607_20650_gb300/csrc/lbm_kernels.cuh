@@ -1,0 +1,627 @@
+// Kernel templates of the D2Q9I BGK update (PortLBM Sec. 3.3), instantiated
+// once per storage type by lbm_ops_*.cu. Every update kernel pulls the nine
+// incoming values of a node (Sec. 3.3, one-step pull), substitutes boundary
+// values, and calls the same collide() so that all layouts and algorithms
+// produce the same bits.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+constexpr int kMaxTileThreads = 512;
+
+template <class S>
+struct Step {
+    using C = typename Codec<S>::C;
+    Geo geo;
+    uint32_t N;
+    Consts<C> k;
+    const uint8_t *links;
+    const S *src;
+    S *dst;
+    const S *halo_rd;
+    S *halo_wr;
+    C *mom;
+    unsigned int *err;
+    const long long *tctr;
+    int toff;
+    int sr;
+    uint64_t seed;
+    int tx, ty, ntx;
+    uint64_t nx_magic;
+};
+
+// Host: FP64 constants rounded once to the compute type.
+template <class S>
+Step<S> make_step(const HostArgs &h, const StepCall &c) {
+    using C = typename Codec<S>::C;
+    Step<S> a;
+    a.geo = Geo{h.nx, h.ny, h.bw, h.be, h.bs, h.bn};
+    a.N = (uint32_t)h.N;
+    Consts<C> &k = a.k;
+    k.omega = (C)h.omega;
+    k.hfx = (C)(0.5 * h.fx);
+    k.hfy = (C)(0.5 * h.fy);
+    k.fx = (C)h.fx;
+    k.fy = (C)h.fy;
+    k.sF = (C)(h.fx + h.fy);
+    k.dF = (C)(h.fx - h.fy);
+    k.w0 = (C)(1.0 / 36.0);
+    k.w1 = (C)(1.0 / 9.0);
+    k.w4 = (C)(4.0 / 9.0);
+    k.kw0 = (C)(h.kf / 36.0);
+    k.kw1 = (C)(h.kf / 9.0);
+    k.kw4 = (C)(4.0 * h.kf / 9.0);
+    k.zh5 = (C)(2.0 / 3.0 * h.ux_in);
+    k.zh8 = (C)(h.ux_in / 6.0 + h.uy_in / 2.0);
+    k.zh2 = (C)(h.ux_in / 6.0 - h.uy_in / 2.0);
+    const double W[9] = {1.0 / 36, 1.0 / 9, 1.0 / 36, 1.0 / 9, 4.0 / 9,
+                         1.0 / 9, 1.0 / 36, 1.0 / 9, 1.0 / 36};
+    for (int i = 0; i < 9; ++i) {
+        double cu = cx(i) * h.ux_in + cy(i) * h.uy_in;
+        double usq = h.ux_in * h.ux_in + h.uy_in * h.uy_in;
+        k.heq_in[i] = (C)(W[i] * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
+    }
+    k.force = (h.fx != 0.0 || h.fy != 0.0) ? 1 : 0;
+    a.links = h.links;
+    a.src = (const S *)h.pop[c.src];
+    a.dst = (S *)(h.pop[1] ? h.pop[c.src ^ 1] : h.pop[0]);
+    S *halo = (S *)h.halo;
+    a.halo_rd = halo ? halo + (int64_t)c.rd_parity * h.halo_parity_elems : nullptr;
+    a.halo_wr = halo ? halo + (int64_t)(c.rd_parity ^ 1) * h.halo_parity_elems : nullptr;
+    a.mom = c.want_moments ? (C *)h.mom : nullptr;
+    a.err = h.err;
+    a.tctr = h.tctr;
+    a.toff = c.toff;
+    a.sr = h.rounding;
+    a.seed = h.seed;
+    a.tx = h.tile_x;
+    a.ty = h.tile_y;
+    a.ntx = h.ntx;
+    a.nx_magic = h.nx_magic;
+    return a;
+}
+
+template <class S, int L>
+__device__ __forceinline__ typename Codec<S>::C ldp(const S *base, uint32_t N, uint32_t n, int i) {
+    return Codec<S>::dec(base[addr<L>(N, n, i)]);
+}
+
+// Inlet substitution, collision, divergence flag, moments, and encoding of
+// the nine post-collision values (canonical direction order) into e.
+template <class S>
+__device__ __forceinline__ void collide_encode(const Step<S> &a, uint32_t x, uint32_t n,
+                                               typename Codec<S>::C *g, S *e) {
+    using C = typename Codec<S>::C;
+    using A = Ar<C>;
+    if (x == 0) {
+        if (a.geo.bw == INLET_ZOUHE) {
+            zou_he(a.k, g);
+        } else if (a.geo.bw == INLET_EQ) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = a.k.heq_in[i];
+        }
+    }
+    C drho, ux, uy;
+    collide(a.k, g, drho, ux, uy);
+    if (!isfinite(drho)) atomicOr(a.err, 1u);
+    if (a.mom) {
+        a.mom[n] = A::add(C(1), drho);
+        a.mom[a.N + n] = ux;
+        a.mom[2 * a.N + n] = uy;
+    }
+    const bool sr = Codec<S>::narrow && a.sr;
+    uint32_t nk = 0;
+    if (sr) nk = node_key(step_key(a.seed, (uint32_t)(*a.tctr + a.toff)), n);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) e[i] = Codec<S>::enc(g[i], sr, sr ? pop_rand(nk, i) : 0u);
+}
+
+// ------------------------------------------------------------ two lattices
+// LPTL (LINEAR: one node per thread over n) and NPTL (2-D tiles).
+template <class S, int L, bool LINEAR>
+__global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice(const Step<S> a) {
+    using C = typename Codec<S>::C;
+    const uint32_t nx = (uint32_t)a.geo.nx, ny = (uint32_t)a.geo.ny;
+    uint32_t x, y, n;
+    if (LINEAR) {
+        n = blockIdx.x * blockDim.x + threadIdx.x;
+        if (n >= a.N) return;
+        y = a.nx_magic ? (uint32_t)__umul64hi((unsigned long long)n, a.nx_magic) : n;
+        x = n - y * nx;
+    } else {
+        x = blockIdx.x * a.tx + threadIdx.x;
+        y = blockIdx.y * a.ty + threadIdx.y;
+        if (x >= nx || y >= ny) return;
+        n = y * nx + x;
+    }
+    const uint32_t lk = a.links[n];
+    if (lk == SOLID_LINKS) return;
+    const bool interior = (x - 1u < nx - 2u) && (y - 1u < ny - 2u);
+    C g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (i == 4) {
+            g[i] = ldp<S, L>(a.src, a.N, n, 4);
+            continue;
+        }
+        if ((lk >> link_bit(i)) & 1u) {
+            g[i] = ldp<S, L>(a.src, a.N, n, opp(i));
+        } else if (interior) {
+            g[i] = ldp<S, L>(a.src, a.N, n - (uint32_t)(cy(i) * (int)nx + cx(i)), i);
+        } else {
+            int xs, ys, j;
+            if (map_pull(a.geo, (int)x, (int)y, i, xs, ys, j) == PULL_NODE)
+                g[i] = ldp<S, L>(a.src, a.N, (uint32_t)ys * nx + (uint32_t)xs, j);
+            else
+                g[i] = C(0);  // inlet unknown, reconstructed in collide_encode
+        }
+    }
+    S e[9];
+    collide_encode(a, x, n, g, e);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) a.dst[addr<L>(a.N, n, i)] = e[i];
+}
+
+// ------------------------------------------------------------ buffer grid
+// Per tile and parity: east edge 3 x ty values (directions 2,5,8), west
+// 3 x ty (0,3,6), north 3 x tx (6,7,8), south 3 x tx (0,1,2).
+enum Edge { EDGE_E = 0, EDGE_W = 1, EDGE_N = 2, EDGE_S = 3 };
+
+__device__ __forceinline__ int64_t halo_slot(int tx, int ty, int ntx, int bx, int by, int edge,
+                                             int k, int pos) {
+    int64_t base = (int64_t)(by * ntx + bx) * (6 * (tx + ty));
+    switch (edge) {
+        case EDGE_E: return base + k * ty + pos;
+        case EDGE_W: return base + 3 * ty + k * ty + pos;
+        case EDGE_N: return base + 6 * ty + k * tx + pos;
+        default: return base + 6 * ty + 3 * tx + k * tx + pos;
+    }
+}
+
+// Value S[(xs, ys)][j] of a node in another tile, as that tile published it.
+template <class S>
+__device__ __forceinline__ typename Codec<S>::C halo_read(const Step<S> &a, int xs, int ys, int j,
+                                                          int bx) {
+    const int bxs = xs / a.tx, bys = ys / a.ty;
+    int64_t s;
+    if (bxs != bx)
+        s = halo_slot(a.tx, a.ty, a.ntx, bxs, bys, cx(j) > 0 ? EDGE_E : EDGE_W, j / 3, ys - bys * a.ty);
+    else
+        s = halo_slot(a.tx, a.ty, a.ntx, bxs, bys, cy(j) > 0 ? EDGE_N : EDGE_S, j % 3, xs - bxs * a.tx);
+    return Codec<S>::dec(a.halo_rd[s]);
+}
+
+// Publish the populations of an edge node that leave its tile.
+template <class S>
+__device__ __forceinline__ void halo_publish(S *hw, int tx, int ty, int ntx, int bx, int by, int x,
+                                             int y, int x0, int y0, int x1, int y1, const S *e) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (x == x1) hw[halo_slot(tx, ty, ntx, bx, by, EDGE_E, k, y - y0)] = e[3 * k + 2];
+        if (x == x0) hw[halo_slot(tx, ty, ntx, bx, by, EDGE_W, k, y - y0)] = e[3 * k];
+        if (y == y1) hw[halo_slot(tx, ty, ntx, bx, by, EDGE_N, k, x - x0)] = e[6 + k];
+        if (y == y0) hw[halo_slot(tx, ty, ntx, bx, by, EDGE_S, k, x - x0)] = e[k];
+    }
+}
+
+// ------------------------------------------------------------ NPOL
+// One lattice, pull: every node reads its nine incoming values (in-tile
+// sources from the lattice, cross-tile sources from the buffer grid of the
+// previous update), the block barrier separates all reads from the in-place
+// writes, and edge nodes publish their outgoing values for the next update.
+template <class S, int L>
+__global__ void __launch_bounds__(kMaxTileThreads) k_npol(const Step<S> a) {
+    using C = typename Codec<S>::C;
+    const int nx = a.geo.nx, ny = a.geo.ny;
+    const int bx = blockIdx.x, by = blockIdx.y;
+    const int x0 = bx * a.tx, y0 = by * a.ty;
+    const int x1 = min(x0 + a.tx, nx) - 1, y1 = min(y0 + a.ty, ny) - 1;
+    const int x = x0 + (int)threadIdx.x, y = y0 + (int)threadIdx.y;
+    const bool valid = x <= x1 && y <= y1;
+    S *lat = a.dst;
+    uint32_t n = 0, lk = SOLID_LINKS;
+    if (valid) {
+        n = (uint32_t)y * (uint32_t)nx + (uint32_t)x;
+        lk = a.links[n];
+    }
+    const bool fluid = lk != SOLID_LINKS;
+    C g[9];
+    if (fluid) {
+        const bool inner = x > x0 && x < x1 && y > y0 && y < y1;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (i == 4) {
+                g[i] = ldp<S, L>(lat, a.N, n, 4);
+            } else if ((lk >> link_bit(i)) & 1u) {
+                g[i] = ldp<S, L>(lat, a.N, n, opp(i));
+            } else if (inner) {
+                g[i] = ldp<S, L>(lat, a.N, n - (uint32_t)(cy(i) * nx + cx(i)), i);
+            } else {
+                int xs, ys, j;
+                if (map_pull(a.geo, x, y, i, xs, ys, j) != PULL_NODE)
+                    g[i] = C(0);
+                else if (xs >= x0 && xs <= x1 && ys >= y0 && ys <= y1)
+                    g[i] = ldp<S, L>(lat, a.N, (uint32_t)ys * (uint32_t)nx + (uint32_t)xs, j);
+                else
+                    g[i] = halo_read(a, xs, ys, j, bx);
+            }
+        }
+    }
+    __syncthreads();
+    if (fluid) {
+        S e[9];
+        collide_encode(a, (uint32_t)x, n, g, e);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) lat[addr<L>(a.N, n, i)] = e[i];
+        if (!(x > x0 && x < x1 && y > y0 && y < y1))
+            halo_publish(a.halo_wr, a.tx, a.ty, a.ntx, bx, by, x, y, x0, y0, x1, y1, e);
+    }
+}
+
+// ------------------------------------------------------------ NSOL
+// One lattice, swap streaming: populations are stored in opposite slots
+// (slot s of node x holds f*_{8-s}(x)). Tiles are staged in shared memory;
+// for each of the four positive directions i, slot 8-i of x is exchanged
+// with slot i of x + c_i when both are fluid (no exchange = bounce-back).
+// Values that enter through domain edges or from other tiles (buffer grid)
+// are substituted afterwards.
+template <class S, int L>
+__global__ void __launch_bounds__(kMaxTileThreads) k_nsol(const Step<S> a) {
+    using C = typename Codec<S>::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int T = a.tx * a.ty;
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    uint8_t *fl = smem_raw + sizeof(C) * 9 * T;
+    const int nx = a.geo.nx, ny = a.geo.ny;
+    const int bx = blockIdx.x, by = blockIdx.y;
+    const int x0 = bx * a.tx, y0 = by * a.ty;
+    const int x1 = min(x0 + a.tx, nx) - 1, y1 = min(y0 + a.ty, ny) - 1;
+    const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * a.tx + lx;
+    const int x = x0 + lx, y = y0 + ly;
+    const bool valid = x <= x1 && y <= y1;
+    S *lat = a.dst;
+    uint32_t n = 0, lk = SOLID_LINKS;
+    if (valid) {
+        n = (uint32_t)y * (uint32_t)nx + (uint32_t)x;
+        lk = a.links[n];
+    }
+    const bool fluid = lk != SOLID_LINKS;
+    fl[tid] = fluid ? 1 : 0;
+    if (fluid) {
+#pragma unroll
+        for (int s = 0; s < 9; ++s) sm[s * T + tid] = ldp<S, L>(lat, a.N, n, s);
+    }
+    __syncthreads();
+    // Substitutions for pulls the in-tile exchange does not cover.
+    C fix[9];
+    unsigned fixmask = 0;
+    if (fluid && !(x > x0 && x < x1 && y > y0 && y < y1)) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            fix[i] = C(0);
+            if (i == 4 || ((lk >> link_bit(i)) & 1u)) continue;
+            int xs, ys, j;
+            const int kind = map_pull(a.geo, x, y, i, xs, ys, j);
+            const bool in_tile = kind == PULL_NODE && xs >= x0 && xs <= x1 && ys >= y0 && ys <= y1;
+            if (in_tile && j == i && xs == x - cx(i) && ys == y - cy(i)) continue;  // exchanged
+            fixmask |= 1u << i;
+            if (kind != PULL_NODE) continue;  // inlet unknown
+            if (in_tile)
+                fix[i] = sm[opp(j) * T + (ys - y0) * a.tx + (xs - x0)];
+            else
+                fix[i] = halo_read(a, xs, ys, j, bx);
+        }
+    }
+    __syncthreads();
+    if (fluid) {
+#pragma unroll
+        for (int i = 5; i < 9; ++i) {
+            const int px = lx + cx(i), py = ly + cy(i);
+            if (px >= 0 && px < a.tx && py < a.ty && x0 + px <= x1 && y0 + py <= y1) {
+                const int pt = py * a.tx + px;
+                if (fl[pt]) {
+                    C t = sm[opp(i) * T + tid];
+                    sm[opp(i) * T + tid] = sm[i * T + pt];
+                    sm[i * T + pt] = t;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (fluid) {
+        C g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = ((fixmask >> i) & 1u) ? fix[i] : sm[i * T + tid];
+        S e[9];
+        collide_encode(a, (uint32_t)x, n, g, e);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) lat[addr<L>(a.N, n, opp(i))] = e[i];
+        if (!(x > x0 && x < x1 && y > y0 && y < y1))
+            halo_publish(a.halo_wr, a.tx, a.ty, a.ntx, bx, by, x, y, x0, y0, x1, y1, e);
+    }
+}
+
+// ------------------------------------------------------------ state kernels
+template <class S, int L>
+__global__ void k_init(const Step<S> a, const double *rho, const double *ux, const double *uy,
+                       uint32_t n0, uint32_t count, int rev) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const uint32_t n = n0 + t;
+    if (a.links[n] == SOLID_LINKS) return;
+    const double dr = rho ? rho[t] - 1.0 : 0.0;
+    const double vx = ux ? ux[t] : 0.0, vy = uy ? uy[t] : 0.0;
+    const double usq = vx * vx + vy * vy;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const double w = i == 4 ? 4.0 / 9.0 : ((i & 1) ? 1.0 / 9.0 : 1.0 / 36.0);
+        const double cu = cx(i) * vx + cy(i) * vy;
+        const double h = w * (dr + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+        typename Codec<S>::C hc = (typename Codec<S>::C)h;
+        a.dst[addr<L>(a.N, n, rev ? opp(i) : i)] = Codec<S>::enc(hc, false, 0u);
+    }
+}
+
+// Copy every tile-edge node's outgoing values into one buffer-grid parity.
+template <class S, int L>
+__global__ void k_publish(const Step<S> a, S *hw, int rev) {
+    const int nx = a.geo.nx, ny = a.geo.ny;
+    const int bx = blockIdx.x, by = blockIdx.y;
+    const int x0 = bx * a.tx, y0 = by * a.ty;
+    const int x1 = min(x0 + a.tx, nx) - 1, y1 = min(y0 + a.ty, ny) - 1;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x > x1 || y > y1) return;
+    if (x > x0 && x < x1 && y > y0 && y < y1) return;
+    const uint32_t n = (uint32_t)y * (uint32_t)nx + (uint32_t)x;
+    if (a.links[n] == SOLID_LINKS) return;
+    S e[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) e[i] = a.src[addr<L>(a.N, n, rev ? opp(i) : i)];
+    halo_publish(hw, a.tx, a.ty, a.ntx, bx, by, x, y, x0, y0, x1, y1, e);
+}
+
+// Moments from a stored state: rho = 1 + sum h, v = sum h c (- F/2 for a
+// post-collision state, since the collision adds F to sum f c).
+template <class S, int L>
+__global__ void k_state_moments(const Step<S> a, int rev, int post) {
+    using C = typename Codec<S>::C;
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= a.N) return;
+    C *m = (C *)a.mom;
+    if (a.links[n] == SOLID_LINKS) {
+        m[n] = C(1);
+        m[a.N + n] = C(0);
+        m[2 * a.N + n] = C(0);
+        return;
+    }
+    double r = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const double h = (double)ldp<S, L>(a.src, a.N, n, rev ? opp(i) : i);
+        r += h;
+        jx += cx(i) * h;
+        jy += cy(i) * h;
+    }
+    if (post) {
+        jx -= 0.5 * (double)a.k.fx;
+        jy -= 0.5 * (double)a.k.fy;
+    }
+    m[n] = (C)(1.0 + r);
+    m[a.N + n] = (C)jx;
+    m[2 * a.N + n] = (C)jy;
+}
+
+// Deterministic FP64 block reduction (fixed grid and tree).
+template <int W>
+__device__ __forceinline__ void block_reduce_store(double (&v)[W], double *partials) {
+    __shared__ double red[W][kReduceThreads];
+    for (int w = 0; w < W; ++w) red[w][threadIdx.x] = v[w];
+    __syncthreads();
+    for (int s = kReduceThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int w = 0; w < W; ++w) red[w][threadIdx.x] += red[w][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int w = 0; w < W; ++w) partials[blockIdx.x * W + w] = red[w][0];
+}
+
+template <class S, int L>
+__global__ void __launch_bounds__(kReduceThreads) k_mass(const Step<S> a, int rev, double *partials) {
+    double acc[1] = {0.0};
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < a.N; n += gridDim.x * blockDim.x) {
+        if (a.links[n] == SOLID_LINKS) continue;
+        double r = 1.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) r += (double)ldp<S, L>(a.src, a.N, n, rev ? opp(i) : i);
+        acc[0] += r;
+    }
+    block_reduce_store<1>(acc, partials);
+}
+
+template <class S, int L>
+__global__ void __launch_bounds__(kReduceThreads) k_force(const Step<S> a, int rev, const uint8_t *body,
+                                                          double *partials) {
+    double acc[2] = {0.0, 0.0};
+    const int nx = a.geo.nx, ny = a.geo.ny;
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < a.N; n += gridDim.x * blockDim.x) {
+        if (a.links[n] == SOLID_LINKS) continue;
+        const int y = a.nx_magic ? (int)__umul64hi((unsigned long long)n, a.nx_magic) : (int)n;
+        const int x = (int)n - y * nx;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (i == 4) continue;
+            int bx = x + cx(i), by = y + cy(i);
+            if (bx < 0 || bx >= nx) {
+                if (a.geo.bw != PERIODIC) continue;
+                bx = bx < 0 ? bx + nx : bx - nx;
+            }
+            if (by < 0 || by >= ny) {
+                if (a.geo.bs != PERIODIC) continue;
+                by = by < 0 ? by + ny : by - ny;
+            }
+            const uint32_t m = (uint32_t)by * (uint32_t)nx + (uint32_t)bx;
+            const bool hit = body ? body[m] != 0 : a.links[m] == SOLID_LINKS;
+            if (!hit) continue;
+            const double w = (i & 1) ? 1.0 / 9.0 : 1.0 / 36.0;
+            const double f = w + (double)ldp<S, L>(a.src, a.N, n, rev ? opp(i) : i);
+            acc[0] += 2.0 * cx(i) * f;
+            acc[1] += 2.0 * cy(i) * f;
+        }
+    }
+    block_reduce_store<2>(acc, partials);
+}
+
+template <class C>
+__global__ void k_moments_f32(const C *mom, uint32_t N, float *r, float *u, float *v) {
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    r[n] = (float)mom[n];
+    u[n] = (float)mom[N + n];
+    v[n] = (float)mom[2 * (size_t)N + n];
+}
+
+// ------------------------------------------------------------ launchers
+template <class S, int L>
+int lptl_block() {
+    static int block = [] {
+        int minGrid = 0, b = 256;
+        if (cudaOccupancyMaxPotentialBlockSize(&minGrid, &b, k_two_lattice<S, L, true>, 0,
+                                               kMaxTileThreads) != cudaSuccess) {
+            cudaGetLastError();
+            b = 256;
+        }
+        return b;
+    }();
+    return block;
+}
+
+template <class S, int L>
+cudaError_t step_layout(const HostArgs &h, const Step<S> &a, cudaStream_t st) {
+    using C = typename Codec<S>::C;
+    const dim3 tile(h.tile_x, h.tile_y), grid(h.ntx, h.nty);
+    switch (h.algo) {
+        case LPTL: {
+            const int b = h.block_1d;
+            const unsigned g = (unsigned)((h.N + b - 1) / b);
+            k_two_lattice<S, L, true><<<g, b, 0, st>>>(a);
+            break;
+        }
+        case NPTL: k_two_lattice<S, L, false><<<grid, tile, 0, st>>>(a); break;
+        case NPOL: k_npol<S, L><<<grid, tile, 0, st>>>(a); break;
+        case NSOL: {
+            const size_t sm = sizeof(C) * 9 * h.tile_x * h.tile_y + h.tile_x * h.tile_y;
+            k_nsol<S, L><<<grid, tile, sm, st>>>(a);
+            break;
+        }
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t op_step(const HostArgs &h, const StepCall &c, cudaStream_t st) {
+    const Step<S> a = make_step<S>(h, c);
+    switch (h.layout) {
+        case STREAM: return step_layout<S, STREAM>(h, a, st);
+        case BUNDLE: return step_layout<S, BUNDLE>(h, a, st);
+        case COLLISION: return step_layout<S, COLLISION>(h, a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+#define LBM_LAYOUT_SWITCH(h, CALL)                          \
+    switch ((h).layout) {                                   \
+        case STREAM: { constexpr int L_ = STREAM; CALL; break; }       \
+        case BUNDLE: { constexpr int L_ = BUNDLE; CALL; break; }       \
+        case COLLISION: { constexpr int L_ = COLLISION; CALL; break; } \
+        default: return cudaErrorInvalidValue;              \
+    }
+
+template <class S>
+cudaError_t op_init(const HostArgs &h, const double *rho, const double *ux, const double *uy,
+                    int64_t n0, int64_t count, cudaStream_t st) {
+    const Step<S> a = make_step<S>(h, StepCall{1, 0, 0, 0});  // dst = pop[0]
+    if (count <= 0) return cudaSuccess;
+    const unsigned g = (unsigned)((count + 255) / 256);
+    const int rev = h.algo == NSOL;
+    LBM_LAYOUT_SWITCH(h, (k_init<S, L_><<<g, 256, 0, st>>>(a, rho, ux, uy, (uint32_t)n0,
+                                                             (uint32_t)count, rev)));
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t op_publish(const HostArgs &h, int src, int parity, cudaStream_t st) {
+    const Step<S> a = make_step<S>(h, StepCall{src, 0, 0, 0});
+    S *hw = (S *)h.halo + (int64_t)parity * h.halo_parity_elems;
+    const int rev = h.algo == NSOL;
+    const dim3 tile(h.tile_x, h.tile_y), grid(h.ntx, h.nty);
+    LBM_LAYOUT_SWITCH(h, (k_publish<S, L_><<<grid, tile, 0, st>>>(a, hw, rev)));
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t op_state_moments(const HostArgs &h, int src, int post, cudaStream_t st) {
+    Step<S> a = make_step<S>(h, StepCall{src, 0, 0, 1});
+    const unsigned g = (unsigned)((h.N + 255) / 256);
+    const int rev = h.algo == NSOL;
+    LBM_LAYOUT_SWITCH(h, (k_state_moments<S, L_><<<g, 256, 0, st>>>(a, rev, post)));
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t op_mass(const HostArgs &h, int src, double *partials, int nblocks, cudaStream_t st) {
+    const Step<S> a = make_step<S>(h, StepCall{src, 0, 0, 0});
+    const int rev = h.algo == NSOL;
+    LBM_LAYOUT_SWITCH(h, (k_mass<S, L_><<<nblocks, kReduceThreads, 0, st>>>(a, rev, partials)));
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t op_force(const HostArgs &h, int src, const uint8_t *body, double *partials, int nblocks,
+                     cudaStream_t st) {
+    const Step<S> a = make_step<S>(h, StepCall{src, 0, 0, 0});
+    const int rev = h.algo == NSOL;
+    LBM_LAYOUT_SWITCH(h, (k_force<S, L_><<<nblocks, kReduceThreads, 0, st>>>(a, rev, body, partials)));
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t op_moments_f32(const HostArgs &h, float *r, float *u, float *v, cudaStream_t st) {
+    using C = typename Codec<S>::C;
+    const unsigned g = (unsigned)((h.N + 255) / 256);
+    k_moments_f32<C><<<g, 256, 0, st>>>((const C *)h.mom, (uint32_t)h.N, r, u, v);
+    return cudaGetLastError();
+}
+
+template <class S>
+int op_lptl_block(int layout) {
+    switch (layout) {
+        case STREAM: return lptl_block<S, STREAM>();
+        case BUNDLE: return lptl_block<S, BUNDLE>();
+        default: return lptl_block<S, COLLISION>();
+    }
+}
+
+template <class S>
+Ops make_ops() {
+    Ops o;
+    o.step = op_step<S>;
+    o.init = op_init<S>;
+    o.publish = op_publish<S>;
+    o.state_moments = op_state_moments<S>;
+    o.mass = op_mass<S>;
+    o.force = op_force<S>;
+    o.moments_f32 = op_moments_f32<S>;
+    o.lptl_block = op_lptl_block<S>;
+    o.elem = sizeof(S);
+    o.compute = sizeof(typename Codec<S>::C);
+    return o;
+}
+
+}  // namespace lbm

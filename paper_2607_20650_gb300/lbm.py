@@ -1,0 +1,323 @@
+"""ctypes binding of liblbm.so (C ABI in include/lbm.h).
+
+Functions carry the C names and only marshal arguments: every step of the
+update runs in the library's CUDA kernels. PyTorch supplies device memory
+(the workspace) and streams. There is no CPU fallback: if the library is not
+built, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ETIMEOUT, LBM_EUNSUPPORTED = range(7)
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EDIVERGED", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
+LAYOUTS = {"stream": 0, "bundle": 1, "collision": 2}
+ALGOS = {"lptl": 0, "nptl": 1, "npol": 2, "nsol": 3}
+STORAGES = {"f64": 0, "f32": 1, "f16s": 2, "bf16s": 3}
+ROUNDINGS = {"rne": 0, "sr": 1}
+PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG = range(6)
+LBM_FLAG_NO_GRAPH = 1
+LBM_AUTO = -1
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+        ("force", ctypes.c_double * 2),
+        ("u_in", ctypes.c_double * 2),
+        ("bc_west", ctypes.c_int32), ("bc_east", ctypes.c_int32),
+        ("bc_south", ctypes.c_int32), ("bc_north", ctypes.c_int32),
+        ("layout", ctypes.c_int32), ("algo", ctypes.c_int32),
+        ("storage", ctypes.c_int32), ("rounding", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+class lbm_info(ctypes.Structure):
+    _fields_ = [
+        ("cells", ctypes.c_int64), ("fluid_cells", ctypes.c_int64), ("steps", ctypes.c_int64),
+        ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("bytes_per_update", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+class lbm_tuning(ctypes.Structure):
+    _fields_ = [
+        ("ns_per_cell", (ctypes.c_double * 4) * 3),
+        ("ns_per_tile", ctypes.c_double),
+        ("valid", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+# Every symbol include/lbm.h declares, with (restype, argtypes).
+_P = ctypes.POINTER
+_vp, _i32, _i64, _u32, _u64, _dbl, _sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                          ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double,
+                                          ctypes.c_size_t)
+SIGNATURES = {
+    "lbm_workspace_bytes": (_i32, [_P(lbm_params), _P(_sz)]),
+    "lbm_create": (_i32, [_P(lbm_params), _vp, _vp, _sz, _vp, _P(_vp)]),
+    "lbm_init": (_i32, [_vp, _vp, _vp, _vp]),
+    "lbm_step": (_i32, [_vp, _i64, _u32]),
+    "lbm_sync": (_i32, [_vp]),
+    "lbm_wait": (_i32, [_vp, _dbl]),
+    "lbm_read_moments": (_i32, [_vp, _vp, _vp, _vp]),
+    "lbm_moments_device": (_i32, [_vp, _vp, _vp, _vp]),
+    "lbm_mass": (_i32, [_vp, _P(_dbl)]),
+    "lbm_force": (_i32, [_vp, _vp, _P(_dbl)]),
+    "lbm_read_populations": (_i32, [_vp, _vp, _i32]),
+    "lbm_write_populations": (_i32, [_vp, _vp, _i32]),
+    "lbm_get_info": (_i32, [_vp, _P(lbm_info)]),
+    "lbm_destroy": (None, [_vp]),
+    "lbm_last_error": (ctypes.c_char_p, []),
+    "lbm_layout_index": (_i64, [_i32, _i64, _i64, _i32]),
+    "lbm_quantize": (_i32, [_i32, _i32, _u64, _i64, _vp, _vp, _vp, _i64, _vp]),
+    "lbm_tune": (_i32, [_P(lbm_params), _vp, _vp, _sz, _vp, _P(lbm_tuning)]),
+    "lbm_batch_plan": (_i32, [_i32, _P(lbm_params), _P(lbm_tuning)]),
+    "lbm_batch_workspace_bytes": (_i32, [_i32, _P(lbm_params), _P(_sz)]),
+    "lbm_batch_create": (_i32, [_i32, _P(lbm_params), _P(_vp), _vp, _sz, _vp, _P(_vp)]),
+    "lbm_batch_init": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "lbm_batch_step": (_i32, [_vp, _i64, _u32]),
+    "lbm_batch_sync": (_i32, [_vp]),
+    "lbm_batch_read_moments": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "lbm_batch_read_populations": (_i32, [_vp, _i32, _vp, _i32]),
+    "lbm_batch_get_info": (_i32, [_vp, _P(_i64), _P(_i32), _P(_i64)]),
+    "lbm_batch_destroy": (None, [_vp]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load liblbm.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise RuntimeError(f"liblbm.so not built ({_build.LIB}); run "
+                                   "paper_2607_20650_gb300.build.build()")
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != LBM_OK:
+        raise LbmError(status, where, load().lbm_last_error().decode())
+
+
+def _ptr(a) -> int | None:
+    """Device or host address of a torch tensor / numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+
+
+def make_params(nx, ny, tau, *, force=(0.0, 0.0), u_in=(0.0, 0.0), bc=(PERIODIC,) * 4,
+                layout="stream", algo="nptl", storage="f32", rounding="rne", seed=0,
+                tile=(0, 0), flags=0) -> lbm_params:
+    """bc = (west, east, south, north)."""
+    p = lbm_params()
+    p.nx, p.ny, p.tau = int(nx), int(ny), float(tau)
+    p.force[0], p.force[1] = force
+    p.u_in[0], p.u_in[1] = u_in
+    p.bc_west, p.bc_east, p.bc_south, p.bc_north = bc
+    p.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+    p.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    p.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
+    p.rounding = ROUNDINGS[rounding] if isinstance(rounding, str) else int(rounding)
+    p.seed = int(seed)
+    p.tile_x, p.tile_y = tile
+    p.flags = int(flags)
+    return p
+
+
+# ------------------------------------------------------------ C names
+
+def lbm_workspace_bytes(p: lbm_params) -> int:
+    b = ctypes.c_size_t()
+    _check(load().lbm_workspace_bytes(ctypes.byref(p), ctypes.byref(b)), "lbm_workspace_bytes")
+    return b.value
+
+
+def lbm_create(p: lbm_params, mask: np.ndarray, workspace, nbytes: int, stream: int):
+    m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    h = ctypes.c_void_p()
+    _check(load().lbm_create(ctypes.byref(p), m.ctypes.data, _ptr(workspace), nbytes, stream,
+                             ctypes.byref(h)), "lbm_create")
+    return h
+
+
+def lbm_init(h, rho=None, ux=None, uy=None):
+    arrs = [_f64(a) for a in (rho, ux, uy)]
+    _check(load().lbm_init(h, *[_ptr(a) for a in arrs]), "lbm_init")
+
+
+def lbm_step(h, nsteps: int, want_moments: bool = False):
+    _check(load().lbm_step(h, int(nsteps), 1 if want_moments else 0), "lbm_step")
+
+
+def lbm_sync(h):
+    _check(load().lbm_sync(h), "lbm_sync")
+
+
+def lbm_wait(h, timeout_s: float) -> int:
+    """Returns the status (LBM_OK or LBM_ETIMEOUT); raises on other errors."""
+    s = load().lbm_wait(h, float(timeout_s))
+    if s not in (LBM_OK, LBM_ETIMEOUT):
+        _check(s, "lbm_wait")
+    return s
+
+
+def lbm_read_moments(h, N: int):
+    out = [np.empty(N) for _ in range(3)]
+    _check(load().lbm_read_moments(h, *[a.ctypes.data for a in out]), "lbm_read_moments")
+    return out
+
+
+def lbm_moments_device(h, rho, ux, uy):
+    _check(load().lbm_moments_device(h, _ptr(rho), _ptr(ux), _ptr(uy)), "lbm_moments_device")
+
+
+def lbm_mass(h) -> float:
+    out = ctypes.c_double()
+    _check(load().lbm_mass(h, ctypes.byref(out)), "lbm_mass")
+    return out.value
+
+
+def lbm_force(h, body=None) -> np.ndarray:
+    out = (ctypes.c_double * 2)()
+    _check(load().lbm_force(h, _ptr(body), out), "lbm_force")
+    return np.array([out[0], out[1]])
+
+
+def lbm_read_populations(h, N: int, as_: str = "f64") -> np.ndarray:
+    out = np.empty((9, N), dtype=np.float64 if as_ == "f64" else np.float32)
+    _check(load().lbm_read_populations(h, out.ctypes.data, STORAGES[as_]), "lbm_read_populations")
+    return out
+
+
+def lbm_write_populations(h, pops: np.ndarray):
+    a = np.ascontiguousarray(pops)
+    as_ = "f64" if a.dtype == np.float64 else "f32"
+    a = a.astype(np.float64 if as_ == "f64" else np.float32, copy=False)
+    _check(load().lbm_write_populations(h, a.ctypes.data, STORAGES[as_]), "lbm_write_populations")
+
+
+def lbm_get_info(h) -> dict:
+    i = lbm_info()
+    _check(load().lbm_get_info(h, ctypes.byref(i)), "lbm_get_info")
+    return {f: getattr(i, f) for f, _ in lbm_info._fields_ if f != "reserved"}
+
+
+def lbm_destroy(h):
+    load().lbm_destroy(h)
+
+
+def lbm_layout_index(layout, N: int, n: int, i: int) -> int:
+    lay = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+    return int(load().lbm_layout_index(lay, int(N), int(n), int(i)))
+
+
+def lbm_quantize(storage, rounding, seed, t, d_in, d_out, d_back, count, stream):
+    _check(load().lbm_quantize(STORAGES[storage] if isinstance(storage, str) else storage,
+                               ROUNDINGS[rounding] if isinstance(rounding, str) else rounding,
+                               int(seed), int(t), _ptr(d_in), _ptr(d_out), _ptr(d_back),
+                               int(count), stream), "lbm_quantize")
+
+
+# ------------------------------------------------------------ convenience
+
+def _torch():
+    import torch
+    return torch
+
+
+def current_stream() -> int:
+    return _torch().cuda.current_stream().cuda_stream
+
+
+class Lattice:
+    """One lattice on the current CUDA device; workspace owned by a torch tensor."""
+
+    def __init__(self, nx, ny, tau, mask=None, **kw):
+        torch = _torch()
+        self.params = make_params(nx, ny, tau, **kw)
+        self.nx, self.ny = int(nx), int(ny)
+        self.N = self.nx * self.ny
+        nbytes = lbm_workspace_bytes(self.params)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = current_stream()
+        if mask is None:
+            mask = np.zeros(self.N, np.uint8)
+        self.h = lbm_create(self.params, mask, self.workspace, nbytes, self.stream)
+
+    def init(self, rho=None, ux=None, uy=None):
+        lbm_init(self.h, rho, ux, uy)
+        return self
+
+    def step(self, n: int, moments: bool = False):
+        lbm_step(self.h, n, moments)
+        return self
+
+    def sync(self):
+        lbm_sync(self.h)
+        return self
+
+    def moments(self):
+        return lbm_read_moments(self.h, self.N)
+
+    def populations(self, as_: str = "f64") -> np.ndarray:
+        return lbm_read_populations(self.h, self.N, as_)
+
+    def write_populations(self, pops):
+        lbm_write_populations(self.h, pops)
+
+    def mass(self) -> float:
+        return lbm_mass(self.h)
+
+    def force(self, body=None):
+        return lbm_force(self.h, body)
+
+    def info(self) -> dict:
+        return lbm_get_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

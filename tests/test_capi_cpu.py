@@ -1,0 +1,88 @@
+"""CPU checks of the C ABI: the library loads, exports every function that
+include/*.h declares, and the host copy of each layout's index map is the
+bijection Fig. 1 (Sec. 3.2) draws. No compute call needs a GPU here."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2607_20650_gb300 import build, lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return lbm.load()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*[\s\*]+(lbm_[A-Za-z0-9_]+)\s*\(",
+                             text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for core in ("lbm_create", "lbm_step", "lbm_read_moments", "lbm_force", "lbm_mass",
+                 "lbm_batch_create", "lbm_batch_step"):
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in sorted(declared_functions()) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(declared_functions()) <= set(lbm.SIGNATURES)
+
+
+def test_layout_maps_match_fig1_and_are_bijections(lib):
+    for nx, ny in [(1, 1), (3, 2), (7, 5)]:
+        N = nx * ny
+        for name in ("stream", "bundle", "collision"):
+            offs = np.array([[lbm.lbm_layout_index(name, N, n, i) for n in range(N)] for i in range(9)])
+            assert sorted(offs.ravel().tolist()) == list(range(9 * N)), name
+            n = np.arange(N)
+            for i in range(9):
+                if name == "stream":
+                    exp = i * N + n                        # SoA: one array per direction
+                elif name == "collision":
+                    exp = 9 * n + i                        # AoS: the nine values of a node together
+                else:
+                    exp = (i // 3) * 3 * N + 3 * n + i % 3  # SoAoS: bundles {SW,S,SE},{W,0,E},{NW,N,NE}
+                assert (offs[i] == exp).all()
+    assert lbm.lbm_layout_index("stream", 4, 4, 0) == -1
+    assert lbm.lbm_layout_index("stream", 4, 0, 9) == -1
+
+
+def test_bad_params_are_rejected_without_gpu(lib):
+    p = lbm.make_params(16, 8, 0.4)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_workspace_bytes(p)
+    assert e.value.status == lbm.LBM_EINVAL
+    p = lbm.make_params(16, 8, 0.8, bc=(lbm.PERIODIC, lbm.WALL, lbm.PERIODIC, lbm.PERIODIC))
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_workspace_bytes(p)
+    p = lbm.make_params(16, 8, 0.8, bc=(lbm.INLET_ZOUHE, lbm.INLET_ZOUHE, lbm.WALL, lbm.WALL))
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_workspace_bytes(p)
+    p = lbm.make_params(16, 8, 0.8, tile=(64, 16), algo="npol")
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_workspace_bytes(p)
+
+
+def test_workspace_sizes(lib):
+    N = 100 * 60
+    two = lbm.lbm_workspace_bytes(lbm.make_params(100, 60, 0.8, algo="nptl", storage="f32"))
+    one = lbm.lbm_workspace_bytes(lbm.make_params(100, 60, 0.8, algo="npol", storage="f32"))
+    half = lbm.lbm_workspace_bytes(lbm.make_params(100, 60, 0.8, algo="nptl", storage="f16s"))
+    assert two >= 2 * 9 * N * 4 + N + 12 * N
+    assert one < two - 9 * N * 4 + 9 * N * 4 // 2     # one lattice + a buffer grid well below a lattice
+    assert half < two

@@ -1,0 +1,244 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars (from the method and the arithmetic):
+  * FP64 GPU vs FP64 oracle: relative L-inf <= 1e-12 on populations and
+    moments (two FP64 implementations that differ only in rounding order;
+    a few ulps per update over <= 100 updates).
+  * All 3 layouts x 4 algorithms: bit-identical states and moments at equal
+    storage precision (the update is the same arithmetic; only the memory
+    traffic differs), including the stochastically rounded 16-bit stores.
+  * Pure streaming (omega = 0): bit-exact cyclic shift.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests.gpu_helpers import ALGOS, COMBOS, LAYOUTS, Spec, rel_linf, specs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2607_20650_gb300 import lbm  # noqa: E402
+
+SPECS = specs()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2607_20650_gb300 import build
+    build.build()
+    lbm.load()
+
+
+def _fluid(spec, ref):
+    return ref.solid == 0
+
+
+@pytest.mark.parametrize("case", list(SPECS))
+@pytest.mark.parametrize("layout,algo", COMBOS)
+def test_fp64_matches_oracle(case, layout, algo):
+    spec = SPECS[case]
+    T = 60
+    ref = spec.oracle().run(T)
+    lat = spec.gpu(layout=layout, algo=algo, storage="f64", tile=(32, 8))
+    lat.step(T, moments=True).sync()
+    h = lat.populations("f64")
+    rho, ux, uy = lat.moments()
+    fl = _fluid(spec, ref)
+    assert rel_linf(h, ref.h, fl) <= 1e-12
+    assert rel_linf(rho, ref.rho, fl) <= 1e-14
+    assert rel_linf(np.stack([ux, uy]), np.stack([ref.ux, ref.uy]), fl) <= 1e-12
+    assert np.all(h[:, ~fl] == 0.0)
+    assert np.all(rho[~fl] == 1.0) and np.all(ux[~fl] == 0.0)
+    lat.close()
+
+
+STORAGE_CASES = [("f64", "rne"), ("f32", "rne"), ("f16s", "rne"), ("f16s", "sr"),
+                 ("bf16s", "rne"), ("bf16s", "sr")]
+
+
+@pytest.mark.parametrize("case", ["channel", "porous", "walls"])
+@pytest.mark.parametrize("storage,rounding", STORAGE_CASES)
+def test_all_layouts_and_algorithms_bit_identical(case, storage, rounding):
+    spec = SPECS[case]
+    T = 37
+    results = {}
+    for layout, algo in COMBOS:
+        tile = (32, 4) if algo in ("npol", "nsol") else (64, 2)
+        lat = spec.gpu(layout=layout, algo=algo, storage=storage, rounding=rounding, seed=1234,
+                       tile=tile)
+        lat.step(T, moments=True).sync()
+        results[(layout, algo)] = (lat.populations("f64"), *lat.moments())
+        lat.close()
+    base = results[("stream", "lptl")]
+    for key, r in results.items():
+        for a, b in zip(r, base):
+            assert np.array_equal(a, b), key
+
+
+@pytest.mark.parametrize("layout,algo", COMBOS)
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_pure_streaming_is_bit_exact_shift(layout, algo, storage):
+    nx, ny, T = 45, 19, 7
+    rng = np.random.default_rng(3)
+    h0 = rng.normal(0.0, 0.01, size=(9, nx * ny))
+    if storage == "f32":
+        h0 = h0.astype(np.float32).astype(np.float64)
+    lat = lbm.Lattice(nx, ny, math.inf, None, layout=layout, algo=algo, storage=storage,
+                      tile=(32, 4))
+    lat.write_populations(h0)
+    lat.step(T).sync()
+    h = lat.populations("f64")
+    cx = np.array([i % 3 - 1 for i in range(9)])
+    cy = np.array([i // 3 - 1 for i in range(9)])
+    for i in range(9):
+        exp = np.roll(h0[i].reshape(ny, nx), (T * cy[i], T * cx[i]), axis=(0, 1)).ravel()
+        assert np.array_equal(h[i], exp), i
+    lat.close()
+
+
+@pytest.mark.parametrize("case", list(SPECS))
+def test_fp32_close_to_oracle(case):
+    """FP32 arithmetic with shifted FP32 storage after 200 updates: relative
+    L-inf error on rho and v below 1e-5."""
+    spec = SPECS[case]
+    T = 200
+    ref = spec.oracle().run(T)
+    lat = spec.gpu(layout="stream", algo="nptl", storage="f32")
+    lat.step(T, moments=True).sync()
+    rho, ux, uy = lat.moments()
+    fl = ref.solid == 0
+    assert rel_linf(rho, ref.rho, fl) <= 1e-5
+    assert rel_linf(np.stack([ux, uy]), np.stack([ref.ux, ref.uy]), fl) <= 1e-5
+    lat.close()
+
+
+@pytest.mark.parametrize("case", ["porous", "walls", "channel"])
+@pytest.mark.parametrize("algo", ["nptl", "nsol"])
+def test_mass_and_force_match_oracle(case, algo):
+    spec = SPECS[case]
+    T = 50
+    ref = spec.oracle().run(T)
+    lat = spec.gpu(layout="bundle", algo=algo, storage="f64")
+    lat.step(T).sync()
+    m_gpu, m_ref = lat.mass(), ref.mass()
+    assert abs(m_gpu - m_ref) <= 1e-13 * m_ref
+    body = torch.from_numpy(spec.mask.reshape(-1).astype(np.uint8)).cuda()
+    f_gpu = lat.force(body)
+    f_ref = ref.force(spec.mask)
+    assert np.max(np.abs(f_gpu - f_ref)) <= 1e-12 * max(np.max(np.abs(f_ref)), 1e-12)
+    lat.close()
+
+
+def test_graphs_match_single_launches():
+    spec = SPECS["channel"]
+    a = spec.gpu(layout="stream", algo="npol", storage="f32")
+    b = spec.gpu(layout="stream", algo="npol", storage="f32", flags=lbm.LBM_FLAG_NO_GRAPH)
+    a.step(150, moments=True).sync()
+    b.step(150, moments=True).sync()
+    assert np.array_equal(a.populations(), b.populations())
+    for x, y in zip(a.moments(), b.moments()):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_checkpoint_resume_is_bit_exact(algo):
+    spec = SPECS["porous"]
+    a = spec.gpu(layout="collision", algo=algo, storage="f32")
+    a.step(30).sync()
+    snap = a.populations("f32")
+    a.step(20, moments=True).sync()
+    b = spec.gpu(layout="stream", algo=algo, storage="f32")
+    b.write_populations(snap)
+    b.step(20, moments=True).sync()
+    assert np.array_equal(a.populations(), b.populations())
+    a.close()
+    b.close()
+
+
+def test_moments_device_matches_host():
+    spec = SPECS["channel"]
+    lat = spec.gpu(storage="f32")
+    lat.step(10, moments=True).sync()
+    r, u, v = [torch.empty(lat.N, dtype=torch.float32, device="cuda") for _ in range(3)]
+    lbm.lbm_moments_device(lat.h, r, u, v)
+    torch.cuda.synchronize()
+    host = lat.moments()
+    for d, hst in zip((r, u, v), host):
+        assert np.array_equal(d.cpu().numpy().astype(np.float64), hst)
+    lat.close()
+
+
+def test_divergence_is_reported_not_trapped():
+    spec = SPECS["walls"]
+    lat = spec.gpu(storage="f32")
+    h = lat.populations("f64")
+    h[3, spec.nx * 10 + 5] = np.nan
+    lat.write_populations(h)
+    lat.step(2)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.sync()
+    assert e.value.status == lbm.LBM_EDIVERGED
+    lat.sync()          # flag cleared after it was reported
+    lat.close()
+
+
+def test_bounded_wait_times_out_then_completes():
+    lat = lbm.Lattice(2048, 1024, 0.8, None, storage="f32", flags=lbm.LBM_FLAG_NO_GRAPH)
+    lat.step(400)
+    s = lbm.lbm_wait(lat.h, 0.0)
+    assert s in (lbm.LBM_ETIMEOUT, lbm.LBM_OK)
+    assert lbm.lbm_wait(lat.h, 120.0) == lbm.LBM_OK
+    lat.close()
+
+
+def _bf16_rne(x32: np.ndarray) -> np.ndarray:
+    """Round-to-nearest-even FP32 -> BF16 (upper 16 bits), textbook bias trick."""
+    b = x32.view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint32) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def test_codec_round_to_nearest_even_matches_numpy():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(0, 1e-3, 40000), rng.normal(0, 1.0, 40000),
+                        rng.uniform(-7e-8, 7e-8, 20000)]).astype(np.float32)
+    d_in = torch.from_numpy(x).cuda()
+    out = torch.empty(x.size, dtype=torch.int16, device="cuda")
+    back = torch.empty_like(d_in)
+    s = lbm.current_stream()
+    lbm.lbm_quantize("f16s", "rne", 0, 0, d_in, out, back, x.size, s)
+    torch.cuda.synchronize()
+    assert np.array_equal(back.cpu().numpy(), x.astype(np.float16).astype(np.float32))
+    lbm.lbm_quantize("bf16s", "rne", 0, 0, d_in, out, back, x.size, s)
+    torch.cuda.synchronize()
+    assert np.array_equal(back.cpu().numpy(), _bf16_rne(x))
+
+
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+def test_codec_stochastic_rounding_is_unbiased_and_keyed(storage):
+    K = 9 * 200000
+    val = np.float32(1.0e-3 + 3.3e-7)
+    x = np.full(K, val, dtype=np.float32)
+    d_in = torch.from_numpy(x).cuda()
+    out = torch.empty(K, dtype=torch.int16, device="cuda")
+    b1, b2, b3 = (torch.empty_like(d_in) for _ in range(3))
+    s = lbm.current_stream()
+    lbm.lbm_quantize(storage, "sr", 42, 5, d_in, out, b1, K, s)
+    lbm.lbm_quantize(storage, "sr", 42, 5, d_in, out, b2, K, s)
+    lbm.lbm_quantize(storage, "sr", 42, 6, d_in, out, b3, K, s)
+    torch.cuda.synchronize()
+    v1, v2, v3 = (b.cpu().numpy().astype(np.float64) for b in (b1, b2, b3))
+    assert np.array_equal(v1, v2)                    # same keys, same bits
+    assert not np.array_equal(v1, v3)                # another update index, other draws
+    lo, hi = np.unique(v1)[[0, -1]]
+    assert len(np.unique(v1)) == 2 and lo < val < hi  # only the two neighbours
+    p = (float(val) - lo) / (hi - lo)
+    frac = np.mean(v1 == hi)
+    assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / K) + 2 ** -24
