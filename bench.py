@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Throughput of the D2Q9I BGK stream-and-collide update on one GB300.
+
+Workload (default): the large porous medium, 16384 x 8192 nodes (134M),
+seeded random overlapping discs (radii 8-32, solid fraction 0.4), periodic
+in x and y, body force g_x = 1e-6, tau = 0.9. One step = one lattice
+update (pull, bounce-back, moments, BGK + Guo collision, store) of the whole
+lattice, FP32 storage and arithmetic, bundle layout (SoAoS), NPTL (2-D tiles
+of 32 x 4 nodes, two lattices): the fastest two-lattice combination measured
+on this workload. MLUPS counts every node (solid ones included), as the paper does.
+
+Also reported: the same update with FP16/BF16 shifted storage, the one-lattice
+NPOL variant, the batched ensemble of 256 channels against 256 sequential
+single-case runs, the FP64 CPU oracle on a bounded sample (cpu_baseline), and
+an end-to-end number through the C ABI with host buffers (e2e).
+
+Prints ONE JSON line. ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "porous 16384x8192 (134M nodes), discs r 8-32 phi 0.4 seed 3, periodic, g_x 1e-6, tau 0.9"
+METRIC = "D2Q9 BGK MLUPS (FP32 two-lattice, 134M-node porous medium)"
+PROFILE = os.path.join(ROOT, "profiles", "k_two_lattice_f32_bundle_nptl_porous16384x8192.md")
+KERNEL_SOURCES = ["paper_2607_20650_gb300/csrc/lbm_kernels.cuh",
+                  "paper_2607_20650_gb300/csrc/lbm_device.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=16384)
+    ap.add_argument("--ny", type=int, default=8192)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tile", default="")
+    ap.add_argument("--layout", default="bundle", choices=["stream", "bundle", "collision"])
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """dram bytes per launch from the committed ncu summary, if the kernel
+    sources still hash to what was profiled."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    if not m or not s or s.group(1) != kernel_sha():
+        return None
+    return float(m.group(1))
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.tmp.flush()
+        rows = [r.split(",") for r in open(self.tmp.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def launches_for(k: int, graph_block: int = 64) -> int:
+    """Kernels one lbm_step(k) call enqueues: k updates, one counter bump per
+    graph block and one after the directly launched remainder."""
+    n = 0
+    left = k
+    while left > graph_block:
+        n += graph_block + 1
+        left -= graph_block
+    if left > 0:
+        n += left + 1
+    return n
+
+
+def time_steps(lat, k, torch):
+    """k updates bracketed by CUDA events on the lattice's own stream."""
+    from paper_2607_20650_gb300 import lbm
+    s = lat.torch_stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    lbm.lbm_step(lat.h, k, False)
+    e1.record(s)
+    e1.synchronize()
+    lbm.lbm_sync(lat.h)
+    return e0.elapsed_time(e1) / 1e3
+
+
+def cpu_sample(target_s: float = 12.0):
+    """FP64 oracle on the 2048x1024 porous sub-run (same disc statistics,
+    seed 33) for as many updates as fit ~target_s seconds."""
+    import oracle as O
+    from paper_2607_20650_gb300 import geometry as G
+    nx, ny = 2048, 1024
+    mask = G.porous_discs(nx, ny, seed=33)
+    lat = O.Lattice(O.Case(nx, ny, 0.9, fx=1e-6), mask)
+    t = time.perf_counter()
+    lat.run(2)
+    per = (time.perf_counter() - t) / 2
+    k = max(2, int(target_s / per))
+    t = time.perf_counter()
+    lat.run(k)
+    dt = time.perf_counter() - t
+    return {"value": nx * ny * k / dt / 1e6, "unit": "MLUPS", "cores": O.omp_threads(),
+            "kind": "oracle",
+            "sample": f"porous 2048x1024 (seed 33, same statistics), {k} FP64 updates, "
+                      f"{dt:.1f} s, OpenMP threads {O.omp_threads()}"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    import oracle as O
+    from paper_2607_20650_gb300 import geometry as G
+    nx, ny = 2048, 1024
+    mask = G.porous_discs(nx, ny, seed=33)
+    lat = O.Lattice(O.Case(nx, ny, 0.9, fx=1e-6), mask)
+    # Bounded sample per step: updates of the 2M-node sub-run; keep the whole
+    # run within a few minutes.
+    t = time.perf_counter()
+    lat.run(1)
+    per = time.perf_counter() - t
+    budget = 120.0
+    k_per_step = max(1, int(budget / max(steps + warm, 1) / per))
+    for _ in range(warm):
+        lat.run(k_per_step)
+    t = time.perf_counter()
+    for _ in range(steps):
+        lat.run(k_per_step)
+    dt = time.perf_counter() - t
+    mlups = nx * ny * k_per_step * steps / dt / 1e6
+    sample = (f"FP64 oracle, porous 2048x1024 sub-run (seed 33, same statistics as the 16384x8192 "
+              f"workload), {k_per_step} updates per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": steps, "warmup": warm,
+        "ms_per_step": dt / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": O.omp_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2607_20650_gb300 import build, geometry as G, lbm
+    build.build()
+    lbm.load()
+    nx, ny = args.nx, args.ny
+    tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else (32, 4)
+    mask = G.porous_discs(nx, ny, seed=3)
+    kw = dict(force=(1e-6, 0.0), bc=(lbm.PERIODIC,) * 4, layout=args.layout, algo="nptl",
+              storage="f32", tile=tile)
+    stream = torch.cuda.Stream()
+    lat = lbm.Lattice(nx, ny, 0.9, mask, stream=stream, **kw)
+    info = lat.info()
+    lat.step(args.warmup).sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = str(getattr(props, "uuid", local))
+    if gpu_id and not gpu_id.startswith("GPU-") and "-" in gpu_id:
+        gpu_id = "GPU-" + gpu_id
+    barrier()
+    clk = Clocks(gpu_id)
+    dt = time_steps(lat, args.steps, torch)
+    clocks = clk.stop()
+    barrier()
+    if dist is not None:
+        t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    cells = nx * ny
+    mlups = cells * args.steps * world / dt / 1e6
+    per_launch = dt / args.steps
+    hbm, peak_kind = peaks()
+    achieved = info["bytes_per_update"] / per_launch / 1e9
+    traffic = profiled_traffic()
+    result = {
+        "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_launch * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "layout": args.layout, "algo": "nptl",
+                   "tile": f"{info['tile_x']}x{info['tile_y']}", "storage": "f32 shifted",
+                   "fluid_nodes": info["fluid_cells"], "nodes": cells,
+                   "l2": "inputs larger than L2 (two 4.8 GB lattices)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "gpu_launches": launches_for(args.steps),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": info["bytes_per_update"],
+                     "kernel": f"k_two_lattice<float, {args.layout.upper()}, NPTL>"},
+        "clocks": clocks,
+        "mlups_fluid": info["fluid_cells"] * args.steps * world / dt / 1e6,
+    }
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+
+    if not args.no_variants:
+        result["variants"] = variants(args, mask, torch, world)
+    result["e2e"] = e2e(args, mask, torch)
+    if rank == 0 and not args.no_cpu and world == 1:
+        result["cpu_baseline"] = cpu_sample()
+    if rank == 0:
+        print(json.dumps(result))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def variants(args, mask, torch, world):
+    from paper_2607_20650_gb300 import lbm
+    nx, ny = args.nx, args.ny
+    k = min(args.steps, 400)
+    out = {}
+    hbm, _ = peaks()
+    for name, kw in [("f32_bundle_nptl_128x1_allfluid", dict(storage="f32", layout="bundle", tile=(128, 1),
+                                                            geo="fluid")),
+                     ("f32_stream_nptl_32x4", dict(storage="f32", tile=(32, 4))),
+                     ("f32_stream_lptl", dict(storage="f32", algo="lptl")),
+                     ("f32_collision_nptl_64x4", dict(storage="f32", layout="collision", tile=(64, 4))),
+                     ("f32_stream_npol_32x8", dict(storage="f32", algo="npol", tile=(32, 8))),
+                     ("f32_stream_nsol_32x8", dict(storage="f32", algo="nsol", tile=(32, 8))),
+                     ("f16s_rne_bundle_nptl_64x4", dict(storage="f16s", layout="bundle", tile=(64, 4))),
+                     ("bf16s_rne_bundle_nptl_64x4", dict(storage="bf16s", layout="bundle", tile=(64, 4))),
+                     ("f16s_sr_bundle_nptl_64x4", dict(storage="f16s", layout="bundle", tile=(64, 4),
+                                                       rounding="sr", seed=7)),
+                     ("f16s_rne_stream_npol_32x8", dict(storage="f16s", algo="npol", tile=(32, 8)))]:
+        kw = dict(kw)
+        kw.setdefault("layout", "stream")
+        geo = kw.pop("geo", "porous")
+        m = mask if geo == "porous" else np.zeros_like(mask)
+        lat = lbm.Lattice(nx, ny, 0.9, m, stream=torch.cuda.Stream(), force=(1e-6, 0.0),
+                          bc=(lbm.PERIODIC,) * 4, **kw)
+        info = lat.info()
+        lat.step(args.warmup).sync()
+        dt = time_steps(lat, k, torch)
+        out[name] = {"MLUPS": nx * ny * k / dt / 1e6, "ms_per_step": dt / k * 1e3,
+                     "GBps_algorithmic": info["bytes_per_update"] / (dt / k) / 1e9,
+                     "frac_of_measured_hbm": info["bytes_per_update"] / (dt / k) / 1e9 / hbm,
+                     "bytes_per_update": info["bytes_per_update"],
+                     "workspace_GB": info["workspace_bytes"] / 1e9, "steps": k}
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+    return out
+
+
+def e2e(args, mask, torch):
+    """Through the C ABI with host buffers: create (mask H2D), init, K
+    updates, moments D2H (three FP64 arrays), all inside the timed region."""
+    from paper_2607_20650_gb300 import lbm
+    nx, ny = args.nx, args.ny
+    N = nx * ny
+    k = args.steps
+    p = lbm.make_params(nx, ny, 0.9, force=(1e-6, 0.0), bc=(lbm.PERIODIC,) * 4,
+                        layout=args.layout, algo="nptl", storage="f32", tile=(32, 4))
+    nbytes = lbm.lbm_workspace_bytes(p)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    host_mask = np.ascontiguousarray(mask.reshape(-1))
+    rho, ux, uy = (np.empty(N) for _ in range(3))
+    stream = torch.cuda.Stream().cuda_stream
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    h = lbm.lbm_create(p, host_mask, ws, nbytes, stream)
+    lbm.lbm_step(h, k, True)
+    lib = lbm.load()
+    st = lib.lbm_read_moments(h, rho.ctypes.data, ux.ctypes.data, uy.ctypes.data)
+    dt = time.perf_counter() - t
+    lbm.lbm_destroy(h)
+    assert st == 0
+    del ws
+    torch.cuda.empty_cache()
+    return {"value": N * k / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": N / k,
+            "d2h_bytes_per_step": 3 * 8 * N / k, "steps": k,
+            "region": "lbm_create(host mask) + init + K updates + lbm_read_moments(host f64)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -542,6 +542,7 @@ extern "C" lbm_status lbm_write_populations(lbm_lattice *L, const void *host, in
     }
     CK(cudaStreamSynchronize(L->stream));
     CK(cudaMemcpy(L->h.pop[L->cur], raw.data(), raw.size(), cudaMemcpyHostToDevice));
+    CK(L->ops->zero_solid(L->h, L->cur, L->stream));
     if (!L->pl.two) CK(L->ops->publish(L->h, L->cur, (int)(L->steps & 1), L->stream));
     CK(cudaStreamSynchronize(L->stream));
     return LBM_OK;

@@ -44,6 +44,8 @@ struct Ops {
                         int64_t n0, int64_t count, cudaStream_t);
     // Copy tile-edge populations of lattice `src` into halo parity `parity`.
     cudaError_t (*publish)(const HostArgs &, int src, int parity, cudaStream_t);
+    // Store h = 0 at every solid node of lattice `src`.
+    cudaError_t (*zero_solid)(const HostArgs &, int src, cudaStream_t);
     // rho = 1 + sum h, v = sum h c (- F/2 if post_collision) into mom.
     cudaError_t (*state_moments)(const HostArgs &, int src, int post_collision, cudaStream_t);
     // FP64 block partial sums: mass (1 value) or force (2 values) per block.

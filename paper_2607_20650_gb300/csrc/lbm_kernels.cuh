@@ -33,6 +33,7 @@ struct Step {
     uint64_t seed;
     int tx, ty, ntx;
     uint64_t nx_magic;
+    int off32;  // 9N < 2^32: element offsets fit 32 bits
 };
 
 // Host: FP64 constants rounded once to the compute type.
@@ -83,12 +84,45 @@ Step<S> make_step(const HostArgs &h, const StepCall &c) {
     a.ty = h.tile_y;
     a.ntx = h.ntx;
     a.nx_magic = h.nx_magic;
+    a.off32 = (9 * h.N) < (int64_t(1) << 32) ? 1 : 0;
     return a;
 }
 
 template <class S, int L>
 __device__ __forceinline__ typename Codec<S>::C ldp(const S *base, uint32_t N, uint32_t n, int i) {
     return Codec<S>::dec(base[addr<L>(N, n, i)]);
+}
+
+#ifndef LBM_LDG_HINT
+#define LBM_LDG_HINT 0
+#endif
+#ifndef LBM_ST_HINT
+#define LBM_ST_HINT 2
+#endif
+// Loads of the read-only source lattice and stores of the destination
+// lattice of the two-lattice update. Stores default to evict-first
+// (st.global.cs) for the bundle layout, where it measured fastest, and to
+// plain stores elsewhere; LBM_ST_HINT=0/1 forces plain / evict-first.
+template <class S>
+__device__ __forceinline__ S ld_src(const S *p) {
+#if LBM_LDG_HINT == 1
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+template <class S, int L>
+__device__ __forceinline__ void st_dst(S *p, S v) {
+#if LBM_ST_HINT == 1
+    __stcs(p, v);
+#elif LBM_ST_HINT == 2
+    if (L == BUNDLE)
+        __stcs(p, v);
+    else
+        *p = v;
+#else
+    *p = v;
+#endif
 }
 
 // Inlet substitution, collision, divergence flag, moments, and encoding of
@@ -122,7 +156,54 @@ __device__ __forceinline__ void collide_encode(const Step<S> &a, uint32_t x, uin
 }
 
 // ------------------------------------------------------------ two lattices
-// LPTL (LINEAR: one node per thread over n) and NPTL (2-D tiles).
+// Element offset of population i of node 0 in layout L; the offset of node n
+// is lay_mul<L>() * n + lay_base<L>(N, i) for every layout.
+template <int L> __host__ __device__ constexpr uint32_t lay_mul() {
+    return L == STREAM ? 1u : (L == BUNDLE ? 3u : 9u);
+}
+template <int L> __device__ __forceinline__ uint32_t lay_base(uint32_t N, int i) {
+    return L == STREAM ? (uint32_t)i * N
+                       : (L == BUNDLE ? (uint32_t)(i / 3) * 3u * N + (uint32_t)(i % 3) : (uint32_t)i);
+}
+
+// Whether a solid node's record shares a 32-byte DRAM sector with a fluid
+// node's record, from the warp's fluid ballot F (lanes = consecutive nodes).
+// Stream layout: aligned groups of 32/sizeof(S) lanes; bundle / collision:
+// lanes within ceil(32 / record bytes) on either side.
+template <class S, int L>
+__device__ __forceinline__ bool shares_sector(unsigned F, int lane) {
+    if (L == STREAM) {
+        constexpr int G = (int)(32 / sizeof(S)) < 32 ? (int)(32 / sizeof(S)) : 32;
+        const unsigned m = G >= 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(G - 1));
+        return (F & m) != 0u;
+    } else {
+        constexpr int b = (int)(lay_mul<L>() * sizeof(S));
+        constexpr int k = (32 + b - 1) / b;
+        const int lo = lane - k < 0 ? 0 : lane - k;
+        const int hi = lane + k > 31 ? 31 : lane + k;
+        const int w = hi - lo + 1;
+        const unsigned m = w >= 32 ? 0xffffffffu : ((1u << w) - 1u) << lo;
+        return (F & m) != 0u;
+    }
+}
+
+template <class S, int L>
+__device__ __forceinline__ void store_zero(S *dst, uint32_t N, uint32_t n, int off32) {
+    const S z = Codec<S>::enc(typename Codec<S>::C(0), false, 0u);
+    if (off32) {
+        const uint32_t base = lay_mul<L>() * n;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st_dst<S, L>(dst + base + lay_base<L>(N, i), z);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst[addr<L>(N, n, i)] = z;
+    }
+}
+
+// LPTL (LINEAR: one node per thread over n) and NPTL (2-D tiles). Interior
+// nodes take a path with 32-bit element offsets where each pull is one
+// select between two block-uniform offsets (pulled neighbour or own opposite
+// slot); nodes on the domain edge take the general mapping.
 template <class S, int L, bool LINEAR>
 __global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice(const Step<S> a) {
     using C = typename Codec<S>::C;
@@ -140,31 +221,64 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice(const Step<S> a
         n = y * nx + x;
     }
     const uint32_t lk = a.links[n];
-    if (lk == SOLID_LINKS) return;
+    S *__restrict__ dst = a.dst;
+    const bool fluid = lk != SOLID_LINKS;
+    const unsigned F = __ballot_sync(__activemask(), fluid);
+    if (!fluid) {
+        // Solid nodes hold h = 0 and are never read. Where a solid node's
+        // record shares a DRAM sector with a fluid node's, store the zeros
+        // again so the sector is written whole (no read-modify-write).
+        const int lane = (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u);
+        if (shares_sector<S, L>(F, lane)) store_zero<S, L>(dst, a.N, n, a.off32);
+        return;
+    }
+    const S *__restrict__ src = a.src;
     const bool interior = (x - 1u < nx - 2u) && (y - 1u < ny - 2u);
     C g[9];
+    if (interior && a.off32) {
+        const uint32_t base = lay_mul<L>() * n;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        if (i == 4) {
-            g[i] = ldp<S, L>(a.src, a.N, n, 4);
-            continue;
+        for (int i = 0; i < 9; ++i) {
+            uint32_t e;
+            if (i == 4) {
+                e = base + lay_base<L>(a.N, 4);
+            } else {
+                const uint32_t kp = lay_base<L>(a.N, i) - lay_mul<L>() * (uint32_t)(cy(i) * (int)nx + cx(i));
+                const uint32_t kb = lay_base<L>(a.N, opp(i));
+                e = base + (((lk >> link_bit(i)) & 1u) ? kb : kp);
+            }
+            g[i] = Codec<S>::dec(ld_src(src + e));
         }
-        if ((lk >> link_bit(i)) & 1u) {
-            g[i] = ldp<S, L>(a.src, a.N, n, opp(i));
-        } else if (interior) {
-            g[i] = ldp<S, L>(a.src, a.N, n - (uint32_t)(cy(i) * (int)nx + cx(i)), i);
-        } else {
-            int xs, ys, j;
-            if (map_pull(a.geo, (int)x, (int)y, i, xs, ys, j) == PULL_NODE)
-                g[i] = ldp<S, L>(a.src, a.N, (uint32_t)ys * nx + (uint32_t)xs, j);
-            else
-                g[i] = C(0);  // inlet unknown, reconstructed in collide_encode
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (i == 4) {
+                g[i] = ldp<S, L>(src, a.N, n, 4);
+                continue;
+            }
+            if ((lk >> link_bit(i)) & 1u) {
+                g[i] = ldp<S, L>(src, a.N, n, opp(i));
+            } else if (interior) {
+                g[i] = ldp<S, L>(src, a.N, n - (uint32_t)(cy(i) * (int)nx + cx(i)), i);
+            } else {
+                int xs, ys, j;
+                if (map_pull(a.geo, (int)x, (int)y, i, xs, ys, j) == PULL_NODE)
+                    g[i] = ldp<S, L>(src, a.N, (uint32_t)ys * nx + (uint32_t)xs, j);
+                else
+                    g[i] = C(0);  // inlet unknown, reconstructed in collide_encode
+            }
         }
     }
     S e[9];
     collide_encode(a, x, n, g, e);
+    if (a.off32) {
+        const uint32_t base = lay_mul<L>() * n;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) a.dst[addr<L>(a.N, n, i)] = e[i];
+        for (int i = 0; i < 9; ++i) st_dst<S, L>(dst + base + lay_base<L>(a.N, i), e[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst[addr<L>(a.N, n, i)] = e[i];
+    }
 }
 
 // ------------------------------------------------------------ buffer grid
@@ -230,6 +344,8 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_npol(const Step<S> a) {
         lk = a.links[n];
     }
     const bool fluid = lk != SOLID_LINKS;
+    const unsigned F = __ballot_sync(__activemask(), fluid);
+    const bool zero_fill = !fluid && shares_sector<S, L>(F, (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u));
     C g[9];
     if (fluid) {
         const bool inner = x > x0 && x < x1 && y > y0 && y < y1;
@@ -260,6 +376,8 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_npol(const Step<S> a) {
         for (int i = 0; i < 9; ++i) lat[addr<L>(a.N, n, i)] = e[i];
         if (!(x > x0 && x < x1 && y > y0 && y < y1))
             halo_publish(a.halo_wr, a.tx, a.ty, a.ntx, bx, by, x, y, x0, y0, x1, y1, e);
+    } else if (valid && zero_fill) {
+        store_zero<S, L>(lat, a.N, n, a.off32);  // whole-sector writes, as in k_two_lattice
     }
 }
 
@@ -291,6 +409,8 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_nsol(const Step<S> a) {
         lk = a.links[n];
     }
     const bool fluid = lk != SOLID_LINKS;
+    const unsigned F = __ballot_sync(__activemask(), fluid);
+    const bool zero_fill = !fluid && shares_sector<S, L>(F, tid & 31);
     fl[tid] = fluid ? 1 : 0;
     if (fluid) {
 #pragma unroll
@@ -343,6 +463,8 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_nsol(const Step<S> a) {
         for (int i = 0; i < 9; ++i) lat[addr<L>(a.N, n, opp(i))] = e[i];
         if (!(x > x0 && x < x1 && y > y0 && y < y1))
             halo_publish(a.halo_wr, a.tx, a.ty, a.ntx, bx, by, x, y, x0, y0, x1, y1, e);
+    } else if (valid && zero_fill) {
+        store_zero<S, L>(lat, a.N, n, a.off32);
     }
 }
 
@@ -365,6 +487,14 @@ __global__ void k_init(const Step<S> a, const double *rho, const double *ux, con
         typename Codec<S>::C hc = (typename Codec<S>::C)h;
         a.dst[addr<L>(a.N, n, rev ? opp(i) : i)] = Codec<S>::enc(hc, false, 0u);
     }
+}
+
+// Solid nodes hold h = 0 (restored after host writes of the state).
+template <class S, int L>
+__global__ void k_zero_solid(const Step<S> a, S *lat) {
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= a.N || a.links[n] != SOLID_LINKS) return;
+    store_zero<S, L>(lat, a.N, n, a.off32);
 }
 
 // Copy every tile-edge node's outgoing values into one buffer-grid parity.
@@ -566,6 +696,15 @@ cudaError_t op_publish(const HostArgs &h, int src, int parity, cudaStream_t st) 
 }
 
 template <class S>
+cudaError_t op_zero_solid(const HostArgs &h, int src, cudaStream_t st) {
+    const Step<S> a = make_step<S>(h, StepCall{src, 0, 0, 0});
+    const unsigned g = (unsigned)((h.N + 255) / 256);
+    S *lat = (S *)h.pop[src];
+    LBM_LAYOUT_SWITCH(h, (k_zero_solid<S, L_><<<g, 256, 0, st>>>(a, lat)));
+    return cudaGetLastError();
+}
+
+template <class S>
 cudaError_t op_state_moments(const HostArgs &h, int src, int post, cudaStream_t st) {
     Step<S> a = make_step<S>(h, StepCall{src, 0, 0, 1});
     const unsigned g = (unsigned)((h.N + 255) / 256);
@@ -614,6 +753,7 @@ Ops make_ops() {
     o.step = op_step<S>;
     o.init = op_init<S>;
     o.publish = op_publish<S>;
+    o.zero_solid = op_zero_solid<S>;
     o.state_moments = op_state_moments<S>;
     o.mass = op_mass<S>;
     o.force = op_force<S>;

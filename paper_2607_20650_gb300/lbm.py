@@ -269,14 +269,16 @@ def current_stream() -> int:
 class Lattice:
     """One lattice on the current CUDA device; workspace owned by a torch tensor."""
 
-    def __init__(self, nx, ny, tau, mask=None, **kw):
+    def __init__(self, nx, ny, tau, mask=None, stream=None, **kw):
+        """stream: a torch.cuda.Stream (default: the current stream)."""
         torch = _torch()
         self.params = make_params(nx, ny, tau, **kw)
         self.nx, self.ny = int(nx), int(ny)
         self.N = self.nx * self.ny
         nbytes = lbm_workspace_bytes(self.params)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-        self.stream = current_stream()
+        self.torch_stream = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = self.torch_stream.cuda_stream
         if mask is None:
             mask = np.zeros(self.N, np.uint8)
         self.h = lbm_create(self.params, mask, self.workspace, nbytes, self.stream)
