@@ -103,8 +103,8 @@ typedef struct lbm_params {
     int32_t storage;         /* lbm_storage */
     int32_t rounding;        /* lbm_rounding */
     uint64_t seed;           /* stochastic-rounding seed */
-    int32_t tile_x, tile_y;  /* NPTL/NPOL/NSOL tile; 0 = default; tile_x*tile_y <= 1024,
-                                tile_x a multiple of 32 */
+    int32_t tile_x, tile_y;  /* NPTL/NPOL/NSOL tile (0, 0 = 32 x 8); tile_x*tile_y <= 512;
+                                tile_x a multiple of 32 keeps warps on one row */
     uint32_t flags;          /* LBM_FLAG_* */
 } lbm_params;
 
@@ -186,6 +186,21 @@ int64_t lbm_layout_index(int32_t layout, int64_t N, int64_t n, int32_t i);
 lbm_status lbm_quantize(int32_t storage, int32_t rounding, uint64_t seed, int64_t t,
                         const float *d_in, void *d_out, float *d_back, int64_t count,
                         void *cuda_stream);
+
+/* Total mass like lbm_mass, for callers that cannot provide device memory:
+ * code hosted by a framework that owns every device allocation and forbids
+ * direct cudaMalloc, or loops that must not incur an allocation's implicit
+ * synchronisation. The paper has no counterpart; this is a library utility.
+ * d_h: canonical FP32 deviations h[i*N + n] (9N floats, device); d_solid: N
+ * bytes, nonzero = solid (device); out: host double, written before return
+ * (the call synchronises cuda_stream). Allocates nothing: its scratch is a
+ * fixed device array inside the library (one per GPU, kept until exit), so
+ * N is limited to 134,217,728 nodes (LBM_EINVAL beyond). All calls share
+ * that array: calls whose GPU work overlaps race. The first call on a device
+ * looks the array up with that device current; make it before any stream
+ * capture. */
+lbm_status lbm_mass_f32_noalloc(const float *d_h, const uint8_t *d_solid, int64_t N, double *out,
+                                void *cuda_stream);
 
 /* ---------------------------------------------------------------- batches
  * Many independent lattices advanced together, one persistent launch per

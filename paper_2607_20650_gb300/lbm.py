@@ -86,6 +86,7 @@ SIGNATURES = {
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_layout_index": (_i64, [_i32, _i64, _i64, _i32]),
     "lbm_quantize": (_i32, [_i32, _i32, _u64, _i64, _vp, _vp, _vp, _i64, _vp]),
+    "lbm_mass_f32_noalloc": (_i32, [_vp, _vp, _i64, _P(_dbl), _vp]),
     "lbm_tune": (_i32, [_P(lbm_params), _vp, _vp, _sz, _vp, _P(lbm_tuning)]),
     "lbm_batch_plan": (_i32, [_i32, _P(lbm_params), _P(lbm_tuning)]),
     "lbm_batch_workspace_bytes": (_i32, [_i32, _P(lbm_params), _P(_sz)]),
@@ -253,6 +254,14 @@ def lbm_quantize(storage, rounding, seed, t, d_in, d_out, d_back, count, stream)
                                ROUNDINGS[rounding] if isinstance(rounding, str) else rounding,
                                int(seed), int(t), _ptr(d_in), _ptr(d_out), _ptr(d_back),
                                int(count), stream), "lbm_quantize")
+
+
+def lbm_mass_f32_noalloc(d_h, d_solid, N: int, stream: int) -> float:
+    """Mass of a canonical FP32 state on the device without any workspace."""
+    out = ctypes.c_double()
+    _check(load().lbm_mass_f32_noalloc(_ptr(d_h), _ptr(d_solid), int(N), ctypes.byref(out), stream),
+           "lbm_mass_f32_noalloc")
+    return out.value
 
 
 # ------------------------------------------------------------ convenience
