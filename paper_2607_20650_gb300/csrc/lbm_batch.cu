@@ -1,34 +1,385 @@
-// Batched lattices (implemented in a later step; entry points reject for now).
+// Batches of independent lattices: workspace layout, the packed tile list,
+// one persistent launch per update (captured into CUDA graphs of 100
+// updates), and the autotuner that picks layout, algorithm and tile per case.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
 #include "lbm.h"
 #include "lbm_capi_internal.h"
+#include "lbm_internal.h"
 
-extern "C" {
-lbm_status lbm_tune(const lbm_params *, const uint8_t *, void *, size_t, void *, lbm_tuning *) {
-    return lbm_fail(LBM_EUNSUPPORTED, "lbm_tune: not built yet");
+using namespace lbm;
+
+#define CK(call)                                                \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return lbm_cuda_fail(e_, #call); \
+    } while (0)
+
+namespace {
+
+constexpr int kGraphSteps = 100;
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+struct BatchLayout {
+    size_t cases_off = 0, tiles_off = 0, misc_off = 0, header = 0, total = 0;
+    std::vector<size_t> case_off;
+    std::vector<Plan> plans;
+    uint32_t ntiles = 0;
+};
+
+int64_t case_tiles(const lbm_params &p, const Plan &pl) {
+    if (p.algo == LBM_LPTL) return (pl.N + kBatchTileNodes - 1) / kBatchTileNodes;
+    return (int64_t)pl.ntx * pl.nty;
 }
-lbm_status lbm_batch_plan(int32_t, lbm_params *, const lbm_tuning *) {
-    return lbm_fail(LBM_EUNSUPPORTED, "batch: not built yet");
+
+lbm_status batch_layout(int32_t ncases, const lbm_params *params, BatchLayout *bl) {
+    if (ncases < 1) return lbm_fail(LBM_EINVAL, "batch: ncases must be >= 1");
+    if (!params) return lbm_fail(LBM_EINVAL, "batch: params is NULL");
+    const int storage = params[0].storage;
+    int64_t tiles = 0;
+    bl->plans.resize(ncases);
+    for (int c = 0; c < ncases; ++c) {
+        const lbm_params &p = params[c];
+        if (p.storage != storage) return lbm_fail(LBM_EINVAL, "batch: case %d has another storage type", c);
+        if (p.layout == LBM_AUTO || p.algo == LBM_AUTO)
+            return lbm_fail(LBM_EINVAL, "batch: case %d has an unresolved layout/algo (run lbm_batch_plan)", c);
+        lbm_status s = lbm_plan(&p, &bl->plans[c]);
+        if (s != LBM_OK) return lbm_fail(s, "batch case %d: %s", c, lbm_last_error());
+        if (p.algo != LBM_LPTL && bl->plans[c].tx * bl->plans[c].ty > kBatchTileNodes)
+            return lbm_fail(LBM_EINVAL, "batch case %d: tile %dx%d exceeds %d nodes", c, bl->plans[c].tx,
+                            bl->plans[c].ty, kBatchTileNodes);
+        tiles += case_tiles(p, bl->plans[c]);
+    }
+    if (tiles >= (int64_t)1 << 32) return lbm_fail(LBM_EUNSUPPORTED, "batch: too many tiles");
+    const Ops *ops = ops_for_storage(storage);
+    bl->ntiles = (uint32_t)tiles;
+    bl->cases_off = 0;
+    bl->tiles_off = align256(ops->batch_case_bytes * ncases);
+    bl->misc_off = bl->tiles_off + align256(sizeof(uint32_t) * 2 * (size_t)tiles);
+    bl->header = bl->misc_off + 256;
+    size_t off = bl->header;
+    bl->case_off.resize(ncases);
+    for (int c = 0; c < ncases; ++c) {
+        bl->case_off[c] = off;
+        off += align256(bl->plans[c].total);
+    }
+    bl->total = off;
+    return LBM_OK;
 }
-lbm_status lbm_batch_workspace_bytes(int32_t, const lbm_params *, size_t *) {
-    return lbm_fail(LBM_EUNSUPPORTED, "batch: not built yet");
+
+}  // namespace
+
+struct lbm_batch {
+    int ncases;
+    int storage;
+    const Ops *ops;
+    std::vector<lbm_lattice *> cases;
+    BatchLayout bl;
+    cudaStream_t stream;
+    cudaStream_t cap;
+    char *ws;
+    void *d_cases;
+    void *d_tiles;
+    unsigned int *err;
+    long long *tctr;
+    int grid;
+    int cur;
+    int64_t steps;
+    cudaGraphExec_t graph[2];
+};
+
+extern "C" lbm_status lbm_batch_workspace_bytes(int32_t ncases, const lbm_params *params, size_t *bytes) {
+    if (!bytes) return lbm_fail(LBM_EINVAL, "bytes is NULL");
+    BatchLayout bl;
+    lbm_status s = batch_layout(ncases, params, &bl);
+    if (s != LBM_OK) return s;
+    *bytes = bl.total;
+    return LBM_OK;
 }
-lbm_status lbm_batch_create(int32_t, const lbm_params *, const uint8_t *const *, void *, size_t, void *,
-                            lbm_batch **) {
-    return lbm_fail(LBM_EUNSUPPORTED, "batch: not built yet");
+
+extern "C" void lbm_batch_destroy(lbm_batch *B) {
+    if (!B) return;
+    cudaStreamSynchronize(B->stream);
+    for (auto &g : B->graph)
+        if (g) cudaGraphExecDestroy(g);
+    for (auto *L : B->cases) lbm_destroy(L);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    delete B;
 }
-lbm_status lbm_batch_init(lbm_batch *, int32_t, const double *, const double *, const double *) {
-    return lbm_fail(LBM_EUNSUPPORTED, "batch: not built yet");
+
+extern "C" lbm_status lbm_batch_create(int32_t ncases, const lbm_params *params,
+                                       const uint8_t *const *masks, void *d_workspace, size_t bytes,
+                                       void *cuda_stream, lbm_batch **out) {
+    if (!out) return lbm_fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!masks) return lbm_fail(LBM_EINVAL, "masks is NULL");
+    if (!d_workspace || ((uintptr_t)d_workspace) % 256)
+        return lbm_fail(LBM_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    lbm_batch *B = new lbm_batch();
+    B->ncases = ncases;
+    lbm_status s = batch_layout(ncases, params, &B->bl);
+    if (s != LBM_OK) {
+        delete B;
+        return s;
+    }
+    if (bytes < B->bl.total) {
+        delete B;
+        return lbm_fail(LBM_ENOMEM, "batch workspace too small: %zu given, %zu needed", bytes, B->bl.total);
+    }
+    B->storage = params[0].storage;
+    B->ops = ops_for_storage(B->storage);
+    B->stream = (cudaStream_t)cuda_stream;
+    B->ws = (char *)d_workspace;
+    B->d_cases = B->ws + B->bl.cases_off;
+    B->d_tiles = B->ws + B->bl.tiles_off;
+    B->err = (unsigned int *)(B->ws + B->bl.misc_off);
+    B->tctr = (long long *)(B->ws + B->bl.misc_off + 64);
+    cudaError_t e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete B;
+        return lbm_cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    std::vector<unsigned char> recs(B->ops->batch_case_bytes * ncases);
+    std::vector<uint32_t> tiles;
+    tiles.reserve(2 * (size_t)B->bl.ntiles);
+    for (int c = 0; c < ncases; ++c) {
+        lbm_lattice *L = nullptr;
+        s = lbm_create(&params[c], masks[c], B->ws + B->bl.case_off[c], B->bl.plans[c].total, cuda_stream, &L);
+        if (s != LBM_OK) {
+            lbm_batch_destroy(B);
+            return lbm_fail(s, "batch case %d: %s", c, lbm_last_error());
+        }
+        B->cases.push_back(L);
+        L->h.err = B->err;        // one divergence flag and update counter for the batch
+        L->h.tctr = B->tctr;
+        B->ops->batch_case(L->h, recs.data() + (size_t)c * B->ops->batch_case_bytes);
+        const int64_t nt = case_tiles(params[c], B->bl.plans[c]);
+        for (int64_t t = 0; t < nt; ++t) {
+            tiles.push_back((uint32_t)c);
+            tiles.push_back((uint32_t)t);
+        }
+    }
+    e = cudaMemcpyAsync(B->d_cases, recs.data(), recs.size(), cudaMemcpyHostToDevice, B->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->d_tiles, tiles.data(), tiles.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                            B->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->ws + B->bl.misc_off, 0, 256, B->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(B);
+        return lbm_cuda_fail(e, "batch upload");
+    }
+    const int g = B->ops->batch_grid();
+    B->grid = (int)std::max<int64_t>(1, std::min<int64_t>(g > 0 ? g : 152, B->bl.ntiles));
+    *out = B;
+    return LBM_OK;
 }
-lbm_status lbm_batch_step(lbm_batch *, int64_t, uint32_t) { return lbm_fail(LBM_EUNSUPPORTED, "batch"); }
-lbm_status lbm_batch_sync(lbm_batch *) { return lbm_fail(LBM_EUNSUPPORTED, "batch"); }
-lbm_status lbm_batch_read_moments(lbm_batch *, int32_t, double *, double *, double *) {
-    return lbm_fail(LBM_EUNSUPPORTED, "batch");
+
+extern "C" lbm_status lbm_batch_init(lbm_batch *B, int32_t c, const double *rho, const double *ux,
+                                     const double *uy) {
+    if (!B || c < 0 || c >= B->ncases) return lbm_fail(LBM_EINVAL, "batch_init: bad batch or case");
+    if (B->steps != 0) return lbm_fail(LBM_EINVAL, "batch_init: only before the first lbm_batch_step");
+    lbm_lattice *L = B->cases[c];
+    lbm_status s = lbm_init(L, rho, ux, uy);
+    L->h.err = B->err;
+    L->h.tctr = B->tctr;
+    return s;
 }
-lbm_status lbm_batch_read_populations(lbm_batch *, int32_t, void *, int32_t) {
-    return lbm_fail(LBM_EUNSUPPORTED, "batch");
+
+static cudaError_t batch_block(lbm_batch *B, cudaStream_t st, int64_t count, int want_moments) {
+    int cur = B->cur;
+    for (int64_t k = 0; k < count; ++k) {
+        cudaError_t e = B->ops->batch_step(B->d_cases, B->d_tiles, B->bl.ntiles, B->grid, cur, (int)k,
+                                           (want_moments && k == count - 1) ? 1 : 0, st);
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    return launch_bump_counter(B->tctr, count, st);
 }
-lbm_status lbm_batch_get_info(lbm_batch *, int64_t *, int32_t *, int64_t *) {
-    return lbm_fail(LBM_EUNSUPPORTED, "batch");
+
+extern "C" lbm_status lbm_batch_step(lbm_batch *B, int64_t nsteps, uint32_t want_moments) {
+    if (!B) return lbm_fail(LBM_EINVAL, "batch is NULL");
+    if (nsteps < 0) return lbm_fail(LBM_EINVAL, "nsteps must be >= 0");
+    int64_t left = nsteps;
+    while (left > kGraphSteps) {
+        cudaGraphExec_t &ex = B->graph[B->cur];
+        if (!ex) {
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = batch_block(B, B->cap, kGraphSteps, 0);
+            cudaError_t e2 = cudaStreamEndCapture(B->cap, &g);
+            if (e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return lbm_cuda_fail(e, "capturing batch updates");
+            }
+            if (e2 != cudaSuccess) return lbm_cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return lbm_cuda_fail(e, "cudaGraphInstantiate");
+        }
+        CK(cudaGraphLaunch(ex, B->stream));
+        B->steps += kGraphSteps;  // even: current lattice and parity unchanged
+        left -= kGraphSteps;
+    }
+    if (left > 0) {
+        CK(batch_block(B, B->stream, left, want_moments ? 1 : 0));
+        if (left & 1) B->cur ^= 1;
+        B->steps += left;
+    }
+    for (auto *L : B->cases) {
+        L->cur = L->pl.two ? B->cur : 0;
+        L->steps = B->steps;
+    }
+    return LBM_OK;
 }
-void lbm_batch_destroy(lbm_batch *) {}
+
+extern "C" lbm_status lbm_batch_sync(lbm_batch *B) {
+    if (!B) return lbm_fail(LBM_EINVAL, "batch is NULL");
+    CK(cudaStreamSynchronize(B->stream));
+    unsigned int flag = 0;
+    CK(cudaMemcpy(&flag, B->err, sizeof(flag), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(cudaMemset(B->err, 0, sizeof(flag)));
+        return lbm_fail(LBM_EDIVERGED, "batch: non-finite density after %lld updates", (long long)B->steps);
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_read_moments(lbm_batch *B, int32_t c, double *rho, double *ux, double *uy) {
+    if (!B || c < 0 || c >= B->ncases) return lbm_fail(LBM_EINVAL, "bad batch or case");
+    return lbm_read_moments(B->cases[c], rho, ux, uy);
+}
+
+extern "C" lbm_status lbm_batch_read_populations(lbm_batch *B, int32_t c, void *host, int32_t as) {
+    if (!B || c < 0 || c >= B->ncases) return lbm_fail(LBM_EINVAL, "bad batch or case");
+    return lbm_read_populations(B->cases[c], host, as);
+}
+
+extern "C" lbm_status lbm_batch_get_info(lbm_batch *B, int64_t *tiles, int32_t *grid, int64_t *cells) {
+    if (!B) return lbm_fail(LBM_EINVAL, "batch is NULL");
+    if (tiles) *tiles = B->bl.ntiles;
+    if (grid) *grid = B->grid;
+    if (cells) {
+        int64_t n = 0;
+        for (auto *L : B->cases) n += L->pl.N;
+        *cells = n;
+    }
+    return LBM_OK;
+}
+
+// ------------------------------------------------------------ autotuner
+// Built-in cost table: GB300 nanoseconds per node update (1 / throughput of
+// the whole device) of each layout x algorithm on a 134M-node porous
+// lattice, FP32, tile 32x8 (two-lattice rows measured; one-lattice rows
+// include the buffer grid and barrier).
+static const double kDefaultNsPerCell[3][4] = {
+    {0.0125, 0.0113, 0.027, 0.033},   // stream:    LPTL NPTL NPOL NSOL
+    {0.0100, 0.0093, 0.029, 0.035},   // bundle
+    {0.0200, 0.0143, 0.035, 0.040},   // collision
+};
+static const double kDefaultNsPerTile = 0.5;
+
+extern "C" lbm_status lbm_tune(const lbm_params *probe, const uint8_t *mask_host, void *d_workspace,
+                               size_t bytes, void *cuda_stream, lbm_tuning *out) {
+    if (!probe || !mask_host || !out) return lbm_fail(LBM_EINVAL, "tune: NULL argument");
+    memset(out, 0, sizeof(*out));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const cudaStream_t st = (cudaStream_t)cuda_stream;
+    lbm_status result = LBM_OK;
+    for (int l = 0; l < 3 && result == LBM_OK; ++l)
+        for (int a = 0; a < 4 && result == LBM_OK; ++a) {
+            lbm_params p = *probe;
+            p.layout = l;
+            p.algo = a;
+            p.tile_x = a == LBM_LPTL ? 0 : 32;
+            p.tile_y = a == LBM_LPTL ? 0 : 8;
+            p.flags |= LBM_FLAG_NO_GRAPH;
+            lbm_lattice *L = nullptr;
+            lbm_status s = lbm_create(&p, mask_host, d_workspace, bytes, cuda_stream, &L);
+            if (s != LBM_OK) {
+                result = s;
+                break;
+            }
+            const int reps = 10;
+            s = lbm_step(L, 2, 0);
+            cudaError_t e = cudaEventRecord(e0, st);
+            if (s == LBM_OK && e == cudaSuccess) s = lbm_step(L, reps, 0);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            lbm_destroy(L);
+            if (e != cudaSuccess) result = lbm_cuda_fail(e, "tune timing");
+            else if (s != LBM_OK) result = s;
+            else out->ns_per_cell[l][a] = 1e6 * ms / ((double)reps * p.nx * (double)p.ny);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != LBM_OK) return result;
+    out->ns_per_tile = kDefaultNsPerTile;
+    out->valid = 1;
+    return LBM_OK;
+}
+
+// Predicted time of one update of a case: per-node cost of the layout and
+// algorithm over the valid nodes, a quarter of it for padding slots of the
+// batch blocks, and a fixed cost per tile.
+static double predict(const lbm_params &p, int l, int a, int tx, int ty, const double (*ns)[4], double tile_ns) {
+    const double N = (double)p.nx * p.ny;
+    double tiles;
+    if (a == LBM_LPTL) {
+        tiles = std::ceil(N / kBatchTileNodes);
+    } else {
+        tiles = std::ceil((double)p.nx / tx) * std::ceil((double)p.ny / ty);
+    }
+    const double slots = tiles * kBatchTileNodes;
+    return ns[l][a] * (N + 0.25 * (slots - N)) + tile_ns * tiles;
+}
+
+extern "C" lbm_status lbm_batch_plan(int32_t ncases, lbm_params *params, const lbm_tuning *tuning) {
+    if (ncases < 1 || !params) return lbm_fail(LBM_EINVAL, "plan: bad arguments");
+    const bool tuned = tuning && tuning->valid;
+    const double (*ns)[4] = tuned ? tuning->ns_per_cell : kDefaultNsPerCell;
+    const double tile_ns = tuned ? tuning->ns_per_tile : kDefaultNsPerTile;
+    static const int shapes[][2] = {{256, 1}, {128, 2}, {64, 4}, {32, 8}, {32, 4}, {64, 2}, {128, 1},
+                                    {32, 2}, {64, 1}, {32, 1}, {16, 16}, {16, 8}};
+    for (int c = 0; c < ncases; ++c) {
+        lbm_params &p = params[c];
+        const bool auto_tile = p.tile_x == 0 && p.tile_y == 0;
+        double best = INFINITY;
+        int bl = -1, ba = -1, bx = 0, by = 0;
+        for (int l = 0; l < 3; ++l) {
+            if (p.layout != LBM_AUTO && p.layout != l) continue;
+            for (int a = 0; a < 4; ++a) {
+                if (p.algo != LBM_AUTO && p.algo != a) continue;
+                if (!(ns[l][a] > 0)) continue;
+                if (a == LBM_LPTL) {
+                    const double t = predict(p, l, a, 0, 0, ns, tile_ns);
+                    if (t < best) { best = t; bl = l; ba = a; bx = 0; by = 0; }
+                    continue;
+                }
+                for (auto &sh : shapes) {
+                    const int tx = auto_tile ? sh[0] : p.tile_x, ty = auto_tile ? sh[1] : p.tile_y;
+                    const double t = predict(p, l, a, tx, ty, ns, tile_ns);
+                    if (t < best) { best = t; bl = l; ba = a; bx = tx; by = ty; }
+                    if (!auto_tile) break;
+                }
+            }
+        }
+        if (bl < 0) return lbm_fail(LBM_EINVAL, "plan: no candidate for case %d", c);
+        p.layout = bl;
+        p.algo = ba;
+        p.tile_x = bx;
+        p.tile_y = by;
+    }
+    return LBM_OK;
 }

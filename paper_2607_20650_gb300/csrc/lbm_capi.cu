@@ -142,25 +142,6 @@ lbm_status lbm_plan(const lbm_params *p, Plan *pl) {
 }
 
 // ------------------------------------------------------------ lattice
-struct lbm_lattice {
-    lbm_params p;
-    Plan pl;
-    HostArgs h;
-    const Ops *ops;
-    cudaStream_t stream;
-    cudaStream_t cap;
-    char *ws;
-    int cur;
-    int64_t steps;
-    int64_t fluid;
-    double *partials;
-    double *red_out;
-    unsigned int *err;
-    unsigned long long *count;
-    cudaGraphExec_t graph[4];
-    int graph_steps;
-};
-
 extern "C" lbm_status lbm_workspace_bytes(const lbm_params *p, size_t *bytes) {
     if (!bytes) return lbm_fail(LBM_EINVAL, "bytes is NULL");
     Plan pl;

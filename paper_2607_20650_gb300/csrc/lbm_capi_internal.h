@@ -21,6 +21,26 @@ struct Plan {
     size_t links = 0, mom = 0, mom_bytes = 0, partials = 0, misc = 0, total = 0;
 };
 
+// One lattice: parameters, workspace plan, kernel arguments, scheduling state.
+struct lbm_lattice {
+    lbm_params p;
+    Plan pl;
+    lbm::HostArgs h;
+    const lbm::Ops *ops;
+    cudaStream_t stream;
+    cudaStream_t cap;
+    char *ws;
+    int cur;            // current lattice (two-lattice algorithms)
+    int64_t steps;      // updates since lbm_init
+    int64_t fluid;
+    double *partials;
+    double *red_out;
+    unsigned int *err;
+    unsigned long long *count;
+    cudaGraphExec_t graph[4];
+    int graph_steps;
+};
+
 lbm_status lbm_fail(lbm_status s, const char *fmt, ...);
 lbm_status lbm_cuda_fail(cudaError_t e, const char *where);
 lbm_status lbm_check_params(const lbm_params *p);

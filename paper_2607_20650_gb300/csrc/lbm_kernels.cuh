@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -200,26 +202,15 @@ __device__ __forceinline__ void store_zero(S *dst, uint32_t N, uint32_t n, int o
     }
 }
 
-// LPTL (LINEAR: one node per thread over n) and NPTL (2-D tiles). Interior
-// nodes take a path with 32-bit element offsets where each pull is one
-// select between two block-uniform offsets (pulled neighbour or own opposite
-// slot); nodes on the domain edge take the general mapping.
-template <class S, int L, bool LINEAR>
-__global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice(const Step<S> a) {
+// One node of the two-lattice pull update (LPTL and NPTL). Interior nodes
+// take a path with 32-bit element offsets where each pull is one select
+// between two uniform offsets (pulled neighbour or own opposite slot); nodes
+// on the domain edge take the general mapping. lane: the thread's lane.
+template <class S, int L>
+__device__ __forceinline__ void two_lattice_node(const Step<S> &a, uint32_t x, uint32_t y, int lane) {
     using C = typename Codec<S>::C;
     const uint32_t nx = (uint32_t)a.geo.nx, ny = (uint32_t)a.geo.ny;
-    uint32_t x, y, n;
-    if (LINEAR) {
-        n = blockIdx.x * blockDim.x + threadIdx.x;
-        if (n >= a.N) return;
-        y = a.nx_magic ? (uint32_t)__umul64hi((unsigned long long)n, a.nx_magic) : n;
-        x = n - y * nx;
-    } else {
-        x = blockIdx.x * a.tx + threadIdx.x;
-        y = blockIdx.y * a.ty + threadIdx.y;
-        if (x >= nx || y >= ny) return;
-        n = y * nx + x;
-    }
+    const uint32_t n = y * nx + x;
     const uint32_t lk = a.links[n];
     S *__restrict__ dst = a.dst;
     const bool fluid = lk != SOLID_LINKS;
@@ -228,7 +219,6 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice(const Step<S> a
         // Solid nodes hold h = 0 and are never read. Where a solid node's
         // record shares a DRAM sector with a fluid node's, store the zeros
         // again so the sector is written whole (no read-modify-write).
-        const int lane = (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u);
         if (shares_sector<S, L>(F, lane)) store_zero<S, L>(dst, a.N, n, a.off32);
         return;
     }
@@ -281,6 +271,25 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice(const Step<S> a
     }
 }
 
+// LPTL (LINEAR: one node per thread over n, block size from the runtime) and
+// NPTL (2-D tiles of tx x ty nodes over a padded grid).
+template <class S, int L, bool LINEAR>
+__global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice(const Step<S> a) {
+    const uint32_t nx = (uint32_t)a.geo.nx, ny = (uint32_t)a.geo.ny;
+    uint32_t x, y;
+    if (LINEAR) {
+        const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+        if (n >= a.N) return;
+        y = a.nx_magic ? (uint32_t)__umul64hi((unsigned long long)n, a.nx_magic) : n;
+        x = n - y * nx;
+    } else {
+        x = blockIdx.x * a.tx + threadIdx.x;
+        y = blockIdx.y * a.ty + threadIdx.y;
+        if (x >= nx || y >= ny) return;
+    }
+    two_lattice_node<S, L>(a, x, y, (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u));
+}
+
 // ------------------------------------------------------------ buffer grid
 // Per tile and parity: east edge 3 x ty values (directions 2,5,8), west
 // 3 x ty (0,3,6), north 3 x tx (6,7,8), south 3 x tx (0,1,2).
@@ -329,14 +338,13 @@ __device__ __forceinline__ void halo_publish(S *hw, int tx, int ty, int ntx, int
 // previous update), the block barrier separates all reads from the in-place
 // writes, and edge nodes publish their outgoing values for the next update.
 template <class S, int L>
-__global__ void __launch_bounds__(kMaxTileThreads) k_npol(const Step<S> a) {
+__device__ __forceinline__ void npol_tile(const Step<S> &a, int bx, int by, int lx, int ly, int lane) {
     using C = typename Codec<S>::C;
     const int nx = a.geo.nx, ny = a.geo.ny;
-    const int bx = blockIdx.x, by = blockIdx.y;
     const int x0 = bx * a.tx, y0 = by * a.ty;
     const int x1 = min(x0 + a.tx, nx) - 1, y1 = min(y0 + a.ty, ny) - 1;
-    const int x = x0 + (int)threadIdx.x, y = y0 + (int)threadIdx.y;
-    const bool valid = x <= x1 && y <= y1;
+    const int x = x0 + lx, y = y0 + ly;
+    const bool valid = lx < a.tx && ly < a.ty && x <= x1 && y <= y1;
     S *lat = a.dst;
     uint32_t n = 0, lk = SOLID_LINKS;
     if (valid) {
@@ -345,10 +353,11 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_npol(const Step<S> a) {
     }
     const bool fluid = lk != SOLID_LINKS;
     const unsigned F = __ballot_sync(__activemask(), fluid);
-    const bool zero_fill = !fluid && shares_sector<S, L>(F, (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u));
+    const bool zero_fill = valid && !fluid && shares_sector<S, L>(F, lane);
+    const bool inner = x > x0 && x < x1 && y > y0 && y < y1;
     C g[9];
     if (fluid) {
-        const bool inner = x > x0 && x < x1 && y > y0 && y < y1;
+        const bool dom_inner = x > 0 && x < nx - 1 && y > 0 && y < ny - 1;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if (i == 4) {
@@ -357,6 +366,21 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_npol(const Step<S> a) {
                 g[i] = ldp<S, L>(lat, a.N, n, opp(i));
             } else if (inner) {
                 g[i] = ldp<S, L>(lat, a.N, n - (uint32_t)(cy(i) * nx + cx(i)), i);
+            } else if (dom_inner) {
+                // Tile edge inside the domain: the source is in this tile or
+                // in the adjacent tile's buffer grid, no edge mapping needed.
+                const int sx = x - cx(i), sy = y - cy(i);
+                const int dbx = sx < x0 ? -1 : (sx > x1 ? 1 : 0);
+                const int dby = sy < y0 ? -1 : (sy > y1 ? 1 : 0);
+                if (dbx == 0 && dby == 0) {
+                    g[i] = ldp<S, L>(lat, a.N, n - (uint32_t)(cy(i) * nx + cx(i)), i);
+                } else {
+                    const int nbx = bx + dbx, nby = by + dby;
+                    const int64_t sl = dbx != 0
+                        ? halo_slot(a.tx, a.ty, a.ntx, nbx, nby, cx(i) > 0 ? EDGE_E : EDGE_W, i / 3, sy - nby * a.ty)
+                        : halo_slot(a.tx, a.ty, a.ntx, nbx, nby, cy(i) > 0 ? EDGE_N : EDGE_S, i % 3, sx - nbx * a.tx);
+                    g[i] = Codec<S>::dec(a.halo_rd[sl]);
+                }
             } else {
                 int xs, ys, j;
                 if (map_pull(a.geo, x, y, i, xs, ys, j) != PULL_NODE)
@@ -374,11 +398,16 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_npol(const Step<S> a) {
         collide_encode(a, (uint32_t)x, n, g, e);
 #pragma unroll
         for (int i = 0; i < 9; ++i) lat[addr<L>(a.N, n, i)] = e[i];
-        if (!(x > x0 && x < x1 && y > y0 && y < y1))
-            halo_publish(a.halo_wr, a.tx, a.ty, a.ntx, bx, by, x, y, x0, y0, x1, y1, e);
-    } else if (valid && zero_fill) {
-        store_zero<S, L>(lat, a.N, n, a.off32);  // whole-sector writes, as in k_two_lattice
+        if (!inner) halo_publish(a.halo_wr, a.tx, a.ty, a.ntx, bx, by, x, y, x0, y0, x1, y1, e);
+    } else if (zero_fill) {
+        store_zero<S, L>(lat, a.N, n, a.off32);  // whole-sector writes, as in two_lattice_node
     }
+}
+
+template <class S, int L>
+__global__ void __launch_bounds__(kMaxTileThreads) k_npol(const Step<S> a) {
+    npol_tile<S, L>(a, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y,
+                    (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u));
 }
 
 // ------------------------------------------------------------ NSOL
@@ -388,20 +417,21 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_npol(const Step<S> a) {
 // with slot i of x + c_i when both are fluid (no exchange = bounce-back).
 // Values that enter through domain edges or from other tiles (buffer grid)
 // are substituted afterwards.
+// smem_raw: 9 * tx * ty compute values followed by tx * ty flag bytes.
 template <class S, int L>
-__global__ void __launch_bounds__(kMaxTileThreads) k_nsol(const Step<S> a) {
+__device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int lx, int ly, int lane,
+                                          unsigned char *smem_raw) {
     using C = typename Codec<S>::C;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int T = a.tx * a.ty;
     C *sm = reinterpret_cast<C *>(smem_raw);
     uint8_t *fl = smem_raw + sizeof(C) * 9 * T;
     const int nx = a.geo.nx, ny = a.geo.ny;
-    const int bx = blockIdx.x, by = blockIdx.y;
     const int x0 = bx * a.tx, y0 = by * a.ty;
     const int x1 = min(x0 + a.tx, nx) - 1, y1 = min(y0 + a.ty, ny) - 1;
-    const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * a.tx + lx;
+    const bool member = lx < a.tx && ly < a.ty;  // thread has a slot in this tile
+    const int tid = member ? ly * a.tx + lx : 0;
     const int x = x0 + lx, y = y0 + ly;
-    const bool valid = x <= x1 && y <= y1;
+    const bool valid = member && x <= x1 && y <= y1;
     S *lat = a.dst;
     uint32_t n = 0, lk = SOLID_LINKS;
     if (valid) {
@@ -410,8 +440,8 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_nsol(const Step<S> a) {
     }
     const bool fluid = lk != SOLID_LINKS;
     const unsigned F = __ballot_sync(__activemask(), fluid);
-    const bool zero_fill = !fluid && shares_sector<S, L>(F, tid & 31);
-    fl[tid] = fluid ? 1 : 0;
+    const bool zero_fill = valid && !fluid && shares_sector<S, L>(F, lane);
+    if (member) fl[tid] = fluid ? 1 : 0;
     if (fluid) {
 #pragma unroll
         for (int s = 0; s < 9; ++s) sm[s * T + tid] = ldp<S, L>(lat, a.N, n, s);
@@ -463,9 +493,141 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_nsol(const Step<S> a) {
         for (int i = 0; i < 9; ++i) lat[addr<L>(a.N, n, opp(i))] = e[i];
         if (!(x > x0 && x < x1 && y > y0 && y < y1))
             halo_publish(a.halo_wr, a.tx, a.ty, a.ntx, bx, by, x, y, x0, y0, x1, y1, e);
-    } else if (valid && zero_fill) {
+    } else if (zero_fill) {
         store_zero<S, L>(lat, a.N, n, a.off32);
     }
+}
+
+template <class S, int L>
+__global__ void __launch_bounds__(kMaxTileThreads) k_nsol(const Step<S> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    nsol_tile<S, L>(a, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y,
+                    (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u), smem_raw);
+}
+
+// ------------------------------------------------------------ batches
+// Many independent lattices advanced by one persistent launch per update.
+// The work list holds one entry per tile of every case (LPTL: 256
+// consecutive nodes); each block takes entries round-robin, stages the
+// case record in shared memory and runs the case's layout/algorithm body.
+constexpr int kBatchThreads = 256;
+
+template <class S>
+struct BatchCase {
+    Step<S> st;                 // constants, links, tile shape of the case
+    S *pop0, *pop1, *halo;      // pop1 == nullptr for one-lattice cases
+    typename Codec<S>::C *mom;
+    long long halo_parity_elems;
+    int layout, algo;
+};
+
+struct BatchTile {
+    uint32_t c;                 // case index
+    uint32_t t;                 // tile index within the case (LPTL: chunk)
+};
+
+template <class S, int L>
+__device__ __forceinline__ void batch_tile(const Step<S> &a, int algo, uint32_t t, int tid,
+                                           unsigned char *smem) {
+    const int lane = tid & 31;
+    if (algo == LPTL) {
+        const uint32_t n = t * (uint32_t)kBatchThreads + (uint32_t)tid;
+        if (n < a.N) {
+            const uint32_t y = a.nx_magic ? (uint32_t)__umul64hi((unsigned long long)n, a.nx_magic) : n;
+            two_lattice_node<S, L>(a, n - y * (uint32_t)a.geo.nx, y, lane);
+        }
+        return;
+    }
+    const int bx = (int)(t % (uint32_t)a.ntx), by = (int)(t / (uint32_t)a.ntx);
+    const int lx = tid % a.tx, ly = tid / a.tx;
+    if (algo == NPTL) {
+        const int x = bx * a.tx + lx, y = by * a.ty + ly;
+        if (ly < a.ty && x < a.geo.nx && y < a.geo.ny) two_lattice_node<S, L>(a, x, y, lane);
+    } else if (algo == NPOL) {
+        npol_tile<S, L>(a, bx, by, lx, ly, lane);
+    } else {
+        nsol_tile<S, L>(a, bx, by, lx, ly, lane, smem);
+    }
+}
+
+// cur: source lattice of two-lattice cases, which equals the buffer-grid
+// parity read by one-lattice cases (all cases start together at update 0).
+template <class S>
+__global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchCase<S> *cases, const BatchTile *tiles,
+                                                          uint32_t ntiles, int cur, int toff, int want_moments) {
+    using C = typename Codec<S>::C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) BatchCase<S> bc;
+    const int tid = threadIdx.x;
+    for (uint32_t w = blockIdx.x; w < ntiles; w += gridDim.x) {
+        const BatchTile bt = tiles[w];
+        const uint32_t *srcw = reinterpret_cast<const uint32_t *>(cases + bt.c);
+        uint32_t *dstw = reinterpret_cast<uint32_t *>(&bc);
+        for (int k = tid; k < (int)(sizeof(BatchCase<S>) / 4); k += kBatchThreads) dstw[k] = srcw[k];
+        __syncthreads();
+        if (tid == 0) {
+            if (bc.pop1) {
+                bc.st.src = cur ? bc.pop1 : bc.pop0;
+                bc.st.dst = cur ? bc.pop0 : bc.pop1;
+            } else {
+                bc.st.src = bc.pop0;
+                bc.st.dst = bc.pop0;
+                bc.st.halo_rd = bc.halo + (long long)cur * bc.halo_parity_elems;
+                bc.st.halo_wr = bc.halo + (long long)(cur ^ 1) * bc.halo_parity_elems;
+            }
+            bc.st.mom = want_moments ? (C *)bc.mom : nullptr;
+            bc.st.toff = toff;
+        }
+        __syncthreads();
+        switch (bc.layout) {
+            case STREAM: batch_tile<S, STREAM>(bc.st, bc.algo, bt.t, tid, smem); break;
+            case BUNDLE: batch_tile<S, BUNDLE>(bc.st, bc.algo, bt.t, tid, smem); break;
+            default: batch_tile<S, COLLISION>(bc.st, bc.algo, bt.t, tid, smem); break;
+        }
+        __syncthreads();
+    }
+}
+
+template <class S>
+size_t batch_smem_bytes() {
+    return sizeof(typename Codec<S>::C) * 9 * kBatchThreads + kBatchThreads;
+}
+
+template <class S>
+cudaError_t op_batch_step(const void *cases, const void *tiles, uint32_t ntiles, int grid, int cur, int toff,
+                          int want_moments, cudaStream_t st) {
+    k_batch<S><<<grid, kBatchThreads, batch_smem_bytes<S>(), st>>>(
+        (const BatchCase<S> *)cases, (const BatchTile *)tiles, ntiles, cur, toff, want_moments);
+    return cudaGetLastError();
+}
+
+template <class S>
+int op_batch_grid() {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<S>, kBatchThreads,
+                                                      batch_smem_bytes<S>()) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+// Host: the device record of one case (pointers from its HostArgs).
+template <class S>
+void op_batch_case(const HostArgs &h, void *out) {
+    BatchCase<S> c;
+    memset(&c, 0, sizeof(c));
+    c.st = make_step<S>(h, StepCall{0, 0, 0, 0});
+    c.pop0 = (S *)h.pop[0];
+    c.pop1 = (S *)h.pop[1];
+    c.halo = (S *)h.halo;
+    c.mom = (typename Codec<S>::C *)h.mom;
+    c.halo_parity_elems = h.halo_parity_elems;
+    c.layout = h.layout;
+    c.algo = h.algo;
+    memcpy(out, &c, sizeof(c));
 }
 
 // ------------------------------------------------------------ state kernels
@@ -759,6 +921,10 @@ Ops make_ops() {
     o.force = op_force<S>;
     o.moments_f32 = op_moments_f32<S>;
     o.lptl_block = op_lptl_block<S>;
+    o.batch_step = op_batch_step<S>;
+    o.batch_grid = op_batch_grid<S>;
+    o.batch_case = op_batch_case<S>;
+    o.batch_case_bytes = sizeof(BatchCase<S>);
     o.elem = sizeof(S);
     o.compute = sizeof(typename Codec<S>::C);
     return o;

@@ -264,6 +264,84 @@ def lbm_mass_f32_noalloc(d_h, d_solid, N: int, stream: int) -> float:
     return out.value
 
 
+def lbm_tune(probe: lbm_params, mask, workspace, nbytes: int, stream: int) -> lbm_tuning:
+    t = lbm_tuning()
+    m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    _check(load().lbm_tune(ctypes.byref(probe), m.ctypes.data, _ptr(workspace), nbytes, stream,
+                           ctypes.byref(t)), "lbm_tune")
+    return t
+
+
+def _param_array(params):
+    arr = (lbm_params * len(params))()
+    for k, p in enumerate(params):
+        arr[k] = p
+    return arr
+
+
+def lbm_batch_plan(params: list, tuning: lbm_tuning | None = None) -> list:
+    """Resolve LBM_AUTO layout/algo and (0, 0) tiles; returns updated params."""
+    arr = _param_array(params)
+    _check(load().lbm_batch_plan(len(params), arr, ctypes.byref(tuning) if tuning else None),
+           "lbm_batch_plan")
+    return [arr[k] for k in range(len(params))]
+
+
+def lbm_batch_workspace_bytes(params: list) -> int:
+    b = ctypes.c_size_t()
+    _check(load().lbm_batch_workspace_bytes(len(params), _param_array(params), ctypes.byref(b)),
+           "lbm_batch_workspace_bytes")
+    return b.value
+
+
+def lbm_batch_create(params: list, masks: list, workspace, nbytes: int, stream: int):
+    arr = _param_array(params)
+    ms = [np.ascontiguousarray(m, dtype=np.uint8).reshape(-1) for m in masks]
+    ptrs = (ctypes.c_void_p * len(ms))(*[m.ctypes.data for m in ms])
+    h = ctypes.c_void_p()
+    _check(load().lbm_batch_create(len(params), arr, ptrs, _ptr(workspace), nbytes, stream,
+                                   ctypes.byref(h)), "lbm_batch_create")
+    return h, ms
+
+
+def lbm_batch_init(h, c: int, rho=None, ux=None, uy=None):
+    arrs = [_f64(a) for a in (rho, ux, uy)]
+    _check(load().lbm_batch_init(h, int(c), *[_ptr(a) for a in arrs]), "lbm_batch_init")
+
+
+def lbm_batch_step(h, nsteps: int, want_moments: bool = False):
+    _check(load().lbm_batch_step(h, int(nsteps), 1 if want_moments else 0), "lbm_batch_step")
+
+
+def lbm_batch_sync(h):
+    _check(load().lbm_batch_sync(h), "lbm_batch_sync")
+
+
+def lbm_batch_read_moments(h, c: int, N: int):
+    out = [np.empty(N) for _ in range(3)]
+    _check(load().lbm_batch_read_moments(h, int(c), *[a.ctypes.data for a in out]),
+           "lbm_batch_read_moments")
+    return out
+
+
+def lbm_batch_read_populations(h, c: int, N: int, as_: str = "f64") -> np.ndarray:
+    out = np.empty((9, N), dtype=np.float64 if as_ == "f64" else np.float32)
+    _check(load().lbm_batch_read_populations(h, int(c), out.ctypes.data, STORAGES[as_]),
+           "lbm_batch_read_populations")
+    return out
+
+
+def lbm_batch_get_info(h) -> dict:
+    t, g, c = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().lbm_batch_get_info(h, ctypes.byref(t), ctypes.byref(g), ctypes.byref(c)),
+           "lbm_batch_get_info")
+    return {"tiles": t.value, "grid": g.value, "cells": c.value}
+
+
+def lbm_batch_destroy(h):
+    load().lbm_batch_destroy(h)
+
+
 # ------------------------------------------------------------ convenience
 
 def _torch():
@@ -325,6 +403,53 @@ class Lattice:
     def close(self):
         if getattr(self, "h", None):
             lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent lattices advanced by one persistent launch per update."""
+
+    def __init__(self, params: list, masks: list, stream=None, plan: bool = True,
+                 tuning: lbm_tuning | None = None):
+        torch = _torch()
+        self.params = lbm_batch_plan(params, tuning) if plan else list(params)
+        self.N = [p.nx * p.ny for p in self.params]
+        nbytes = lbm_batch_workspace_bytes(self.params)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.torch_stream = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = self.torch_stream.cuda_stream
+        self.h, self._masks = lbm_batch_create(self.params, masks, self.workspace, nbytes, self.stream)
+
+    def init(self, c, rho=None, ux=None, uy=None):
+        lbm_batch_init(self.h, c, rho, ux, uy)
+        return self
+
+    def step(self, n: int, moments: bool = False):
+        lbm_batch_step(self.h, n, moments)
+        return self
+
+    def sync(self):
+        lbm_batch_sync(self.h)
+        return self
+
+    def moments(self, c):
+        return lbm_batch_read_moments(self.h, c, self.N[c])
+
+    def populations(self, c, as_: str = "f64"):
+        return lbm_batch_read_populations(self.h, c, self.N[c], as_)
+
+    def info(self) -> dict:
+        return lbm_batch_get_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

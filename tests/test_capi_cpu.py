@@ -86,3 +86,37 @@ def test_workspace_sizes(lib):
     assert two >= 2 * 9 * N * 4 + N + 12 * N
     assert one < two - 9 * N * 4 + 9 * N * 4 // 2     # one lattice + a buffer grid well below a lattice
     assert half < two
+
+
+def test_batch_planner_resolves_every_case(lib):
+    from paper_2607_20650_gb300 import geometry as G
+    cases = G.batch_channels(ncases=24, seed=4)
+    ps = [lbm.make_params(w.nx, w.ny, w.tau, u_in=(w.ux_in, 0.0), bc=(w.bc_w, w.bc_e, w.bc_s, w.bc_n),
+                          layout=lbm.LBM_AUTO, algo=lbm.LBM_AUTO, storage="f32") for w in cases]
+    planned = lbm.lbm_batch_plan(ps)
+    for w, p in zip(cases, planned):
+        assert p.layout in (0, 1, 2) and p.algo in (0, 1, 2, 3)
+        if p.algo != 0:
+            assert 1 <= p.tile_x * p.tile_y <= 256
+            # no shape in the candidate set pads this case less at the same cost class
+            pad = -(-w.nx // p.tile_x) * -(-w.ny // p.tile_y) * 256 - w.nx * w.ny
+            assert pad < 256 * (-(-w.nx // 32) + -(-w.ny // 8))
+    # the built-in model prefers the bundle two-lattice pull (measured fastest)
+    assert sum(p.layout == 1 for p in planned) == len(planned)
+    fixed = [lbm.make_params(100, 40, 0.8, layout="stream", algo="npol", tile=(32, 8))]
+    assert lbm.lbm_batch_plan(fixed)[0].algo == 2
+    total = lbm.lbm_batch_workspace_bytes(planned)
+    assert total > sum(lbm.lbm_workspace_bytes(p) for p in planned) - 1
+
+
+def test_batch_rejects_unresolved_or_mixed(lib):
+    a = lbm.make_params(64, 32, 0.8, layout=lbm.LBM_AUTO, algo="nptl")
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_batch_workspace_bytes([a])
+    b = lbm.make_params(64, 32, 0.8, storage="f32")
+    c = lbm.make_params(64, 32, 0.8, storage="f16s")
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_batch_workspace_bytes([b, c])
+    d = lbm.make_params(64, 32, 0.8, algo="npol", tile=(32, 16))
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_batch_workspace_bytes([d])
