@@ -291,6 +291,7 @@ def run_ours(args):
 
     if not args.no_variants:
         result["variants"] = variants(args, mask, torch, world)
+        result["batched"] = batched(args, torch)
     result["e2e"] = e2e(args, mask, torch)
     if rank == 0 and not args.no_cpu and world == 1:
         result["cpu_baseline"] = cpu_sample()
@@ -336,6 +337,74 @@ def variants(args, mask, torch, world):
         del lat
         torch.cuda.empty_cache()
     return out
+
+
+def batched(args, torch):
+    """256 independent channels (seeded widths 64-1024, heights 32-512, tau in
+    [0.55, 1.5], one obstacle each, Zou-He inlet, zero-gradient outflow, FP32):
+    one persistent launch per update (graphs of 100 updates, layout /
+    algorithm / tile per case from the autotuner) against the same 256 cases
+    run one after another as single lattices (each lbm_step(K), graphs of 64)."""
+    from paper_2607_20650_gb300 import geometry as G, lbm
+    ws = G.batch_channels(256, seed=4)
+    probe_w = G.batch_channels(1, seed=99, wmin=1024, wmax=1024, hmin=512, hmax=512)[0]
+    bc = lambda w: (w.bc_w, w.bc_e, w.bc_s, w.bc_n)
+    probe = lbm.make_params(probe_w.nx, probe_w.ny, probe_w.tau, u_in=(probe_w.ux_in, 0.0), bc=bc(probe_w),
+                            storage="f32")
+    pb = lbm.lbm_workspace_bytes(lbm.make_params(probe_w.nx, probe_w.ny, 0.8, storage="f32",
+                                                 layout="collision", algo="lptl"))
+    stream = torch.cuda.Stream()
+    pws = torch.empty(pb, dtype=torch.uint8, device="cuda")
+    tuning = lbm.lbm_tune(probe, probe_w.mask, pws, pb, stream.cuda_stream)
+    del pws
+    params = [lbm.make_params(w.nx, w.ny, w.tau, u_in=(w.ux_in, 0.0), bc=bc(w), storage="f32",
+                              layout=lbm.LBM_AUTO, algo=lbm.LBM_AUTO) for w in ws]
+    b = lbm.Batch(params, [w.mask for w in ws], stream=stream, tuning=tuning)
+    for c, w in enumerate(ws):
+        b.init(c, None, w.ux0, w.uy0)
+    cells = sum(w.cells for w in ws)
+    k = max(100, min(args.steps, 1000) // 100 * 100)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.step(100).sync()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(k)
+    e1.record(stream)
+    e1.synchronize()
+    b.sync()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    info = b.info()
+    chosen = {}
+    for p in b.params:
+        key = f"{['stream', 'bundle', 'collision'][p.layout]}/{['lptl', 'nptl', 'npol', 'nsol'][p.algo]}"
+        chosen[key] = chosen.get(key, 0) + 1
+    b.close()
+    del b
+    singles = []
+    for w, p in zip(ws, [lbm.lbm_batch_plan([q], tuning)[0] for q in params]):
+        lat = lbm.Lattice(w.nx, w.ny, w.tau, w.mask, stream=stream, u_in=(w.ux_in, 0.0), bc=bc(w),
+                          storage="f32", layout=p.layout, algo=p.algo,
+                          tile=(p.tile_x, p.tile_y))
+        lat.init(None, w.ux0, w.uy0)
+        singles.append(lat)
+    for lat in singles:
+        lbm.lbm_step(lat.h, 100, False)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for lat in singles:
+        lbm.lbm_step(lat.h, k, False)
+    e1.record(stream)
+    e1.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    for lat in singles:
+        lat.close()
+    del singles
+    torch.cuda.empty_cache()
+    return {"cases": len(ws), "nodes": cells, "steps": k,
+            "batched_MLUPS": cells * k / t_batch / 1e6, "sequential_MLUPS": cells * k / t_seq / 1e6,
+            "speedup": t_seq / t_batch, "tiles": info["tiles"], "grid": info["grid"],
+            "chosen": chosen,
+            "tuned_ns_per_node": [[round(tuning.ns_per_cell[l][a], 5) for a in range(4)] for l in range(3)]}
 
 
 def e2e(args, mask, torch):

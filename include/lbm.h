@@ -244,8 +244,9 @@ lbm_status lbm_batch_step(lbm_batch *B, int64_t nsteps, uint32_t want_moments);
 lbm_status lbm_batch_sync(lbm_batch *B);
 lbm_status lbm_batch_read_moments(lbm_batch *B, int32_t c, double *rho, double *ux, double *uy);
 lbm_status lbm_batch_read_populations(lbm_batch *B, int32_t c, void *host, int32_t as);
-/* Number of tiles in the packed work list and the persistent grid size. */
-lbm_status lbm_batch_get_info(lbm_batch *B, int64_t *tiles, int32_t *grid, int64_t *cells);
+/* Entries in the packed work list (4 tiles of a two-lattice case or one tile
+ * of a one-lattice case each), the persistent grid size, and total nodes. */
+lbm_status lbm_batch_get_info(lbm_batch *B, int64_t *items, int32_t *grid, int64_t *cells);
 void lbm_batch_destroy(lbm_batch *B);
 
 #ifdef __cplusplus

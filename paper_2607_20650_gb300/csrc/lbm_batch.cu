@@ -34,9 +34,16 @@ struct BatchLayout {
     uint32_t ntiles = 0;
 };
 
+// Work items of a case: groups of kBatchSuperHost tiles for the two-lattice
+// algorithms (LPTL tile = 256 consecutive nodes), single tiles otherwise.
 int64_t case_tiles(const lbm_params &p, const Plan &pl) {
-    if (p.algo == LBM_LPTL) return (pl.N + kBatchTileNodes - 1) / kBatchTileNodes;
-    return (int64_t)pl.ntx * pl.nty;
+    if (p.algo == LBM_LPTL) {
+        const int64_t t = (pl.N + kBatchTileNodes - 1) / kBatchTileNodes;
+        return (t + kBatchSuperHost - 1) / kBatchSuperHost;
+    }
+    const int64_t t = (int64_t)pl.ntx * pl.nty;
+    if (p.algo == LBM_NPTL) return (t + kBatchSuperHost - 1) / kBatchSuperHost;
+    return t;
 }
 
 lbm_status batch_layout(int32_t ncases, const lbm_params *params, BatchLayout *bl) {
@@ -90,6 +97,7 @@ struct lbm_batch {
     unsigned int *err;
     long long *tctr;
     int grid;
+    int kind;      // layout * 4 + algo shared by every case, -1 if mixed
     int cur;
     int64_t steps;
     cudaGraphExec_t graph[2];
@@ -176,7 +184,10 @@ extern "C" lbm_status lbm_batch_create(int32_t ncases, const lbm_params *params,
         lbm_batch_destroy(B);
         return lbm_cuda_fail(e, "batch upload");
     }
-    const int g = B->ops->batch_grid();
+    B->kind = params[0].layout * 4 + params[0].algo;
+    for (int c = 1; c < ncases; ++c)
+        if (params[c].layout * 4 + params[c].algo != B->kind) B->kind = -1;
+    const int g = B->ops->batch_grid(B->kind);
     B->grid = (int)std::max<int64_t>(1, std::min<int64_t>(g > 0 ? g : 152, B->bl.ntiles));
     *out = B;
     return LBM_OK;
@@ -196,7 +207,7 @@ extern "C" lbm_status lbm_batch_init(lbm_batch *B, int32_t c, const double *rho,
 static cudaError_t batch_block(lbm_batch *B, cudaStream_t st, int64_t count, int want_moments) {
     int cur = B->cur;
     for (int64_t k = 0; k < count; ++k) {
-        cudaError_t e = B->ops->batch_step(B->d_cases, B->d_tiles, B->bl.ntiles, B->grid, cur, (int)k,
+        cudaError_t e = B->ops->batch_step(B->kind, B->d_cases, B->d_tiles, B->bl.ntiles, B->grid, cur, (int)k,
                                            (want_moments && k == count - 1) ? 1 : 0, st);
         if (e != cudaSuccess) return e;
         cur ^= 1;
@@ -262,9 +273,9 @@ extern "C" lbm_status lbm_batch_read_populations(lbm_batch *B, int32_t c, void *
     return lbm_read_populations(B->cases[c], host, as);
 }
 
-extern "C" lbm_status lbm_batch_get_info(lbm_batch *B, int64_t *tiles, int32_t *grid, int64_t *cells) {
+extern "C" lbm_status lbm_batch_get_info(lbm_batch *B, int64_t *items, int32_t *grid, int64_t *cells) {
     if (!B) return lbm_fail(LBM_EINVAL, "batch is NULL");
-    if (tiles) *tiles = B->bl.ntiles;
+    if (items) *items = B->bl.ntiles;
     if (grid) *grid = B->grid;
     if (cells) {
         int64_t n = 0;

@@ -56,9 +56,10 @@ struct Ops {
     cudaError_t (*moments_f32)(const HostArgs &, float *r, float *u, float *v, cudaStream_t);
     int (*lptl_block)(int layout);  // occupancy-chosen LPTL block size
     // Batches: one persistent launch over the packed tile list.
-    cudaError_t (*batch_step)(const void *cases, const void *tiles, uint32_t ntiles, int grid, int cur,
-                              int toff, int want_moments, cudaStream_t);
-    int (*batch_grid)();                                   // resident blocks on the device
+    // kind = layout * 4 + algo shared by every case, or -1 for a mixed batch.
+    cudaError_t (*batch_step)(int kind, const void *cases, const void *tiles, uint32_t ntiles, int grid,
+                              int cur, int toff, int want_moments, cudaStream_t);
+    int (*batch_grid)(int kind);                           // resident blocks on the device
     void (*batch_case)(const HostArgs &, void *out);       // device record of one case
     size_t batch_case_bytes;
     size_t elem;               // bytes per stored population
@@ -83,6 +84,7 @@ cudaError_t launch_quantize(int storage, int rounding, uint64_t seed, int64_t t,
 
 constexpr int kReduceBlocks = 1024;
 constexpr int kReduceThreads = 256;
-constexpr int kBatchTileNodes = 256;  // threads per batch block = nodes per LPTL chunk
+constexpr int kBatchTileNodes = 256;  // threads per batch block = nodes per LPTL tile
+constexpr int kBatchSuperHost = 4;    // tiles per work item of a two-lattice case
 
 }  // namespace lbm

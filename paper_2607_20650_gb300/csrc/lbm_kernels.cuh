@@ -507,10 +507,12 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_nsol(const Step<S> a) {
 
 // ------------------------------------------------------------ batches
 // Many independent lattices advanced by one persistent launch per update.
-// The work list holds one entry per tile of every case (LPTL: 256
-// consecutive nodes); each block takes entries round-robin, stages the
-// case record in shared memory and runs the case's layout/algorithm body.
+// The work list holds one entry per work item of every case: four tiles of
+// a two-lattice case (LPTL tile = 256 consecutive nodes), one tile of a
+// one-lattice case. Blocks take entries round-robin; a block stages a case
+// record in shared memory only when the case changes.
 constexpr int kBatchThreads = 256;
+constexpr int kBatchSuper = 4;  // tiles per work item of a two-lattice case
 
 template <class S>
 struct BatchCase {
@@ -518,73 +520,96 @@ struct BatchCase {
     S *pop0, *pop1, *halo;      // pop1 == nullptr for one-lattice cases
     typename Codec<S>::C *mom;
     long long halo_parity_elems;
+    unsigned long long ntx_magic;  // ceil(2^64 / ntx), 0 when ntx == 1
     int layout, algo;
 };
 
 struct BatchTile {
     uint32_t c;                 // case index
-    uint32_t t;                 // tile index within the case (LPTL: chunk)
+    uint32_t t;                 // work item within the case
 };
 
 template <class S, int L>
-__device__ __forceinline__ void batch_tile(const Step<S> &a, int algo, uint32_t t, int tid,
+__device__ __forceinline__ void batch_item(const BatchCase<S> &bc, int algo, uint32_t t, int tid,
                                            unsigned char *smem) {
+    const Step<S> &a = bc.st;
     const int lane = tid & 31;
     if (algo == LPTL) {
-        const uint32_t n = t * (uint32_t)kBatchThreads + (uint32_t)tid;
-        if (n < a.N) {
-            const uint32_t y = a.nx_magic ? (uint32_t)__umul64hi((unsigned long long)n, a.nx_magic) : n;
-            two_lattice_node<S, L>(a, n - y * (uint32_t)a.geo.nx, y, lane);
+#pragma unroll 1
+        for (int k = 0; k < kBatchSuper; ++k) {
+            const uint32_t n = (t * kBatchSuper + k) * (uint32_t)kBatchThreads + (uint32_t)tid;
+            if (n < a.N) {
+                const uint32_t y = a.nx_magic ? (uint32_t)__umul64hi((unsigned long long)n, a.nx_magic) : n;
+                two_lattice_node<S, L>(a, n - y * (uint32_t)a.geo.nx, y, lane);
+            }
         }
         return;
     }
-    const int bx = (int)(t % (uint32_t)a.ntx), by = (int)(t / (uint32_t)a.ntx);
     const int lx = tid % a.tx, ly = tid / a.tx;
     if (algo == NPTL) {
-        const int x = bx * a.tx + lx, y = by * a.ty + ly;
-        if (ly < a.ty && x < a.geo.nx && y < a.geo.ny) two_lattice_node<S, L>(a, x, y, lane);
-    } else if (algo == NPOL) {
-        npol_tile<S, L>(a, bx, by, lx, ly, lane);
-    } else {
-        nsol_tile<S, L>(a, bx, by, lx, ly, lane, smem);
+        const uint32_t ntiles = (uint32_t)a.ntx * (uint32_t)((a.geo.ny + a.ty - 1) / a.ty);
+#pragma unroll 1
+        for (int k = 0; k < kBatchSuper; ++k) {
+            const uint32_t tt = t * kBatchSuper + k;
+            if (tt >= ntiles) break;
+            const uint32_t by = bc.ntx_magic ? (uint32_t)__umul64hi((unsigned long long)tt, bc.ntx_magic) : tt;
+            const uint32_t bx = tt - by * (uint32_t)a.ntx;
+            const int x = (int)bx * a.tx + lx, y = (int)by * a.ty + ly;
+            if (ly < a.ty && x < a.geo.nx && y < a.geo.ny) two_lattice_node<S, L>(a, x, y, lane);
+        }
+        return;
     }
+    const int by = (int)(t / (uint32_t)a.ntx), bx = (int)(t - (uint32_t)by * (uint32_t)a.ntx);
+    if (algo == NPOL)
+        npol_tile<S, L>(a, bx, by, lx, ly, lane);
+    else
+        nsol_tile<S, L>(a, bx, by, lx, ly, lane, smem);
 }
 
+// LK / AK: the layout / algorithm shared by every case, or -1 (any).
 // cur: source lattice of two-lattice cases, which equals the buffer-grid
 // parity read by one-lattice cases (all cases start together at update 0).
-template <class S>
-__global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchCase<S> *cases, const BatchTile *tiles,
-                                                          uint32_t ntiles, int cur, int toff, int want_moments) {
+template <class S, int LK, int AK>
+__global__ void __launch_bounds__(kBatchThreads, LK < 0 ? 2 : (AK <= NPTL ? 5 : 3))
+    k_batch(const BatchCase<S> *cases, const BatchTile *tiles, uint32_t ntiles, int cur, int toff,
+            int want_moments) {
     using C = typename Codec<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(16) BatchCase<S> bc;
     const int tid = threadIdx.x;
+    uint32_t have = 0xffffffffu;  // case staged in bc (same in every thread)
     for (uint32_t w = blockIdx.x; w < ntiles; w += gridDim.x) {
         const BatchTile bt = tiles[w];
-        const uint32_t *srcw = reinterpret_cast<const uint32_t *>(cases + bt.c);
-        uint32_t *dstw = reinterpret_cast<uint32_t *>(&bc);
-        for (int k = tid; k < (int)(sizeof(BatchCase<S>) / 4); k += kBatchThreads) dstw[k] = srcw[k];
-        __syncthreads();
-        if (tid == 0) {
-            if (bc.pop1) {
-                bc.st.src = cur ? bc.pop1 : bc.pop0;
-                bc.st.dst = cur ? bc.pop0 : bc.pop1;
-            } else {
-                bc.st.src = bc.pop0;
-                bc.st.dst = bc.pop0;
-                bc.st.halo_rd = bc.halo + (long long)cur * bc.halo_parity_elems;
-                bc.st.halo_wr = bc.halo + (long long)(cur ^ 1) * bc.halo_parity_elems;
+        if (bt.c != have) {
+            __syncthreads();  // every thread is done with the previous record
+            const uint32_t *srcw = reinterpret_cast<const uint32_t *>(cases + bt.c);
+            uint32_t *dstw = reinterpret_cast<uint32_t *>(&bc);
+            for (int k = tid; k < (int)(sizeof(BatchCase<S>) / 4); k += kBatchThreads) dstw[k] = srcw[k];
+            __syncthreads();
+            if (tid == 0) {
+                if (bc.pop1) {
+                    bc.st.src = cur ? bc.pop1 : bc.pop0;
+                    bc.st.dst = cur ? bc.pop0 : bc.pop1;
+                } else {
+                    bc.st.src = bc.pop0;
+                    bc.st.dst = bc.pop0;
+                    bc.st.halo_rd = bc.halo + (long long)cur * bc.halo_parity_elems;
+                    bc.st.halo_wr = bc.halo + (long long)(cur ^ 1) * bc.halo_parity_elems;
+                }
+                bc.st.mom = want_moments ? (C *)bc.mom : nullptr;
+                bc.st.toff = toff;
             }
-            bc.st.mom = want_moments ? (C *)bc.mom : nullptr;
-            bc.st.toff = toff;
+            __syncthreads();
+            have = bt.c;
         }
-        __syncthreads();
-        switch (bc.layout) {
-            case STREAM: batch_tile<S, STREAM>(bc.st, bc.algo, bt.t, tid, smem); break;
-            case BUNDLE: batch_tile<S, BUNDLE>(bc.st, bc.algo, bt.t, tid, smem); break;
-            default: batch_tile<S, COLLISION>(bc.st, bc.algo, bt.t, tid, smem); break;
+        const int algo = AK >= 0 ? AK : bc.algo;
+        const int layout = LK >= 0 ? LK : bc.layout;
+        switch (layout) {
+            case STREAM: batch_item<S, STREAM>(bc, algo, bt.t, tid, smem); break;
+            case BUNDLE: batch_item<S, BUNDLE>(bc, algo, bt.t, tid, smem); break;
+            default: batch_item<S, COLLISION>(bc, algo, bt.t, tid, smem); break;
         }
-        __syncthreads();
+        if (algo == NSOL) __syncthreads();  // shared-memory tile reused by the next item
     }
 }
 
@@ -593,25 +618,47 @@ size_t batch_smem_bytes() {
     return sizeof(typename Codec<S>::C) * 9 * kBatchThreads + kBatchThreads;
 }
 
-template <class S>
-cudaError_t op_batch_step(const void *cases, const void *tiles, uint32_t ntiles, int grid, int cur, int toff,
-                          int want_moments, cudaStream_t st) {
-    k_batch<S><<<grid, kBatchThreads, batch_smem_bytes<S>(), st>>>(
-        (const BatchCase<S> *)cases, (const BatchTile *)tiles, ntiles, cur, toff, want_moments);
-    return cudaGetLastError();
-}
+// kind = layout * 4 + algo when every case shares them, else -1.
+#define LBM_BATCH_KINDS(X, S)                                                              \
+    X(S, -1, -1) X(S, 0, 0) X(S, 0, 1) X(S, 0, 2) X(S, 0, 3) X(S, 1, 0) X(S, 1, 1) X(S, 1, 2) \
+        X(S, 1, 3) X(S, 2, 0) X(S, 2, 1) X(S, 2, 2) X(S, 2, 3)
 
 template <class S>
-int op_batch_grid() {
+cudaError_t op_batch_step(int kind, const void *cases, const void *tiles, uint32_t ntiles, int grid, int cur,
+                          int toff, int want_moments, cudaStream_t st) {
+    const size_t sm = batch_smem_bytes<S>();
+    const auto *c = (const BatchCase<S> *)cases;
+    const auto *t = (const BatchTile *)tiles;
+#define LBM_BATCH_LAUNCH(S_, L_, A_)                                                       \
+    if (kind == ((L_) < 0 ? -1 : (L_) * 4 + (A_))) {                                      \
+        k_batch<S_, L_, A_><<<grid, kBatchThreads, sm, st>>>(c, t, ntiles, cur, toff, want_moments); \
+        return cudaGetLastError();                                                          \
+    }
+    LBM_BATCH_KINDS(LBM_BATCH_LAUNCH, S)
+#undef LBM_BATCH_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+template <class S, int LK, int AK>
+int batch_grid_of() {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<S>, kBatchThreads,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<S, LK, AK>, kBatchThreads,
                                                       batch_smem_bytes<S>()) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+template <class S>
+int op_batch_grid(int kind) {
+#define LBM_BATCH_GRID(S_, L_, A_) \
+    if (kind == ((L_) < 0 ? -1 : (L_) * 4 + (A_))) return batch_grid_of<S_, L_, A_>();
+    LBM_BATCH_KINDS(LBM_BATCH_GRID, S)
+#undef LBM_BATCH_GRID
+    return 0;
 }
 
 // Host: the device record of one case (pointers from its HostArgs).
@@ -625,6 +672,7 @@ void op_batch_case(const HostArgs &h, void *out) {
     c.halo = (S *)h.halo;
     c.mom = (typename Codec<S>::C *)h.mom;
     c.halo_parity_elems = h.halo_parity_elems;
+    c.ntx_magic = h.ntx > 1 ? (~0ull / (unsigned long long)h.ntx) + 1ull : 0ull;
     c.layout = h.layout;
     c.algo = h.algo;
     memcpy(out, &c, sizeof(c));
