@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tile", default="")
     ap.add_argument("--layout", default="bundle", choices=["stream", "bundle", "collision"])
+    ap.add_argument("--algo", default="nptl", choices=["lptl", "nptl", "npol", "nsol"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s", "f64"])
     return ap.parse_args()
 
 
@@ -133,6 +135,12 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def kernel_name(args) -> str:
+    t = {"f32": "float", "f64": "double", "f16s": "__half", "bf16s": "__nv_bfloat16"}[args.storage]
+    k = {"lptl": "k_two_lattice", "nptl": "k_two_lattice", "npol": "k_npol", "nsol": "k_nsol"}[args.algo]
+    return f"{k}<{t}, {args.layout.upper()}, {args.algo.upper()}>"
 
 
 def launches_for(k: int, graph_block: int = 64) -> int:
@@ -235,8 +243,8 @@ def run_ours(args):
     nx, ny = args.nx, args.ny
     tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else (32, 4)
     mask = G.porous_discs(nx, ny, seed=3)
-    kw = dict(force=(1e-6, 0.0), bc=(lbm.PERIODIC,) * 4, layout=args.layout, algo="nptl",
-              storage="f32", tile=tile)
+    kw = dict(force=(1e-6, 0.0), bc=(lbm.PERIODIC,) * 4, layout=args.layout, algo=args.algo,
+              storage=args.storage, tile=tile)
     stream = torch.cuda.Stream()
     lat = lbm.Lattice(nx, ny, 0.9, mask, stream=stream, **kw)
     info = lat.info()
@@ -266,14 +274,17 @@ def run_ours(args):
     per_launch = dt / args.steps
     hbm, peak_kind = peaks()
     achieved = info["bytes_per_update"] / per_launch / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic() if (args.layout, args.algo, args.storage, nx, ny, tile) == \
+        ("bundle", "nptl", "f32", 16384, 8192, (32, 4)) else None
     result = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_launch * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "f64": "f64", "f16s": "f16 storage, f32 arithmetic",
+                  "bf16s": "bf16 storage, f32 arithmetic"}[args.storage],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "layout": args.layout, "algo": "nptl",
-                   "tile": f"{info['tile_x']}x{info['tile_y']}", "storage": "f32 shifted",
+        "config": {"workload": WORKLOAD, "layout": args.layout, "algo": args.algo,
+                   "tile": f"{info['tile_x']}x{info['tile_y']}", "storage": f"{args.storage} shifted",
                    "fluid_nodes": info["fluid_cells"], "nodes": cells,
                    "l2": "inputs larger than L2 (two 4.8 GB lattices)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -281,7 +292,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": info["bytes_per_update"],
-                     "kernel": f"k_two_lattice<float, {args.layout.upper()}, NPTL>"},
+                     "kernel": kernel_name(args)},
         "clocks": clocks,
         "mlups_fluid": info["fluid_cells"] * args.steps * world / dt / 1e6,
     }

@@ -6,7 +6,7 @@
  *   f_i(r + c_i, t + 1) = f_i(r, t) - (1/tau) [f_i(r, t) - f_i^eq(r, t)],
  * with the incompressible D2Q9I equilibrium of Eq. (2)
  *   f_i^eq = w_i [rho + 3 v.c_i + 9/2 (v.c_i)^2 - 3/2 v^2],  v = sum_i f_i c_i,
- * directions i = 0..8 = SW, S, SE, W, rest, E, NW, N, NE (Fig. 1), i.e.
+ * directions i = 0..8 = SW, S, SE, W, rest, E, NW, N, NE (Fig. 2), i.e.
  * c_i = (i%3 - 1, i/3 - 1), opposite(i) = 8 - i. Half-way bounce-back at
  * fluid-solid links; Sec. 3.1 boundary kinds plus the edge conditions below.
  *
@@ -48,7 +48,7 @@ typedef enum {
     LBM_EUNSUPPORTED = 6   /* valid but not implemented combination */
 } lbm_status;
 
-/* Population layouts of Sec. 3.2 / Fig. 1 (addresses in elements, N = nx*ny):
+/* Population layouts of Sec. 3.2 / Fig. 2 (addresses in elements, N = nx*ny):
  *   STREAM    (SoA)   addr(n, i) = i*N + n
  *   BUNDLE    (SoAoS) addr(n, i) = (i/3)*3N + 3n + i%3
  *               bundles {SW,S,SE}, {W,rest,E}, {NW,N,NE}

@@ -10,7 +10,7 @@
  *   Eq. (2)  f_i^eq = w_i [rho + 3 v.c_i + 9/2 (v.c_i)^2 - 3/2 v^2],
  *            v = sum_i f_i c_i   (D2Q9I: no division by rho),
  *            w_4 = 4/9, w_{1,3,5,7} = 1/9, w_{0,2,6,8} = 1/36.
- *   Directions (Fig. 1, the collision layout's order): i = 0..8 is
+ *   Directions (Fig. 2, the collision layout's order): i = 0..8 is
  *   SW, S, SE, W, rest, E, NW, N, NE, i.e. c_i = (i%3 - 1, i/3 - 1).
  *
  * Algorithm: the plain two-lattice one-step pull of Sec. 3.3 (every node pulls
@@ -59,7 +59,7 @@ typedef struct {
     int32_t bc_w, bc_e, bc_s, bc_n;
 } oracle_params;
 
-/* Fig. 1 direction order: c_i = (i%3 - 1, i/3 - 1). */
+/* Fig. 2 direction order: c_i = (i%3 - 1, i/3 - 1). */
 static const int CX[9] = {-1, 0, 1, -1, 0, 1, -1, 0, 1};
 static const int CY[9] = {-1, -1, -1, 0, 0, 0, 1, 1, 1};
 /* Eq. (2) weights. */

@@ -18,14 +18,14 @@ enum Pull : int { PULL_NODE = 0, PULL_BOUNCE = 1, PULL_UNKNOWN = 2 };
 // bounced back (source solid or a wall edge); 0xFF marks a solid node.
 constexpr uint8_t SOLID_LINKS = 0xFF;
 
-// Fig. 1 order: i = 0..8 = SW, S, SE, W, rest, E, NW, N, NE.
+// Fig. 2 order: i = 0..8 = SW, S, SE, W, rest, E, NW, N, NE.
 __host__ __device__ constexpr int cx(int i) { return i % 3 - 1; }
 __host__ __device__ constexpr int cy(int i) { return i / 3 - 1; }
 __host__ __device__ constexpr int opp(int i) { return 8 - i; }
 __host__ __device__ constexpr int mir_y(int i) { return (i % 3) + 3 * (2 - i / 3); }
 __host__ __device__ constexpr int link_bit(int i) { return i < 4 ? i : i - 1; }
 
-// Layouts of Fig. 1 (element offsets, N nodes).
+// Layouts of Fig. 2 (element offsets, N nodes).
 template <int L>
 __host__ __device__ __forceinline__ int64_t addr(int64_t N, int64_t n, int i) {
     if (L == STREAM) return (int64_t)i * N + n;
@@ -172,9 +172,11 @@ __host__ __device__ __forceinline__ int map_pull(const Geo &g, int x, int y, int
 // ------------------------------------------------------------ collision
 template <class C> struct Consts {
     C omega;              // 1/tau
+    C c1;                 // 1 - omega
     C hfx, hfy;           // F/2
     C fx, fy, sF, dF;     // F, fx+fy, fx-fy
     C w0, w1, w4;         // 1/36, 1/9, 4/9
+    C ow0, ow1, ow4;      // omega * w
     C kw0, kw1, kw4;      // (1 - omega/2) * w
     C zh5, zh8, zh2;      // Zou-He: 2/3 Ux, Ux/6 + Uy/2, Ux/6 - Uy/2
     C heq_in[9];          // equilibrium inlet populations
@@ -193,33 +195,36 @@ __device__ __forceinline__ void zou_he(const Consts<C> &k, C *g) {
 }
 
 // Moments, Eq. (2) equilibrium in deviation form and Eq. (1) BGK relaxation
-// with the Guo source, in a fixed operation order. g (pulled h values) is
-// replaced by the post-collision values.
+// with the Guo source, in one fixed operation order:
+//   P_i   = drho - 3/2 u^2 + cu_i (3 + 9/2 cu_i)          (h_i^eq = w_i P_i)
+//   h*_i  = (1 - omega) g_i + (omega w_i) P_i
+//           + (1 - omega/2) w_i [cF_i (3 + 9 cu_i) - 3 u.F]
+// with cu_i = c_i.u, cF_i = c_i.F. g (pulled h values) is replaced by h*.
 template <class C>
 __device__ __forceinline__ void collide(const Consts<C> &k, C *g, C &drho, C &ux, C &uy) {
     using A = Ar<C>;
-    drho = A::add(A::add(A::add(A::add(g[0], g[1]), A::add(g[2], g[3])),
-                         A::add(A::add(g[4], g[5]), A::add(g[6], g[7]))),
-                  g[8]);
-    C jx = A::add(A::add(A::sub(g[2], g[0]), A::sub(g[5], g[3])), A::sub(g[8], g[6]));
-    C jy = A::sub(A::add(A::add(g[6], g[7]), g[8]), A::add(A::add(g[0], g[1]), g[2]));
-    ux = A::add(jx, k.hfx);
-    uy = A::add(jy, k.hfy);
+    const C cw = A::add(A::add(g[0], g[3]), g[6]);   // c_x = -1 column
+    const C cm = A::add(A::add(g[1], g[4]), g[7]);   // c_x =  0
+    const C ce = A::add(A::add(g[2], g[5]), g[8]);   // c_x = +1
+    const C rs = A::add(A::add(g[0], g[1]), g[2]);   // c_y = -1 row
+    const C rn = A::add(A::add(g[6], g[7]), g[8]);   // c_y = +1
+    drho = A::add(A::add(cw, cm), ce);
+    ux = A::add(A::sub(ce, cw), k.hfx);
+    uy = A::add(A::sub(rn, rs), k.hfy);
     const C usq = A::fma(ux, ux, A::mul(uy, uy));
     const C base = A::fma(C(-1.5), usq, drho);
     const C s = A::add(ux, uy), d = A::sub(ux, uy);
     const C cu[9] = {-s, -uy, d, -ux, C(0), ux, -d, uy, s};
     const C cF[9] = {-k.sF, -k.fy, k.dF, -k.fx, C(0), k.fx, -k.dF, k.fy, k.sF};
-    const C uF = A::fma(ux, k.fx, A::mul(uy, k.fy));
+    const C m3uF = A::mul(C(-3), A::fma(ux, k.fx, A::mul(uy, k.fy)));
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const C w = i == 4 ? k.w4 : ((i & 1) ? k.w1 : k.w0);
-        const C heq = A::mul(w, A::fma(cu[i], A::fma(C(4.5), cu[i], C(3)), base));
-        C o = A::fma(k.omega, A::sub(heq, g[i]), g[i]);
+        const C ow = i == 4 ? k.ow4 : ((i & 1) ? k.ow1 : k.ow0);
+        const C P = A::fma(cu[i], A::fma(C(4.5), cu[i], C(3)), base);
+        C o = A::fma(ow, P, A::mul(k.c1, g[i]));
         if (k.force) {
             const C kw = i == 4 ? k.kw4 : ((i & 1) ? k.kw1 : k.kw0);
-            const C src = A::mul(kw, A::fma(A::mul(C(9), cu[i]), cF[i], A::mul(C(3), A::sub(cF[i], uF))));
-            o = A::add(o, src);
+            o = A::fma(kw, A::fma(cF[i], A::fma(C(9), cu[i], C(3)), m3uF), o);
         }
         g[i] = o;
     }

@@ -47,6 +47,10 @@ Step<S> make_step(const HostArgs &h, const StepCall &c) {
     a.N = (uint32_t)h.N;
     Consts<C> &k = a.k;
     k.omega = (C)h.omega;
+    k.c1 = (C)(1.0 - h.omega);
+    k.ow0 = (C)(h.omega / 36.0);
+    k.ow1 = (C)(h.omega / 9.0);
+    k.ow4 = (C)(4.0 * h.omega / 9.0);
     k.hfx = (C)(0.5 * h.fx);
     k.hfy = (C)(0.5 * h.fy);
     k.fx = (C)h.fx;
@@ -202,6 +206,41 @@ __device__ __forceinline__ void store_zero(S *dst, uint32_t N, uint32_t n, int o
     }
 }
 
+// Pulls of an interior node (requires 9N < 2^32): pointers to the node's
+// own record and to the rows above and below, plus per-direction constant
+// offsets (immediates for the bundle and collision layouts); each pull picks
+// the pulled neighbour or, for a bounced link, the node's opposite slot.
+template <class S, int L>
+__device__ __forceinline__ void pull_interior(const S *src, uint32_t n, uint32_t nx, uint32_t N, uint32_t lk,
+                                              typename Codec<S>::C *g) {
+    const S *own = src + lay_mul<L>() * n;
+    const S *rs = own + (ptrdiff_t)lay_mul<L>() * nx;  // row y+1: source of c_y = -1
+    const S *rn = own - (ptrdiff_t)lay_mul<L>() * nx;  // row y-1: source of c_y = +1
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (i == 4) {
+            g[i] = Codec<S>::dec(ld_src(own + (ptrdiff_t)lay_base<L>(N, 4)));
+            continue;
+        }
+        const S *row = cy(i) < 0 ? rs : (cy(i) > 0 ? rn : own);
+        const S *pp = row + ((ptrdiff_t)lay_base<L>(N, i) - (ptrdiff_t)lay_mul<L>() * cx(i));
+        const S *pb = own + (ptrdiff_t)lay_base<L>(N, opp(i));
+        g[i] = Codec<S>::dec(ld_src(((lk >> link_bit(i)) & 1u) ? pb : pp));
+    }
+}
+
+template <class S, int L>
+__device__ __forceinline__ void store_node(S *dst, uint32_t n, uint32_t N, int off32, const S *e) {
+    if (off32) {
+        S *od = dst + lay_mul<L>() * n;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st_dst<S, L>(od + (ptrdiff_t)lay_base<L>(N, i), e[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst[addr<L>(N, n, i)] = e[i];
+    }
+}
+
 // One node of the two-lattice pull update (LPTL and NPTL). Interior nodes
 // take a path with 32-bit element offsets where each pull is one select
 // between two uniform offsets (pulled neighbour or own opposite slot); nodes
@@ -226,19 +265,7 @@ __device__ __forceinline__ void two_lattice_node(const Step<S> &a, uint32_t x, u
     const bool interior = (x - 1u < nx - 2u) && (y - 1u < ny - 2u);
     C g[9];
     if (interior && a.off32) {
-        const uint32_t base = lay_mul<L>() * n;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            uint32_t e;
-            if (i == 4) {
-                e = base + lay_base<L>(a.N, 4);
-            } else {
-                const uint32_t kp = lay_base<L>(a.N, i) - lay_mul<L>() * (uint32_t)(cy(i) * (int)nx + cx(i));
-                const uint32_t kb = lay_base<L>(a.N, opp(i));
-                e = base + (((lk >> link_bit(i)) & 1u) ? kb : kp);
-            }
-            g[i] = Codec<S>::dec(ld_src(src + e));
-        }
+        pull_interior<S, L>(src, n, nx, a.N, lk, g);
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -261,14 +288,7 @@ __device__ __forceinline__ void two_lattice_node(const Step<S> &a, uint32_t x, u
     }
     S e[9];
     collide_encode(a, x, n, g, e);
-    if (a.off32) {
-        const uint32_t base = lay_mul<L>() * n;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) st_dst<S, L>(dst + base + lay_base<L>(a.N, i), e[i]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) dst[addr<L>(a.N, n, i)] = e[i];
-    }
+    store_node<S, L>(dst, n, a.N, a.off32, e);
 }
 
 // LPTL (LINEAR: one node per thread over n, block size from the runtime) and
@@ -356,7 +376,9 @@ __device__ __forceinline__ void npol_tile(const Step<S> &a, int bx, int by, int 
     const bool zero_fill = valid && !fluid && shares_sector<S, L>(F, lane);
     const bool inner = x > x0 && x < x1 && y > y0 && y < y1;
     C g[9];
-    if (fluid) {
+    if (fluid && inner && a.off32) {
+        pull_interior<S, L>(lat, n, (uint32_t)nx, a.N, lk, g);
+    } else if (fluid) {
         const bool dom_inner = x > 0 && x < nx - 1 && y > 0 && y < ny - 1;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -396,8 +418,7 @@ __device__ __forceinline__ void npol_tile(const Step<S> &a, int bx, int by, int 
     if (fluid) {
         S e[9];
         collide_encode(a, (uint32_t)x, n, g, e);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) lat[addr<L>(a.N, n, i)] = e[i];
+        store_node<S, L>(lat, n, a.N, a.off32, e);
         if (!inner) halo_publish(a.halo_wr, a.tx, a.ty, a.ntx, bx, by, x, y, x0, y0, x1, y1, e);
     } else if (zero_fill) {
         store_zero<S, L>(lat, a.N, n, a.off32);  // whole-sector writes, as in two_lattice_node

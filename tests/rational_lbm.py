@@ -8,7 +8,7 @@ obtains the Zou-He unknowns by solving their three defining conditions
 the normal population) instead of using closed formulas.
 
 Method: PortLBM Sec. 3.1, Eq. (1) (BGK), Eq. (2) (D2Q9I equilibrium,
-v = sum f c), directions of Fig. 1 (c_i = (i%3-1, i//3-1)), half-way
+v = sum f c), directions of Fig. 2 (c_i = (i%3-1, i//3-1)), half-way
 bounce-back; Guo body force with v = sum f c + F/2.
 """
 from fractions import Fraction as Fr

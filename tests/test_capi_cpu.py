@@ -1,6 +1,6 @@
 """CPU checks of the C ABI: the library loads, exports every function that
 include/*.h declares, and the host copy of each layout's index map is the
-bijection Fig. 1 (Sec. 3.2) draws. No compute call needs a GPU here."""
+bijection Fig. 2 (Sec. 3.2) draws. No compute call needs a GPU here."""
 import glob
 import os
 import re

@@ -38,7 +38,7 @@ def test_equilibrium_moments(drho, ux, uy):
 
 
 def test_weights_and_directions():
-    """Fig. 1 order: opposite(i) = 8 - i, rest at 4, weights of Eq. (2)."""
+    """Fig. 2 order: opposite(i) = 8 - i, rest at 4, weights of Eq. (2)."""
     assert (CX[::-1] == -CX).all() and (CY[::-1] == -CY).all()
     assert CX[4] == 0 and CY[4] == 0
     np.testing.assert_allclose(O.equilibrium(0.0, 0.0, 0.0), 0.0, atol=0)
