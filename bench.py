@@ -137,6 +137,16 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, device: str) -> float:
+    """Largest value over all ranks of the default process group (the timed
+    region's length: the job is as slow as its slowest replica)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def kernel_name(args) -> str:
     t = {"f32": "float", "f64": "double", "f16s": "__half", "bf16s": "__nv_bfloat16"}[args.storage]
     k = {"lptl": "k_two_lattice", "nptl": "k_two_lattice", "npol": "k_npol", "nsol": "k_nsol"}[args.algo]
@@ -266,9 +276,7 @@ def run_ours(args):
     clocks = clk.stop()
     barrier()
     if dist is not None:
-        t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+        dt = max_over_ranks(dt, "cuda")
     cells = nx * ny
     mlups = cells * args.steps * world / dt / 1e6
     per_launch = dt / args.steps
@@ -320,6 +328,8 @@ def variants(args, mask, torch, world):
     hbm, _ = peaks()
     for name, kw in [("f32_bundle_nptl_128x1_allfluid", dict(storage="f32", layout="bundle", tile=(128, 1),
                                                             geo="fluid")),
+                     ("f64_bundle_nptl_128x1_allfluid", dict(storage="f64", layout="bundle", tile=(128, 1),
+                                                             geo="fluid")),
                      ("f32_stream_nptl_32x4", dict(storage="f32", tile=(32, 4))),
                      ("f32_stream_lptl", dict(storage="f32", algo="lptl")),
                      ("f32_collision_nptl_64x4", dict(storage="f32", layout="collision", tile=(64, 4))),

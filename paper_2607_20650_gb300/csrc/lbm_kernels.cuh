@@ -343,12 +343,14 @@ __device__ __forceinline__ typename Codec<S>::C halo_read(const Step<S> &a, int 
 template <class S>
 __device__ __forceinline__ void halo_publish(S *hw, int tx, int ty, int ntx, int bx, int by, int x,
                                              int y, int x0, int y0, int x1, int y1, const S *e) {
+    S *t = hw + (int64_t)(by * ntx + bx) * (6 * (tx + ty));
+    const int r = y - y0, c = x - x0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        if (x == x1) hw[halo_slot(tx, ty, ntx, bx, by, EDGE_E, k, y - y0)] = e[3 * k + 2];
-        if (x == x0) hw[halo_slot(tx, ty, ntx, bx, by, EDGE_W, k, y - y0)] = e[3 * k];
-        if (y == y1) hw[halo_slot(tx, ty, ntx, bx, by, EDGE_N, k, x - x0)] = e[6 + k];
-        if (y == y0) hw[halo_slot(tx, ty, ntx, bx, by, EDGE_S, k, x - x0)] = e[k];
+        if (x == x1) t[k * ty + r] = e[3 * k + 2];                  // east:  2, 5, 8
+        if (x == x0) t[3 * ty + k * ty + r] = e[3 * k];             // west:  0, 3, 6
+        if (y == y1) t[6 * ty + k * tx + c] = e[6 + k];             // north: 6, 7, 8
+        if (y == y0) t[6 * ty + 3 * tx + k * tx + c] = e[k];        // south: 0, 1, 2
     }
 }
 
@@ -389,19 +391,21 @@ __device__ __forceinline__ void npol_tile(const Step<S> &a, int bx, int by, int 
             } else if (inner) {
                 g[i] = ldp<S, L>(lat, a.N, n - (uint32_t)(cy(i) * nx + cx(i)), i);
             } else if (dom_inner) {
-                // Tile edge inside the domain: the source is in this tile or
-                // in the adjacent tile's buffer grid, no edge mapping needed.
-                const int sx = x - cx(i), sy = y - cy(i);
-                const int dbx = sx < x0 ? -1 : (sx > x1 ? 1 : 0);
-                const int dby = sy < y0 ? -1 : (sy > y1 ? 1 : 0);
+                // Tile edge inside the domain: the source is in this tile or in
+                // the adjacent tile's buffer grid; the crossed edge follows from
+                // c_i and the node's place on the tile edge.
+                const int dbx = (cx(i) > 0 && x == x0) ? -1 : ((cx(i) < 0 && x == x1) ? 1 : 0);
+                const int dby = (cy(i) > 0 && y == y0) ? -1 : ((cy(i) < 0 && y == y1) ? 1 : 0);
                 if (dbx == 0 && dby == 0) {
                     g[i] = ldp<S, L>(lat, a.N, n - (uint32_t)(cy(i) * nx + cx(i)), i);
                 } else {
-                    const int nbx = bx + dbx, nby = by + dby;
-                    const int64_t sl = dbx != 0
-                        ? halo_slot(a.tx, a.ty, a.ntx, nbx, nby, cx(i) > 0 ? EDGE_E : EDGE_W, i / 3, sy - nby * a.ty)
-                        : halo_slot(a.tx, a.ty, a.ntx, nbx, nby, cy(i) > 0 ? EDGE_N : EDGE_S, i % 3, sx - nbx * a.tx);
-                    g[i] = Codec<S>::dec(a.halo_rd[sl]);
+                    const int64_t tb = (int64_t)((by + dby) * a.ntx + (bx + dbx)) * (6 * (a.tx + a.ty));
+                    int off;
+                    if (dbx != 0)  // east (c_x > 0) or west edge buffer, row of the source
+                        off = (cx(i) > 0 ? 0 : 3 * a.ty) + (i / 3) * a.ty + (ly - cy(i) - dby * a.ty);
+                    else           // north (c_y > 0) or south edge buffer, column of the source
+                        off = 6 * a.ty + (cy(i) > 0 ? 0 : 3 * a.tx) + (i % 3) * a.tx + (lx - cx(i));
+                    g[i] = Codec<S>::dec(a.halo_rd[tb + off]);
                 }
             } else {
                 int xs, ys, j;
@@ -471,7 +475,25 @@ __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int 
     // Substitutions for pulls the in-tile exchange does not cover.
     C fix[9];
     unsigned fixmask = 0;
-    if (fluid && !(x > x0 && x < x1 && y > y0 && y < y1)) {
+    const bool dom_inner = x > 0 && x < nx - 1 && y > 0 && y < ny - 1;
+    if (fluid && dom_inner && !(x > x0 && x < x1 && y > y0 && y < y1)) {
+        // Tile edge inside the domain: values from other tiles come from their
+        // buffer grid (same slots as NPOL); in-tile sources are exchanged.
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            fix[i] = C(0);
+            if (i == 4 || ((lk >> link_bit(i)) & 1u)) continue;
+            const int dbx = (cx(i) > 0 && x == x0) ? -1 : ((cx(i) < 0 && x == x1) ? 1 : 0);
+            const int dby = (cy(i) > 0 && y == y0) ? -1 : ((cy(i) < 0 && y == y1) ? 1 : 0);
+            if (dbx == 0 && dby == 0) continue;
+            const int64_t tb = (int64_t)((by + dby) * a.ntx + (bx + dbx)) * (6 * (a.tx + a.ty));
+            const int off = dbx != 0
+                ? (cx(i) > 0 ? 0 : 3 * a.ty) + (i / 3) * a.ty + (ly - cy(i) - dby * a.ty)
+                : 6 * a.ty + (cy(i) > 0 ? 0 : 3 * a.tx) + (i % 3) * a.tx + (lx - cx(i));
+            fixmask |= 1u << i;
+            fix[i] = Codec<S>::dec(a.halo_rd[tb + off]);
+        }
+    } else if (fluid && !(x > x0 && x < x1 && y > y0 && y < y1)) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             fix[i] = C(0);

@@ -1,0 +1,50 @@
+"""Host-side logic of bench.py on the CPU: the max-over-ranks reduction of
+the timed region on a world of two gloo ranks, and the launch accounting."""
+import os
+import socket
+
+import pytest
+
+import bench
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        q.put((rank, bench.max_over_ranks(0.5 + rank, "cpu")))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_world_2():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert all(p.exitcode == 0 for p in procs)
+    got = dict(q.get(timeout=5) for _ in range(2))
+    assert got == {0: 1.5, 1: 1.5}
+
+
+def test_launch_accounting_matches_graph_blocks():
+    # 64-update graphs end in one counter bump; the remainder is launched
+    # directly and followed by one bump.
+    assert bench.launches_for(64) == 65
+    assert bench.launches_for(65) == 65 + 2
+    assert bench.launches_for(1000) == 15 * 65 + 40 + 1

@@ -1,0 +1,114 @@
+"""Wing flow: NACA 2412 at 8 degrees, Zou-He inlet U = 0.05, Re = 1000,
+zero-gradient outflow, free-slip top and bottom. Lift and drag come from the
+FP64 momentum-exchange reduction: C_D = 2 F_x / (U^2 c), C_L = 2 F_y / (U^2 c)
+(rho_0 = 1, chord c).
+
+The FP64 reference is the coarsened copy (chord 512 on 4096 x 2048, same U and
+Re, 25,000 updates = the same convective time as 50,000 updates at chord
+1024). Its GPU FP64 run is first matched to the CPU oracle over 400 updates;
+then FP32 and FP16 shifted storage (stochastic rounding) are compared with it
+at the final update and as averages over the last 5,000 updates, and the
+full-size 8192 x 4096 case runs 50,000 updates in FP32 and FP16.
+
+Set LBM_TEST_RECORD=<file> to append the coefficients as JSON lines."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2607_20650_gb300 import build, geometry as G, lbm  # noqa: E402
+
+
+def record(**kw):
+    path = os.environ.get("LBM_TEST_RECORD")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(kw) + "\n")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    lbm.load()
+
+
+def _lattice(w, **kw):
+    lat = lbm.Lattice(w.nx, w.ny, w.tau, w.mask, u_in=(w.ux_in, 0.0), bc=(w.bc_w, w.bc_e, w.bc_s, w.bc_n),
+                      **kw)
+    lat.init(None, w.ux0, w.uy0)
+    return lat
+
+
+def _coefficients(F, w):
+    q = 0.5 * w.meta["U"] ** 2 * w.meta["L"]
+    return F[0] / q, F[1] / q          # C_D, C_L
+
+
+def _run(w, total, every, window, **kw):
+    """C_D, C_L at the end and averaged over the last `window` updates."""
+    lat = _lattice(w, **kw)
+    body = torch.from_numpy(w.body.reshape(-1).astype(np.uint8)).cuda()
+    samples = []
+    done = 0
+    while done < total:
+        k = min(every, total - done)
+        lat.step(k)
+        done += k
+        if done > total - window:
+            samples.append(_coefficients(lat.force(body), w))
+    lat.sync()
+    lat.close()
+    s = np.array(samples)
+    return s[-1], s.mean(axis=0)
+
+
+def test_wing_gpu_fp64_matches_oracle_on_coarse_copy():
+    w = G.wing(nx=4096, ny=2048, chord=512)
+    T = 400
+    lat = _lattice(w, layout="stream", algo="nptl", storage="f64")
+    lat.step(T, moments=True).sync()
+    body = torch.from_numpy(w.body.reshape(-1).astype(np.uint8)).cuda()
+    f_gpu = lat.force(body)
+    rho, ux, uy = lat.moments()
+    lat.close()
+    ref = O.Lattice(O.Case(w.nx, w.ny, w.tau, ux_in=w.ux_in, bc_w=w.bc_w, bc_e=w.bc_e, bc_s=w.bc_s,
+                           bc_n=w.bc_n), w.mask, ux=w.ux0, uy=w.uy0).run(T)
+    f_ref = ref.force(w.body)
+    fl = ref.solid == 0
+    e_u = float(np.max(np.abs(np.stack([ux, uy])[:, fl] - np.stack([ref.ux, ref.uy])[:, fl])) /
+                np.max(np.abs(ref.ux[fl])))
+    e_f = float(np.max(np.abs(f_gpu - f_ref)) / np.max(np.abs(f_ref)))
+    record(test="wing_fp64_vs_oracle", updates=T, err_u=e_u, err_force=e_f,
+           cd_cl_gpu=list(_coefficients(f_gpu, w)), cd_cl_oracle=list(_coefficients(f_ref, w)))
+    assert e_u <= 1e-11
+    assert e_f <= 1e-11
+
+
+def test_wing_lift_drag_precision():
+    coarse = G.wing(nx=4096, ny=2048, chord=512)
+    ref_end, ref_avg = _run(coarse, 25000, 250, 5000, layout="bundle", algo="nptl", storage="f64")
+    out = {"fp64_coarse": {"end": list(ref_end), "avg": list(ref_avg)}}
+    rel = {}
+    for name, kw in [("f32", dict(storage="f32")), ("f16s_sr", dict(storage="f16s", rounding="sr", seed=9))]:
+        end, avg = _run(coarse, 25000, 250, 5000, layout="bundle", algo="nptl", tile=(32, 4), **kw)
+        out[f"{name}_coarse"] = {"end": list(end), "avg": list(avg)}
+        rel[name] = {"end": list(np.abs(end - ref_end) / np.abs(ref_end)),
+                     "avg": list(np.abs(avg - ref_avg) / np.abs(ref_avg))}
+    fine = G.wing()
+    for name, kw in [("f32", dict(storage="f32")), ("f16s_sr", dict(storage="f16s", rounding="sr", seed=9))]:
+        end, avg = _run(fine, 50000, 500, 10000, layout="bundle", algo="nptl", tile=(32, 4), **kw)
+        out[f"{name}_fine"] = {"end": list(end), "avg": list(avg)}
+    record(test="wing_lift_drag", coefficients=out, rel_err_vs_fp64_coarse=rel)
+    assert max(rel["f32"]["end"] + rel["f32"]["avg"]) <= 1e-3
+    assert max(rel["f16s_sr"]["avg"]) <= 5e-2
+    for v in out.values():
+        assert np.isfinite(v["end"]).all() and np.isfinite(v["avg"]).all()
