@@ -65,8 +65,17 @@ typedef enum { LBM_LAYOUT_STREAM = 0, LBM_LAYOUT_BUNDLE = 1, LBM_LAYOUT_COLLISIO
  *   NSOL 2-D tiles, swap streaming (one lattice, populations stored in
  *        opposite slots), in-tile exchanges in shared memory, the same buffer
  *        grid across tiles.
- * All four produce bit-identical states at equal storage precision.          */
-typedef enum { LBM_LPTL = 0, LBM_NPTL = 1, LBM_NPOL = 2, LBM_NSOL = 3 } lbm_algo;
+ * All four produce bit-identical states at equal storage precision.
+ * Beyond the paper's four (Sec. 3.3 names it among state-of-the-art schemes,
+ * Sec. 6 as future work):
+ *   AA   in-place streaming with one lattice and no buffer grid (the AA
+ *        pattern): updates alternate between a phase that pulls from and
+ *        pushes to neighbours and a phase that only touches the node's own
+ *        slots. Same bits as the others. The state (lbm_read_populations,
+ *        lbm_write_populations, lbm_mass, lbm_force) is accessible after an
+ *        even number of updates only (LBM_EINVAL otherwise); zero-gradient
+ *        outflow is not supported (LBM_EUNSUPPORTED); not in batches.       */
+typedef enum { LBM_LPTL = 0, LBM_NPTL = 1, LBM_NPOL = 2, LBM_NSOL = 3, LBM_AA = 4 } lbm_algo;
 
 /* Storage precision of h; arithmetic is FP64 for F64 and FP32 otherwise. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_storage;

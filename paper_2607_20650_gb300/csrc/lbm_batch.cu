@@ -55,6 +55,8 @@ lbm_status batch_layout(int32_t ncases, const lbm_params *params, BatchLayout *b
     for (int c = 0; c < ncases; ++c) {
         const lbm_params &p = params[c];
         if (p.storage != storage) return lbm_fail(LBM_EINVAL, "batch: case %d has another storage type", c);
+        if (p.algo == LBM_AA)
+            return lbm_fail(LBM_EUNSUPPORTED, "batch: case %d uses the AA pattern (single lattices only)", c);
         if (p.layout == LBM_AUTO || p.algo == LBM_AUTO)
             return lbm_fail(LBM_EINVAL, "batch: case %d has an unresolved layout/algo (run lbm_batch_plan)", c);
         lbm_status s = lbm_plan(&p, &bl->plans[c]);

@@ -71,7 +71,7 @@ lbm_status lbm_check_params(const lbm_params *p) {
         !std::isfinite(p->u_in[1]))
         return lbm_fail(LBM_EINVAL, "force and u_in must be finite");
     if (p->layout < 0 || p->layout > 2) return lbm_fail(LBM_EINVAL, "bad layout %d", p->layout);
-    if (p->algo < 0 || p->algo > 3) return lbm_fail(LBM_EINVAL, "bad algo %d", p->algo);
+    if (p->algo < 0 || p->algo > 4) return lbm_fail(LBM_EINVAL, "bad algo %d", p->algo);
     if (p->storage < 0 || p->storage > 3) return lbm_fail(LBM_EINVAL, "bad storage %d", p->storage);
     if (p->rounding < 0 || p->rounding > 1) return lbm_fail(LBM_EINVAL, "bad rounding %d", p->rounding);
     const int s = p->bc_south, nn = p->bc_north, w = p->bc_west, e = p->bc_east;
@@ -87,6 +87,9 @@ lbm_status lbm_check_params(const lbm_params *p) {
         return lbm_fail(LBM_EINVAL, "west and east must both be PERIODIC or neither");
     if ((w == LBM_BC_INLET_ZOUHE || w == LBM_BC_INLET_EQ) && p->nx < 2)
         return lbm_fail(LBM_EINVAL, "an inlet needs nx >= 2");
+    if (p->algo == LBM_AA && (w == LBM_BC_OUTFLOW_ZG || e == LBM_BC_OUTFLOW_ZG))
+        return lbm_fail(LBM_EUNSUPPORTED,
+                        "AA pattern: zero-gradient outflow reads one slot from two nodes in place");
     return LBM_OK;
 }
 
@@ -125,7 +128,8 @@ lbm_status lbm_plan(const lbm_params *p, Plan *pl) {
     };
     pl->pop[0] = take(9 * (size_t)N * elem);
     pl->pop[1] = pl->two ? take(9 * (size_t)N * elem) : (size_t)-1;
-    if (!pl->two) {
+    pl->halo_grid = p->algo == LBM_NPOL || p->algo == LBM_NSOL;
+    if (pl->halo_grid) {
         pl->halo_parity_elems = (int64_t)pl->ntx * pl->nty * 6 * (tx + ty);
         pl->halo = take(2 * (size_t)pl->halo_parity_elems * elem);
     } else {
@@ -180,7 +184,7 @@ void lbm_fill_args(const lbm_params *p, const Plan &pl, char *ws, const Ops *ops
     h->links = (const uint8_t *)(ws + pl.links);
     h->pop[0] = ws + pl.pop[0];
     h->pop[1] = pl.two ? ws + pl.pop[1] : nullptr;
-    h->halo = pl.two ? nullptr : ws + pl.halo;
+    h->halo = pl.halo_grid ? ws + pl.halo : nullptr;
     h->halo_parity_elems = pl.halo_parity_elems;
     h->mom = ws + pl.mom;
     h->err = (unsigned int *)(ws + pl.misc);
@@ -276,7 +280,7 @@ extern "C" lbm_status lbm_init(lbm_lattice *L, const double *rho, const double *
     CK(cudaStreamSynchronize(st));
     CK(cudaMemsetAsync(L->h.pop[0], 0, popb, st));
     if (pl.two) CK(cudaMemsetAsync(L->h.pop[1], 0, popb, st));
-    if (!pl.two) CK(cudaMemsetAsync(L->h.halo, 0, 2 * (size_t)pl.halo_parity_elems * L->ops->elem, st));
+    if (pl.halo_grid) CK(cudaMemsetAsync(L->h.halo, 0, 2 * (size_t)pl.halo_parity_elems * L->ops->elem, st));
     CK(cudaMemsetAsync(L->ws + pl.misc, 0, 256, st));
     L->cur = 0;
     L->steps = 0;
@@ -294,7 +298,7 @@ extern "C" lbm_status lbm_init(lbm_lattice *L, const double *rho, const double *
         }
     }
     CK(L->ops->state_moments(L->h, 0, 0, st));
-    if (!pl.two) CK(L->ops->publish(L->h, 0, 0, st));
+    if (pl.halo_grid) CK(L->ops->publish(L->h, 0, 0, st));
     CK(cudaStreamSynchronize(st));
     return LBM_OK;
 }
@@ -425,8 +429,17 @@ extern "C" lbm_status lbm_moments_device(lbm_lattice *L, float *r, float *u, flo
     return LBM_OK;
 }
 
+// The AA pattern holds the canonical state (in opposite slots) only after an
+// even number of updates.
+static lbm_status aa_state_readable(lbm_lattice *L) {
+    if (L->p.algo == LBM_AA && (L->steps & 1))
+        return lbm_fail(LBM_EINVAL, "AA pattern: the state is readable after an even number of updates");
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm_mass(lbm_lattice *L, double *out) {
     if (!L || !out) return lbm_fail(LBM_EINVAL, "NULL argument");
+    if (aa_state_readable(L) != LBM_OK) return LBM_EINVAL;
     CK(L->ops->mass(L->h, L->cur, L->partials, kReduceBlocks, L->stream));
     CK(launch_sum_partials(L->partials, kReduceBlocks, 1, L->red_out, L->stream));
     CK(cudaMemcpyAsync(out, L->red_out, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
@@ -436,6 +449,7 @@ extern "C" lbm_status lbm_mass(lbm_lattice *L, double *out) {
 
 extern "C" lbm_status lbm_force(lbm_lattice *L, const uint8_t *d_body, double out[2]) {
     if (!L || !out) return lbm_fail(LBM_EINVAL, "NULL argument");
+    if (aa_state_readable(L) != LBM_OK) return LBM_EINVAL;
     CK(L->ops->force(L->h, L->cur, d_body, L->partials, kReduceBlocks, L->stream));
     CK(launch_sum_partials(L->partials, kReduceBlocks, 2, L->red_out, L->stream));
     CK(cudaMemcpyAsync(out, L->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
@@ -498,21 +512,24 @@ lbm_status lbm_pops_to_host(const unsigned char *raw, int storage, int layout, i
 
 extern "C" lbm_status lbm_read_populations(lbm_lattice *L, void *host, int32_t as) {
     if (!L || !host) return lbm_fail(LBM_EINVAL, "NULL argument");
+    if (aa_state_readable(L) != LBM_OK) return LBM_EINVAL;
     if (as != LBM_F64 && as != LBM_F32) return lbm_fail(LBM_EINVAL, "as must be LBM_F64 or LBM_F32");
     const int64_t N = L->pl.N;
     std::vector<unsigned char> raw(9 * (size_t)N * L->ops->elem);
     CK(cudaStreamSynchronize(L->stream));
     CK(cudaMemcpy(raw.data(), L->h.pop[L->cur], raw.size(), cudaMemcpyDeviceToHost));
-    lbm_pops_to_host(raw.data(), L->p.storage, L->p.layout, L->p.algo == LBM_NSOL, N, host, as);
+    lbm_pops_to_host(raw.data(), L->p.storage, L->p.layout, L->p.algo == LBM_NSOL || L->p.algo == LBM_AA, N,
+                     host, as);
     return check_err(L);
 }
 
 extern "C" lbm_status lbm_write_populations(lbm_lattice *L, const void *host, int32_t as) {
     if (!L || !host) return lbm_fail(LBM_EINVAL, "NULL argument");
+    if (aa_state_readable(L) != LBM_OK) return LBM_EINVAL;
     if (as != LBM_F64 && as != LBM_F32) return lbm_fail(LBM_EINVAL, "as must be LBM_F64 or LBM_F32");
     const int64_t N = L->pl.N;
     std::vector<unsigned char> raw(9 * (size_t)N * L->ops->elem);
-    const int rev = L->p.algo == LBM_NSOL;
+    const int rev = L->p.algo == LBM_NSOL || L->p.algo == LBM_AA;
     for (int i = 0; i < 9; ++i) {
         const int slot = rev ? 8 - i : i;
         for (int64_t n = 0; n < N; ++n) {
@@ -524,7 +541,7 @@ extern "C" lbm_status lbm_write_populations(lbm_lattice *L, const void *host, in
     CK(cudaStreamSynchronize(L->stream));
     CK(cudaMemcpy(L->h.pop[L->cur], raw.data(), raw.size(), cudaMemcpyHostToDevice));
     CK(L->ops->zero_solid(L->h, L->cur, L->stream));
-    if (!L->pl.two) CK(L->ops->publish(L->h, L->cur, (int)(L->steps & 1), L->stream));
+    if (L->pl.halo_grid) CK(L->ops->publish(L->h, L->cur, (int)(L->steps & 1), L->stream));
     CK(cudaStreamSynchronize(L->stream));
     return LBM_OK;
 }
@@ -539,7 +556,7 @@ extern "C" lbm_status lbm_get_info(lbm_lattice *L, lbm_info *out) {
     out->tile_y = L->p.algo == LBM_LPTL ? 1 : L->pl.ty;
     const double elem = (double)L->ops->elem;
     double bytes = (double)L->fluid * 18.0 * elem + (double)L->pl.N;  // 9 reads + 9 writes, link byte
-    if (!L->pl.two) bytes += 2.0 * (double)L->pl.halo_parity_elems * elem;  // buffer grid read + write
+    if (L->pl.halo_grid) bytes += 2.0 * (double)L->pl.halo_parity_elems * elem;  // buffer grid read + write
     out->bytes_per_update = bytes;
     out->workspace_bytes = L->pl.total;
     return LBM_OK;

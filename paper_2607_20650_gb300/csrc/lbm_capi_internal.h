@@ -14,6 +14,7 @@ constexpr int kMaxTileThreadsHost = 512;
 struct Plan {
     int64_t N = 0;
     int two = 1;                 // two-lattice algorithm
+    int halo_grid = 0;           // one-lattice algorithm with a buffer grid (NPOL, NSOL)
     int tx = 0, ty = 1, ntx = 0, nty = 0;
     size_t pop[2] = {0, 0};
     size_t halo = 0;

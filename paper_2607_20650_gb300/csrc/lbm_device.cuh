@@ -10,7 +10,7 @@
 namespace lbm {
 
 enum Layout : int { STREAM = 0, BUNDLE = 1, COLLISION = 2 };
-enum Algo : int { LPTL = 0, NPTL = 1, NPOL = 2, NSOL = 3 };
+enum Algo : int { LPTL = 0, NPTL = 1, NPOL = 2, NSOL = 3, AA = 4 };
 enum Bc : int { PERIODIC = 0, WALL = 1, FREESLIP = 2, INLET_ZOUHE = 3, INLET_EQ = 4, OUTFLOW_ZG = 5 };
 enum Pull : int { PULL_NODE = 0, PULL_BOUNCE = 1, PULL_UNKNOWN = 2 };
 

@@ -548,6 +548,148 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_nsol(const Step<S> a) {
                     (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u), smem_raw);
 }
 
+// ------------------------------------------------------------ AA pattern
+// In-place streaming with one lattice and no buffer grid (the AA pattern of
+// Bailey et al., which Sec. 3.3 names as a state-of-the-art scheme). Updates
+// alternate between two phases on the same array:
+//  phase 0 (state: post-collision values in opposite slots, slot 8-i of x
+//           holds S[x]_i): pull every value through the edge mapping,
+//           collide, and store each result in the slot its puller reads next,
+//           i.e. slot i of x + c_i (slot 8-i of x itself for a bounced link);
+//  phase 1 (state: every node's pulled values in its own slots): read them,
+//           collide, store the results in the node's opposite slots.
+// Each slot is read and written by the same node within a phase, so no
+// synchronisation is needed. Zero-gradient outflow reads one slot from two
+// nodes and is not supported here.
+template <class S, int L>
+__device__ __forceinline__ void aa_node(const Step<S> &a, uint32_t x, uint32_t y, int lane, int phase) {
+    using C = typename Codec<S>::C;
+    const uint32_t nx = (uint32_t)a.geo.nx, ny = (uint32_t)a.geo.ny;
+    const uint32_t n = y * nx + x;
+    const uint32_t lk = a.links[n];
+    S *lat = a.dst;
+    const bool fluid = lk != SOLID_LINKS;
+    const unsigned F = __ballot_sync(__activemask(), fluid);
+    if (!fluid) {
+        if (shares_sector<S, L>(F, lane)) store_zero<S, L>(lat, a.N, n, a.off32);
+        return;
+    }
+    C g[9];
+    S e[9];
+    if (phase == 1) {
+        if (a.off32) {
+            S *own = lat + lay_mul<L>() * n;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = Codec<S>::dec(own[(ptrdiff_t)lay_base<L>(a.N, i)]);
+            collide_encode(a, x, n, g, e);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) own[(ptrdiff_t)lay_base<L>(a.N, opp(i))] = e[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = ldp<S, L>(lat, a.N, n, i);
+            collide_encode(a, x, n, g, e);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) lat[addr<L>(a.N, n, opp(i))] = e[i];
+        }
+        return;
+    }
+    const bool interior = (x - 1u < nx - 2u) && (y - 1u < ny - 2u);
+    if (interior && a.off32) {
+        // Row pointers with constant offsets: pull slot 8-i of x - c_i (or
+        // own slot i when bounced), push to slot i of x + c_i (or own slot 8-i).
+        S *own = lat + lay_mul<L>() * n;
+        S *ra = own + (ptrdiff_t)lay_mul<L>() * nx;  // row y+1
+        S *rb = own - (ptrdiff_t)lay_mul<L>() * nx;  // row y-1
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (i == 4) {
+                g[i] = Codec<S>::dec(own[(ptrdiff_t)lay_base<L>(a.N, 4)]);
+                continue;
+            }
+            S *src_row = cy(i) < 0 ? ra : (cy(i) > 0 ? rb : own);
+            const S *pp = src_row + ((ptrdiff_t)lay_base<L>(a.N, opp(i)) - (ptrdiff_t)lay_mul<L>() * cx(i));
+            const S *pb = own + (ptrdiff_t)lay_base<L>(a.N, i);
+            g[i] = Codec<S>::dec(*(((lk >> link_bit(i)) & 1u) ? pb : pp));
+        }
+        collide_encode(a, x, n, g, e);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (i == 4) {
+                own[(ptrdiff_t)lay_base<L>(a.N, 4)] = e[4];
+                continue;
+            }
+            S *dst_row = cy(i) > 0 ? ra : (cy(i) < 0 ? rb : own);
+            S *pp = dst_row + ((ptrdiff_t)lay_base<L>(a.N, i) + (ptrdiff_t)lay_mul<L>() * cx(i));
+            S *pb = own + (ptrdiff_t)lay_base<L>(a.N, opp(i));
+            *(((lk >> link_bit(opp(i))) & 1u) ? pb : pp) = e[i];
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (i == 4) {
+            g[i] = ldp<S, L>(lat, a.N, n, 4);
+        } else if ((lk >> link_bit(i)) & 1u) {
+            g[i] = ldp<S, L>(lat, a.N, n, i);  // slot i of x holds S[x]_{8-i}
+        } else if (interior) {
+            g[i] = ldp<S, L>(lat, a.N, n - (uint32_t)(cy(i) * (int)nx + cx(i)), opp(i));
+        } else {
+            int xs, ys, j;
+            if (map_pull(a.geo, (int)x, (int)y, i, xs, ys, j) == PULL_NODE)
+                g[i] = ldp<S, L>(lat, a.N, (uint32_t)ys * nx + (uint32_t)xs, opp(j));
+            else
+                g[i] = C(0);  // inlet unknown
+        }
+    }
+    collide_encode(a, x, n, g, e);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (i == 4) {
+            lat[addr<L>(a.N, n, 4)] = e[4];
+        } else if ((lk >> link_bit(opp(i))) & 1u) {
+            lat[addr<L>(a.N, n, opp(i))] = e[i];  // bounced back into this node
+        } else if (interior) {
+            lat[addr<L>(a.N, n + (uint32_t)(cy(i) * (int)nx + cx(i)), i)] = e[i];
+        } else {
+            // Every fluid node (within one cell, across periodic edges) whose
+            // mapped pull reads S[x]_i receives it in the slot it pulls.
+#pragma unroll 1
+            for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll 1
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int ux = (int)x + dx, uy = (int)y + dy;
+                    if (ux < 0 || ux >= (int)nx) {
+                        if (a.geo.bw != PERIODIC) continue;
+                        ux = ux < 0 ? ux + (int)nx : ux - (int)nx;
+                    }
+                    if (uy < 0 || uy >= (int)ny) {
+                        if (a.geo.bs != PERIODIC) continue;
+                        uy = uy < 0 ? uy + (int)ny : uy - (int)ny;
+                    }
+                    const uint32_t m = (uint32_t)uy * nx + (uint32_t)ux;
+                    const uint32_t ml = a.links[m];
+                    if (ml == SOLID_LINKS) continue;
+#pragma unroll 1
+                    for (int k = 0; k < 9; ++k) {
+                        if (k == 4 || ((ml >> link_bit(k)) & 1u)) continue;
+                        int xs, ys, j;
+                        if (map_pull(a.geo, ux, uy, k, xs, ys, j) == PULL_NODE && xs == (int)x &&
+                            ys == (int)y && j == i)
+                            lat[addr<L>(a.N, m, k)] = e[i];
+                    }
+                }
+        }
+    }
+}
+
+template <class S, int L>
+__global__ void __launch_bounds__(kMaxTileThreads) k_aa(const Step<S> a, int phase) {
+    const uint32_t x = blockIdx.x * a.tx + threadIdx.x;
+    const uint32_t y = blockIdx.y * a.ty + threadIdx.y;
+    if (x >= (uint32_t)a.geo.nx || y >= (uint32_t)a.geo.ny) return;
+    aa_node<S, L>(a, x, y, (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u), phase);
+}
+
 // ------------------------------------------------------------ batches
 // Many independent lattices advanced by one persistent launch per update.
 // The work list holds one entry per work item of every case: four tiles of
@@ -885,7 +1027,7 @@ int lptl_block() {
 }
 
 template <class S, int L>
-cudaError_t step_layout(const HostArgs &h, const Step<S> &a, cudaStream_t st) {
+cudaError_t step_layout(const HostArgs &h, const Step<S> &a, int phase, cudaStream_t st) {
     using C = typename Codec<S>::C;
     const dim3 tile(h.tile_x, h.tile_y), grid(h.ntx, h.nty);
     switch (h.algo) {
@@ -902,6 +1044,7 @@ cudaError_t step_layout(const HostArgs &h, const Step<S> &a, cudaStream_t st) {
             k_nsol<S, L><<<grid, tile, sm, st>>>(a);
             break;
         }
+        case AA: k_aa<S, L><<<grid, tile, 0, st>>>(a, phase); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -911,9 +1054,9 @@ template <class S>
 cudaError_t op_step(const HostArgs &h, const StepCall &c, cudaStream_t st) {
     const Step<S> a = make_step<S>(h, c);
     switch (h.layout) {
-        case STREAM: return step_layout<S, STREAM>(h, a, st);
-        case BUNDLE: return step_layout<S, BUNDLE>(h, a, st);
-        case COLLISION: return step_layout<S, COLLISION>(h, a, st);
+        case STREAM: return step_layout<S, STREAM>(h, a, c.rd_parity, st);
+        case BUNDLE: return step_layout<S, BUNDLE>(h, a, c.rd_parity, st);
+        case COLLISION: return step_layout<S, COLLISION>(h, a, c.rd_parity, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -932,7 +1075,7 @@ cudaError_t op_init(const HostArgs &h, const double *rho, const double *ux, cons
     const Step<S> a = make_step<S>(h, StepCall{1, 0, 0, 0});  // dst = pop[0]
     if (count <= 0) return cudaSuccess;
     const unsigned g = (unsigned)((count + 255) / 256);
-    const int rev = h.algo == NSOL;
+    const int rev = h.algo == NSOL || h.algo == AA;
     LBM_LAYOUT_SWITCH(h, (k_init<S, L_><<<g, 256, 0, st>>>(a, rho, ux, uy, (uint32_t)n0,
                                                              (uint32_t)count, rev)));
     return cudaGetLastError();
@@ -942,7 +1085,7 @@ template <class S>
 cudaError_t op_publish(const HostArgs &h, int src, int parity, cudaStream_t st) {
     const Step<S> a = make_step<S>(h, StepCall{src, 0, 0, 0});
     S *hw = (S *)h.halo + (int64_t)parity * h.halo_parity_elems;
-    const int rev = h.algo == NSOL;
+    const int rev = h.algo == NSOL || h.algo == AA;
     const dim3 tile(h.tile_x, h.tile_y), grid(h.ntx, h.nty);
     LBM_LAYOUT_SWITCH(h, (k_publish<S, L_><<<grid, tile, 0, st>>>(a, hw, rev)));
     return cudaGetLastError();
@@ -961,7 +1104,7 @@ template <class S>
 cudaError_t op_state_moments(const HostArgs &h, int src, int post, cudaStream_t st) {
     Step<S> a = make_step<S>(h, StepCall{src, 0, 0, 1});
     const unsigned g = (unsigned)((h.N + 255) / 256);
-    const int rev = h.algo == NSOL;
+    const int rev = h.algo == NSOL || h.algo == AA;
     LBM_LAYOUT_SWITCH(h, (k_state_moments<S, L_><<<g, 256, 0, st>>>(a, rev, post)));
     return cudaGetLastError();
 }
@@ -969,7 +1112,7 @@ cudaError_t op_state_moments(const HostArgs &h, int src, int post, cudaStream_t 
 template <class S>
 cudaError_t op_mass(const HostArgs &h, int src, double *partials, int nblocks, cudaStream_t st) {
     const Step<S> a = make_step<S>(h, StepCall{src, 0, 0, 0});
-    const int rev = h.algo == NSOL;
+    const int rev = h.algo == NSOL || h.algo == AA;
     LBM_LAYOUT_SWITCH(h, (k_mass<S, L_><<<nblocks, kReduceThreads, 0, st>>>(a, rev, partials)));
     return cudaGetLastError();
 }
@@ -978,7 +1121,7 @@ template <class S>
 cudaError_t op_force(const HostArgs &h, int src, const uint8_t *body, double *partials, int nblocks,
                      cudaStream_t st) {
     const Step<S> a = make_step<S>(h, StepCall{src, 0, 0, 0});
-    const int rev = h.algo == NSOL;
+    const int rev = h.algo == NSOL || h.algo == AA;
     LBM_LAYOUT_SWITCH(h, (k_force<S, L_><<<nblocks, kReduceThreads, 0, st>>>(a, rev, body, partials)));
     return cudaGetLastError();
 }

@@ -17,7 +17,7 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ETIMEOUT, LBM_EUNSUPPORTED = range(7)
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EDIVERGED", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
 LAYOUTS = {"stream": 0, "bundle": 1, "collision": 2}
-ALGOS = {"lptl": 0, "nptl": 1, "npol": 2, "nsol": 3}
+ALGOS = {"lptl": 0, "nptl": 1, "npol": 2, "nsol": 3, "aa": 4}
 STORAGES = {"f64": 0, "f32": 1, "f16s": 2, "bf16s": 3}
 ROUNDINGS = {"rne": 0, "sr": 1}
 PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG = range(6)

@@ -82,3 +82,17 @@ def rel_linf(a, b, mask=None):
     if mask is not None:
         a, b = a[..., mask], b[..., mask]
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def aa_specs() -> dict[str, Spec]:
+    """Cases the AA pattern supports (every edge kind but zero-gradient
+    outflow): the periodic/wall/equilibrium-inlet specs above plus a Zou-He
+    channel closed by a wall at the east end, free-slip top and bottom."""
+    out = {k: v for k, v in specs().items() if G.OUTFLOW_ZG not in v.bc}
+    nx, ny = 53, 27
+    m = G.disc(nx, ny, 20.0, 13.0, 4.0)
+    r = G.SplitMix64(12, 9)
+    out["zouhe_wall"] = Spec("zouhe_wall", nx, ny, 0.7, m, (G.INLET_ZOUHE, G.WALL, G.FREESLIP, G.FREESLIP),
+                             u_in=(0.03, 0.002), ux0=np.where(m.ravel() > 0, 0.0, 0.03),
+                             uy0=np.where(m.ravel() > 0, 0.0, r.uniform(nx * ny, -1e-3, 1e-3)))
+    return out

@@ -120,3 +120,13 @@ def test_batch_rejects_unresolved_or_mixed(lib):
     d = lbm.make_params(64, 32, 0.8, algo="npol", tile=(32, 16))
     with pytest.raises(lbm.LbmError):
         lbm.lbm_batch_workspace_bytes([d])
+
+
+def test_aa_rejects_outflow_without_gpu(lib):
+    p = lbm.make_params(64, 32, 0.8, algo="aa", bc=(lbm.INLET_ZOUHE, lbm.OUTFLOW_ZG, lbm.WALL, lbm.WALL))
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_workspace_bytes(p)
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    one = lbm.lbm_workspace_bytes(lbm.make_params(100, 60, 0.8, algo="aa"))
+    two = lbm.lbm_workspace_bytes(lbm.make_params(100, 60, 0.8, algo="nptl"))
+    assert one < two - 9 * 100 * 60 * 4 + 4096          # one lattice, no buffer grid
