@@ -24,7 +24,7 @@ _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liblbm_oracle.so")
 
 # Edge conditions (same numbering as the C source).
-PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG = range(6)
+PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG, INLET_EQ_NEUMANN, OUTLET_PRESSURE = range(8)
 
 CX = np.array([-1, 0, 1, -1, 0, 1, -1, 0, 1])
 CY = np.array([-1, -1, -1, 0, 0, 0, 1, 1, 1])
@@ -37,6 +37,7 @@ class _Params(ctypes.Structure):
         ("ux_in", ctypes.c_double), ("uy_in", ctypes.c_double),
         ("bc_w", ctypes.c_int32), ("bc_e", ctypes.c_int32),
         ("bc_s", ctypes.c_int32), ("bc_n", ctypes.c_int32),
+        ("rho_out", ctypes.c_double),
     ]
 
 
@@ -101,10 +102,11 @@ class Case:
     bc_e: int = PERIODIC
     bc_s: int = PERIODIC
     bc_n: int = PERIODIC
+    rho_out: float = 1.0
 
     def _c(self):
         return _Params(self.nx, self.ny, self.tau, self.fx, self.fy, self.ux_in,
-                       self.uy_in, self.bc_w, self.bc_e, self.bc_s, self.bc_n)
+                       self.uy_in, self.bc_w, self.bc_e, self.bc_s, self.bc_n, self.rho_out)
 
 
 def omp_threads() -> int:

@@ -31,8 +31,10 @@
  *     (the population arriving from a solid node is the node's own opposite
  *     population). Domain edges are periodic, a half-way wall, specular
  *     free-slip (south/north), an incompressible Zou-He velocity inlet or an
- *     equilibrium (Dirichlet rho = 1) inlet (west), or a zero-gradient
- *     outflow (source column clamped into the domain).
+ *     equilibrium inlet with Dirichlet (rho = 1) or Neumann density (rho of
+ *     node (1, y) in the previous state) (west), a zero-gradient outflow
+ *     (source column clamped into the domain) or a Zou-He pressure outlet
+ *     (rho = rho_out, v_y = 0) (east).
  *   - A fluid node whose eight pull sources are all solid or wall exchanges
  *     nothing with the flow; it is treated as solid.
  *   - Solid nodes hold h = 0 and are never written; their moments are
@@ -48,7 +50,7 @@
 #endif
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_FREESLIP = 2, BC_INLET_ZOUHE = 3,
-       BC_INLET_EQ = 4, BC_OUTFLOW_ZG = 5 };
+       BC_INLET_EQ = 4, BC_OUTFLOW_ZG = 5, BC_INLET_EQ_NEUMANN = 6, BC_OUTLET_PRESSURE = 7 };
 enum { PULL_NODE = 0, PULL_BOUNCE = 1, PULL_UNKNOWN = 2 };
 
 typedef struct {
@@ -57,6 +59,7 @@ typedef struct {
     double fx, fy;         /* Guo body force */
     double ux_in, uy_in;   /* inlet velocity */
     int32_t bc_w, bc_e, bc_s, bc_n;
+    double rho_out;        /* outlet density for BC_OUTLET_PRESSURE */
 } oracle_params;
 
 /* Fig. 2 direction order: c_i = (i%3 - 1, i/3 - 1). */
@@ -113,7 +116,8 @@ static int pull_source(const oracle_params *p, int x, int y, int i,
             sx = (sx + p->nx) % p->nx;
         } else if (bc == BC_OUTFLOW_ZG) {
             sx = sx < 0 ? 0 : p->nx - 1;
-        } else if (bc == BC_INLET_ZOUHE || bc == BC_INLET_EQ) {
+        } else if (bc == BC_INLET_ZOUHE || bc == BC_INLET_EQ || bc == BC_INLET_EQ_NEUMANN ||
+                   bc == BC_OUTLET_PRESSURE) {
             return PULL_UNKNOWN;
         } else {
             return PULL_BOUNCE;
@@ -200,6 +204,25 @@ void oracle_step(const oracle_params *p, const uint8_t *solid, const double *h_i
             } else if (x == 0 && p->bc_w == BC_INLET_EQ) {
                 /* Equilibrium inlet with Dirichlet density rho = 1. */
                 oracle_equilibrium(0.0, p->ux_in, p->uy_in, g);
+            } else if (x == 0 && p->bc_w == BC_INLET_EQ_NEUMANN) {
+                /* Equilibrium inlet, zero density gradient: rho of node (1, y)
+                 * in the previous state (collision conserves mass, so the
+                 * post-collision sum is that node's density). */
+                double d = 0.0;
+                int64_t m = n + 1;
+                if (!solid[m])
+                    for (int i = 0; i < 9; ++i) d += h_in[(int64_t)i * N + m];
+                oracle_equilibrium(d, p->ux_in, p->uy_in, g);
+            }
+            if (x == nx - 1 && p->bc_e == BC_OUTLET_PRESSURE) {
+                /* Zou-He pressure outlet: rho = rho_out and v_y = 0 fix the
+                 * three populations entering from the east together with
+                 * bounce-back of the normal non-equilibrium part. */
+                double dr = p->rho_out - 1.0;
+                double ux = 2.0 * (g[2] + g[5] + g[8]) + (g[1] + g[4] + g[7]) - dr;
+                g[3] = g[5] - (2.0 / 3.0) * ux;
+                g[6] = g[2] + 0.5 * (g[1] - g[7]) - ux / 6.0;
+                g[0] = g[8] + 0.5 * (g[7] - g[1]) - ux / 6.0;
             }
             double drho = 0.0, jx = 0.0, jy = 0.0;
             for (int i = 0; i < 9; ++i) {

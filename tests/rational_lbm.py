@@ -15,7 +15,7 @@ from fractions import Fraction as Fr
 
 W = [Fr(1, 36), Fr(1, 9), Fr(1, 36), Fr(1, 9), Fr(4, 9), Fr(1, 9), Fr(1, 36), Fr(1, 9), Fr(1, 36)]
 C = [(i % 3 - 1, i // 3 - 1) for i in range(9)]
-PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG = range(6)
+PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG, INLET_EQ_NEUMANN, OUTLET_PRESSURE = range(8)
 
 
 def feq(rho, ux, uy):
@@ -31,13 +31,14 @@ def index_of(cx, cy):
 
 
 class RationalLBM:
-    def __init__(self, nx, ny, tau, solid, bc, force=(0, 0), u_in=(0, 0), rho0=None, u0=None):
+    def __init__(self, nx, ny, tau, solid, bc, force=(0, 0), u_in=(0, 0), rho0=None, u0=None, rho_out=1):
         self.nx, self.ny = nx, ny
         self.omega = 1 / Fr(tau)
         self.solid = solid  # set of (x, y)
         self.bc = bc        # dict: 'w','e','s','n' -> code
         self.F = (Fr(force[0]), Fr(force[1]))
         self.U = (Fr(u_in[0]), Fr(u_in[1]))
+        self.rho_out = Fr(rho_out)
         self.f = {}
         for y in range(ny):
             for x in range(nx):
@@ -68,7 +69,7 @@ class RationalLBM:
                 sx %= self.nx
             elif kind == OUTFLOW_ZG:
                 sx = min(max(sx, 0), self.nx - 1)
-            elif kind in (INLET_ZOUHE, INLET_EQ):
+            elif kind in (INLET_ZOUHE, INLET_EQ, INLET_EQ_NEUMANN, OUTLET_PRESSURE):
                 return None
             else:
                 return self.f[(x, y)][index_of(-cx, -cy)]
@@ -96,6 +97,20 @@ class RationalLBM:
                 g[2], g[5], g[8] = (s - dlt) / 2, b, (s + dlt) / 2
             elif x == 0 and self.bc['w'] == INLET_EQ:
                 g = feq(Fr(1), *self.U)
+            elif x == 0 and self.bc['w'] == INLET_EQ_NEUMANN:
+                # density of the east neighbour in the previous state
+                r_in = Fr(1) if (1, y) in self.solid else sum(self.f[(1, y)])
+                g = feq(r_in, *self.U)
+            if x == self.nx - 1 and self.bc['e'] == OUTLET_PRESSURE:
+                # unknowns a=g0, b=g3, c=g6 from: sum g = rho_out, sum g c_y = 0,
+                # b - b_eq = g5 - g5_eq (rho cancels; the equilibria differ by
+                # w 6 u_x with u_x = sum g c_x).
+                K = g[1] + g[2] + g[4] + g[5] + g[7] + g[8]
+                ux = (g[2] + g[5] + g[8]) - (self.rho_out - K)
+                b = g[5] - (W[5] * 3 * ux - W[3] * 3 * (-ux))
+                s_ac = self.rho_out - K - b
+                d_ca = g[1] + g[2] - g[7] - g[8]
+                g[0], g[3], g[6] = (s_ac - d_ca) / 2, b, (s_ac + d_ca) / 2
             rho = sum(g)
             ux = sum(gi * c[0] for gi, c in zip(g, C)) + Fx / 2
             uy = sum(gi * c[1] for gi, c in zip(g, C)) + Fy / 2

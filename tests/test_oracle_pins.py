@@ -250,15 +250,15 @@ def test_force_balance_steady_poiseuille():
 
 # ---------------------------------------------------------------- brute force
 
-def _compare_rational(nx, ny, tau, solid, bc, force=(0, 0), u_in=(0, 0), u0=None, steps=3):
+def _compare_rational(nx, ny, tau, solid, bc, force=(0, 0), u_in=(0, 0), u0=None, steps=3, rho_out=1):
     from fractions import Fraction as Fr
-    r = RationalLBM(nx, ny, Fr(tau), solid, bc, force=force, u_in=u_in, u0=u0)
+    r = RationalLBM(nx, ny, Fr(tau), solid, bc, force=force, u_in=u_in, u0=u0, rho_out=rho_out)
     mask = np.zeros((ny, nx), np.uint8)
     for (x, y) in solid:
         mask[y, x] = 1
     case = O.Case(nx, ny, float(Fr(tau)), fx=float(force[0]), fy=float(force[1]),
                   ux_in=float(u_in[0]), uy_in=float(u_in[1]),
-                  bc_w=bc['w'], bc_e=bc['e'], bc_s=bc['s'], bc_n=bc['n'])
+                  bc_w=bc['w'], bc_e=bc['e'], bc_s=bc['s'], bc_n=bc['n'], rho_out=float(Fr(rho_out)))
     ux0 = uy0 = None
     if u0 is not None:
         ux0 = np.array([float(u0[(n % nx, n // nx)][0]) for n in range(nx * ny)])
@@ -309,3 +309,41 @@ def test_bruteforce_fully_periodic_obstacles():
     _compare_rational(nx, ny, Fr(11, 20), {(0, 0), (3, 2), (4, 2)},
                       {'w': O.PERIODIC, 'e': O.PERIODIC, 's': O.PERIODIC, 'n': O.PERIODIC},
                       force=(Fr(1, 500), Fr(1, 700)), u0=u0)
+
+
+def test_bruteforce_neumann_inlet_pressure_outlet():
+    from fractions import Fraction as Fr
+    nx, ny = 6, 4
+    u0 = {(x, y): (Fr(1, 40) + Fr(x, 300), Fr(y - 2, 500)) for x in range(nx) for y in range(ny)}
+    _compare_rational(nx, ny, Fr(3, 4), {(3, 2)},
+                      {'w': O.INLET_EQ_NEUMANN, 'e': O.OUTLET_PRESSURE, 's': O.FREESLIP, 'n': O.WALL},
+                      u_in=(Fr(1, 25), Fr(1, 200)), u0=u0, rho_out=Fr(999, 1000))
+
+
+def test_pressure_outlet_prescribes_density_and_normal_flow():
+    """After the Zou-He pressure reconstruction sum_i g_i = rho_out and
+    sum_i g_i c_y = 0 exactly (F = 0)."""
+    nx, ny = 9, 7
+    rng = np.random.default_rng(6)
+    case = O.Case(nx, ny, 0.7, ux_in=0.04, bc_w=O.INLET_ZOUHE, bc_e=O.OUTLET_PRESSURE,
+                  bc_s=O.WALL, bc_n=O.FREESLIP, rho_out=1.002)
+    lat = O.Lattice(case, ux=0.03 + 0.01 * rng.random(nx * ny), uy=0.005 * rng.random(nx * ny))
+    lat.run(4)
+    col = lambda a: lat.field(a)[:, -1]
+    np.testing.assert_allclose(col(lat.rho), 1.002, rtol=0, atol=4e-16)
+    np.testing.assert_allclose(col(lat.uy), 0.0, rtol=0, atol=4e-17)
+
+
+def test_neumann_inlet_takes_previous_neighbour_density():
+    """The equilibrium inlet's density at update k is the density of node
+    (1, y) in the state after update k - 1 (and Eq. 2 reproduces it)."""
+    nx, ny = 8, 5
+    rng = np.random.default_rng(7)
+    case = O.Case(nx, ny, 0.8, ux_in=0.05, bc_w=O.INLET_EQ_NEUMANN, bc_e=O.OUTLET_PRESSURE,
+                  bc_s=O.FREESLIP, bc_n=O.FREESLIP)
+    lat = O.Lattice(case, rho=1 + 1e-3 * rng.random(nx * ny), ux=np.full(nx * ny, 0.05))
+    lat.run(3)
+    prev = 1.0 + lat.h.reshape(9, ny, nx)[:, :, 1].sum(axis=0)
+    lat.run(1)
+    np.testing.assert_allclose(lat.field(lat.rho)[:, 0], prev, rtol=0, atol=4e-16)
+    np.testing.assert_allclose(lat.field(lat.ux)[:, 0], 0.05, rtol=0, atol=2e-17)
