@@ -86,17 +86,23 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_stora
 typedef enum { LBM_ROUND_RNE = 0, LBM_ROUND_SR = 1 } lbm_rounding;
 
 /* Edge conditions. SOUTH/NORTH: PERIODIC (both), WALL, FREESLIP.
- * WEST: PERIODIC (with EAST), WALL, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG.
- * EAST: PERIODIC (with WEST), WALL, OUTFLOW_ZG.
+ * WEST: PERIODIC (with EAST), WALL, INLET_ZOUHE, INLET_EQ, INLET_EQ_NEUMANN, OUTFLOW_ZG.
+ * EAST: PERIODIC (with WEST), WALL, OUTFLOW_ZG, OUTLET_PRESSURE.
  *   WALL        half-way bounce-back one half cell outside the edge
  *   FREESLIP    specular reflection: the value pulled across the edge is the
  *               neighbour row's mirror population of the node's own row
  *   INLET_ZOUHE incompressible Zou-He velocity inlet (u_in) in column 0
  *   INLET_EQ    column 0 set to f^eq(rho = 1, u_in) (Sec. 3.1 Dirichlet)
- *   OUTFLOW_ZG  zero gradient: the pulled source column is clamped         */
+ *   OUTFLOW_ZG  zero gradient: the pulled source column is clamped
+ *   INLET_EQ_NEUMANN  column 0 set to f^eq(rho of node (1, y) in the previous
+ *               state, u_in): Sec. 3.1's equilibrium inlet with a Neumann
+ *               density (one-lattice algorithms need tile_x >= 2; not AA)
+ *   OUTLET_PRESSURE  Zou-He pressure outlet in column nx-1 (Sec. 3.1's
+ *               "adapted Zou and He" outlet): rho = rho_out, v_y = 0       */
 typedef enum {
     LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_FREESLIP = 2,
-    LBM_BC_INLET_ZOUHE = 3, LBM_BC_INLET_EQ = 4, LBM_BC_OUTFLOW_ZG = 5
+    LBM_BC_INLET_ZOUHE = 3, LBM_BC_INLET_EQ = 4, LBM_BC_OUTFLOW_ZG = 5,
+    LBM_BC_INLET_EQ_NEUMANN = 6, LBM_BC_OUTLET_PRESSURE = 7
 } lbm_bc;
 
 #define LBM_FLAG_NO_GRAPH 0x1u   /* lbm_step launches kernels one by one */
@@ -115,6 +121,7 @@ typedef struct lbm_params {
     int32_t tile_x, tile_y;  /* NPTL/NPOL/NSOL tile (0, 0 = 32 x 8); tile_x*tile_y <= 512;
                                 tile_x a multiple of 32 keeps warps on one row */
     uint32_t flags;          /* LBM_FLAG_* */
+    double rho_out;          /* outlet density for OUTLET_PRESSURE (> 0) */
 } lbm_params;
 
 typedef struct lbm_lattice lbm_lattice;

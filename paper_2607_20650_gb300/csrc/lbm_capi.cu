@@ -79,14 +79,20 @@ lbm_status lbm_check_params(const lbm_params *p) {
     if (!ok_sn(s) || !ok_sn(nn)) return lbm_fail(LBM_EINVAL, "south/north must be PERIODIC, WALL or FREESLIP");
     if ((s == LBM_BC_PERIODIC) != (nn == LBM_BC_PERIODIC))
         return lbm_fail(LBM_EINVAL, "south and north must both be PERIODIC or neither");
-    if (!(w >= 0 && w <= 5 && w != LBM_BC_FREESLIP))
-        return lbm_fail(LBM_EINVAL, "west must be PERIODIC, WALL, INLET_ZOUHE, INLET_EQ or OUTFLOW_ZG");
-    if (!(e == LBM_BC_PERIODIC || e == LBM_BC_WALL || e == LBM_BC_OUTFLOW_ZG))
-        return lbm_fail(LBM_EINVAL, "east must be PERIODIC, WALL or OUTFLOW_ZG");
+    if (!(w >= 0 && w <= 6 && w != LBM_BC_FREESLIP))
+        return lbm_fail(LBM_EINVAL,
+                        "west must be PERIODIC, WALL, INLET_ZOUHE, INLET_EQ, INLET_EQ_NEUMANN or OUTFLOW_ZG");
+    if (!(e == LBM_BC_PERIODIC || e == LBM_BC_WALL || e == LBM_BC_OUTFLOW_ZG || e == LBM_BC_OUTLET_PRESSURE))
+        return lbm_fail(LBM_EINVAL, "east must be PERIODIC, WALL, OUTFLOW_ZG or OUTLET_PRESSURE");
+    if (e == LBM_BC_OUTLET_PRESSURE && !(std::isfinite(p->rho_out) && p->rho_out > 0))
+        return lbm_fail(LBM_EINVAL, "rho_out must be finite and > 0 (got %g)", p->rho_out);
+    if (w == LBM_BC_INLET_EQ_NEUMANN && p->algo == LBM_AA)
+        return lbm_fail(LBM_EUNSUPPORTED, "AA pattern: the Neumann inlet reads a neighbour that is updated in place");
     if ((w == LBM_BC_PERIODIC) != (e == LBM_BC_PERIODIC))
         return lbm_fail(LBM_EINVAL, "west and east must both be PERIODIC or neither");
-    if ((w == LBM_BC_INLET_ZOUHE || w == LBM_BC_INLET_EQ) && p->nx < 2)
-        return lbm_fail(LBM_EINVAL, "an inlet needs nx >= 2");
+    if ((w == LBM_BC_INLET_ZOUHE || w == LBM_BC_INLET_EQ || w == LBM_BC_INLET_EQ_NEUMANN ||
+         e == LBM_BC_OUTLET_PRESSURE) && p->nx < 2)
+        return lbm_fail(LBM_EINVAL, "an inlet or pressure outlet needs nx >= 2");
     if (p->algo == LBM_AA && (w == LBM_BC_OUTFLOW_ZG || e == LBM_BC_OUTFLOW_ZG))
         return lbm_fail(LBM_EUNSUPPORTED,
                         "AA pattern: zero-gradient outflow reads one slot from two nodes in place");
@@ -113,6 +119,8 @@ lbm_status lbm_plan(const lbm_params *p, Plan *pl) {
         if (tx < 1 || ty < 1 || (int64_t)tx * ty > kMaxTileThreadsHost)
             return lbm_fail(LBM_EINVAL, "tile %dx%d: need tile_x, tile_y >= 1, tile_x*tile_y <= %d", tx, ty,
                             kMaxTileThreadsHost);
+        if (p->bc_west == LBM_BC_INLET_EQ_NEUMANN && (p->algo == LBM_NPOL || p->algo == LBM_NSOL) && tx < 2)
+            return lbm_fail(LBM_EINVAL, "the Neumann inlet needs tile_x >= 2 for one-lattice algorithms");
         pl->ntx = (p->nx + tx - 1) / tx;
         pl->nty = (p->ny + ty - 1) / ty;
         if (pl->nty > 65535) return lbm_fail(LBM_EUNSUPPORTED, "too many tile rows (%d)", pl->nty);
@@ -174,6 +182,7 @@ void lbm_fill_args(const lbm_params *p, const Plan &pl, char *ws, const Ops *ops
     h->fy = p->force[1];
     h->ux_in = p->u_in[0];
     h->uy_in = p->u_in[1];
+    h->rho_out = p->bc_east == LBM_BC_OUTLET_PRESSURE ? p->rho_out : 1.0;
     h->seed = p->seed;
     h->tile_x = pl.tx;
     h->tile_y = pl.ty;

@@ -11,7 +11,10 @@ namespace lbm {
 
 enum Layout : int { STREAM = 0, BUNDLE = 1, COLLISION = 2 };
 enum Algo : int { LPTL = 0, NPTL = 1, NPOL = 2, NSOL = 3, AA = 4 };
-enum Bc : int { PERIODIC = 0, WALL = 1, FREESLIP = 2, INLET_ZOUHE = 3, INLET_EQ = 4, OUTFLOW_ZG = 5 };
+enum Bc : int {
+    PERIODIC = 0, WALL = 1, FREESLIP = 2, INLET_ZOUHE = 3, INLET_EQ = 4, OUTFLOW_ZG = 5,
+    INLET_EQ_NEUMANN = 6, OUTLET_PRESSURE = 7
+};
 enum Pull : int { PULL_NODE = 0, PULL_BOUNCE = 1, PULL_UNKNOWN = 2 };
 
 // Per-node link byte: bit b(i) set when the value pulled in direction i is
@@ -157,7 +160,7 @@ __host__ __device__ __forceinline__ int map_pull(const Geo &g, int x, int y, int
             sx = sx < 0 ? sx + g.nx : sx - g.nx;
         } else if (bc == OUTFLOW_ZG) {
             sx = sx < 0 ? 0 : g.nx - 1;
-        } else if (bc == INLET_ZOUHE || bc == INLET_EQ) {
+        } else if (bc == INLET_ZOUHE || bc == INLET_EQ || bc == INLET_EQ_NEUMANN || bc == OUTLET_PRESSURE) {
             return PULL_UNKNOWN;
         } else {
             return PULL_BOUNCE;
@@ -179,6 +182,7 @@ template <class C> struct Consts {
     C ow0, ow1, ow4;      // omega * w
     C kw0, kw1, kw4;      // (1 - omega/2) * w
     C zh5, zh8, zh2;      // Zou-He: 2/3 Ux, Ux/6 + Uy/2, Ux/6 - Uy/2
+    C drho_out;           // pressure outlet: rho_out - 1
     C heq_in[9];          // equilibrium inlet populations
     int force;            // F != 0
 };
@@ -192,6 +196,19 @@ __device__ __forceinline__ void zou_he(const Consts<C> &k, C *g) {
     g[5] = A::add(g[3], k.zh5);
     g[8] = A::fma(C(0.5), A::sub(g1, g7), A::add(g[0], k.zh8));
     g[2] = A::fma(C(0.5), A::sub(g7, g1), A::add(g[6], k.zh2));
+}
+
+// Zou-He pressure outlet: rho = rho_out and v_y = 0, with bounce-back of the
+// normal non-equilibrium part, fix the three populations entering from the east.
+template <class C>
+__device__ __forceinline__ void zou_he_pressure(const Consts<C> &k, C *g) {
+    using A = Ar<C>;
+    const C g1 = g[1], g7 = g[7];
+    const C ux = A::sub(A::fma(C(2), A::add(A::add(g[2], g[5]), g[8]), A::add(A::add(g1, g[4]), g7)), k.drho_out);
+    const C u6 = A::mul(ux, C(1.0 / 6.0));
+    g[3] = A::fma(C(-2.0 / 3.0), ux, g[5]);
+    g[6] = A::sub(A::fma(C(0.5), A::sub(g1, g7), g[2]), u6);
+    g[0] = A::sub(A::fma(C(0.5), A::sub(g7, g1), g[8]), u6);
 }
 
 // Moments, Eq. (2) equilibrium in deviation form and Eq. (1) BGK relaxation

@@ -14,7 +14,7 @@ struct HostArgs {
     int64_t N;
     int bw, be, bs, bn;
     int layout, algo, storage, rounding;
-    double omega, kf, fx, fy, ux_in, uy_in;
+    double omega, kf, fx, fy, ux_in, uy_in, rho_out;
     uint64_t seed;
     int tile_x, tile_y, ntx, nty;
     int block_1d;              // LPTL block size

@@ -66,6 +66,7 @@ Step<S> make_step(const HostArgs &h, const StepCall &c) {
     k.zh5 = (C)(2.0 / 3.0 * h.ux_in);
     k.zh8 = (C)(h.ux_in / 6.0 + h.uy_in / 2.0);
     k.zh2 = (C)(h.ux_in / 6.0 - h.uy_in / 2.0);
+    k.drho_out = (C)(h.rho_out - 1.0);
     const double W[9] = {1.0 / 36, 1.0 / 9, 1.0 / 36, 1.0 / 9, 4.0 / 9,
                          1.0 / 9, 1.0 / 36, 1.0 / 9, 1.0 / 36};
     for (int i = 0; i < 9; ++i) {
@@ -131,11 +132,27 @@ __device__ __forceinline__ void st_dst(S *p, S v) {
 #endif
 }
 
+// Density deviation of node n + 1 (the Neumann inlet's east neighbour) in a
+// stored state, summed in canonical direction order; 0 if it is solid.
+template <class S, int L>
+__device__ __forceinline__ typename Codec<S>::C neighbour_drho(const Step<S> &a, const S *lat, uint32_t n,
+                                                               int rev) {
+    using C = typename Codec<S>::C;
+    if (a.links[n + 1] == SOLID_LINKS) return C(0);
+    C d = C(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d = Ar<C>::add(d, ldp<S, L>(lat, a.N, n + 1, rev ? opp(i) : i));
+    return d;
+}
+
 // Inlet substitution, collision, divergence flag, moments, and encoding of
 // the nine post-collision values (canonical direction order) into e.
+// drho_nb: density deviation of node (1, y) in the previous state, used by
+// the Neumann equilibrium inlet only.
 template <class S>
 __device__ __forceinline__ void collide_encode(const Step<S> &a, uint32_t x, uint32_t n,
-                                               typename Codec<S>::C *g, S *e) {
+                                               typename Codec<S>::C *g, S *e,
+                                               typename Codec<S>::C drho_nb = 0) {
     using C = typename Codec<S>::C;
     using A = Ar<C>;
     if (x == 0) {
@@ -144,8 +161,15 @@ __device__ __forceinline__ void collide_encode(const Step<S> &a, uint32_t x, uin
         } else if (a.geo.bw == INLET_EQ) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) g[i] = a.k.heq_in[i];
+        } else if (a.geo.bw == INLET_EQ_NEUMANN) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const C w = i == 4 ? a.k.w4 : ((i & 1) ? a.k.w1 : a.k.w0);
+                g[i] = A::fma(w, drho_nb, a.k.heq_in[i]);
+            }
         }
     }
+    if (x == (uint32_t)a.geo.nx - 1 && a.geo.be == OUTLET_PRESSURE) zou_he_pressure(a.k, g);
     C drho, ux, uy;
     collide(a.k, g, drho, ux, uy);
     if (!isfinite(drho)) atomicOr(a.err, 1u);
@@ -287,7 +311,8 @@ __device__ __forceinline__ void two_lattice_node(const Step<S> &a, uint32_t x, u
         }
     }
     S e[9];
-    collide_encode(a, x, n, g, e);
+    const C dnb = (x == 0 && a.geo.bw == INLET_EQ_NEUMANN) ? neighbour_drho<S, L>(a, src, n, 0) : C(0);
+    collide_encode(a, x, n, g, e, dnb);
     store_node<S, L>(dst, n, a.N, a.off32, e);
 }
 
@@ -418,10 +443,11 @@ __device__ __forceinline__ void npol_tile(const Step<S> &a, int bx, int by, int 
             }
         }
     }
+    const C dnb = (fluid && x == 0 && a.geo.bw == INLET_EQ_NEUMANN) ? neighbour_drho<S, L>(a, lat, n, 0) : C(0);
     __syncthreads();
     if (fluid) {
         S e[9];
-        collide_encode(a, (uint32_t)x, n, g, e);
+        collide_encode(a, (uint32_t)x, n, g, e, dnb);
         store_node<S, L>(lat, n, a.N, a.off32, e);
         if (!inner) halo_publish(a.halo_wr, a.tx, a.ty, a.ntx, bx, by, x, y, x0, y0, x1, y1, e);
     } else if (zero_fill) {
@@ -471,6 +497,7 @@ __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int 
 #pragma unroll
         for (int s = 0; s < 9; ++s) sm[s * T + tid] = ldp<S, L>(lat, a.N, n, s);
     }
+    const C dnb = (fluid && x == 0 && a.geo.bw == INLET_EQ_NEUMANN) ? neighbour_drho<S, L>(a, lat, n, 1) : C(0);
     __syncthreads();
     // Substitutions for pulls the in-tile exchange does not cover.
     C fix[9];
@@ -531,7 +558,7 @@ __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int 
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = ((fixmask >> i) & 1u) ? fix[i] : sm[i * T + tid];
         S e[9];
-        collide_encode(a, (uint32_t)x, n, g, e);
+        collide_encode(a, (uint32_t)x, n, g, e, dnb);
 #pragma unroll
         for (int i = 0; i < 9; ++i) lat[addr<L>(a.N, n, opp(i))] = e[i];
         if (!(x > x0 && x < x1 && y > y0 && y < y1))

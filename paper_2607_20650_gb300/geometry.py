@@ -18,7 +18,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # Edge-condition codes (identical numbering in the C ABI header).
-PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG = range(6)
+PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG, INLET_EQ_NEUMANN, OUTLET_PRESSURE = range(8)
 
 _M64 = (1 << 64) - 1
 _GAMMA = 0x9E3779B97F4A7C15

@@ -20,7 +20,7 @@ LAYOUTS = {"stream": 0, "bundle": 1, "collision": 2}
 ALGOS = {"lptl": 0, "nptl": 1, "npol": 2, "nsol": 3, "aa": 4}
 STORAGES = {"f64": 0, "f32": 1, "f16s": 2, "bf16s": 3}
 ROUNDINGS = {"rne": 0, "sr": 1}
-PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG = range(6)
+PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG, INLET_EQ_NEUMANN, OUTLET_PRESSURE = range(8)
 LBM_FLAG_NO_GRAPH = 1
 LBM_AUTO = -1
 
@@ -44,6 +44,7 @@ class lbm_params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
         ("flags", ctypes.c_uint32),
+        ("rho_out", ctypes.c_double),
     ]
 
 
@@ -145,7 +146,7 @@ def _f64(a):
 
 def make_params(nx, ny, tau, *, force=(0.0, 0.0), u_in=(0.0, 0.0), bc=(PERIODIC,) * 4,
                 layout="stream", algo="nptl", storage="f32", rounding="rne", seed=0,
-                tile=(0, 0), flags=0) -> lbm_params:
+                tile=(0, 0), flags=0, rho_out=1.0) -> lbm_params:
     """bc = (west, east, south, north)."""
     p = lbm_params()
     p.nx, p.ny, p.tau = int(nx), int(ny), float(tau)
@@ -159,6 +160,7 @@ def make_params(nx, ny, tau, *, force=(0.0, 0.0), u_in=(0.0, 0.0), bc=(PERIODIC,
     p.seed = int(seed)
     p.tile_x, p.tile_y = tile
     p.flags = int(flags)
+    p.rho_out = float(rho_out)
     return p
 
 

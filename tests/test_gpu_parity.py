@@ -61,7 +61,7 @@ STORAGE_CASES = [("f64", "rne"), ("f32", "rne"), ("f16s", "rne"), ("f16s", "sr")
                  ("bf16s", "rne"), ("bf16s", "sr")]
 
 
-@pytest.mark.parametrize("case", ["channel", "porous", "walls"])
+@pytest.mark.parametrize("case", ["channel", "porous", "walls", "neumann_pressure"])
 @pytest.mark.parametrize("storage,rounding", STORAGE_CASES)
 def test_all_layouts_and_algorithms_bit_identical(case, storage, rounding):
     spec = SPECS[case]
@@ -242,3 +242,12 @@ def test_codec_stochastic_rounding_is_unbiased_and_keyed(storage):
     p = (float(val) - lo) / (hi - lo)
     frac = np.mean(v1 == hi)
     assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / K) + 2 ** -24
+
+
+def test_neumann_inlet_rejected_for_aa_and_thin_one_lattice_tiles():
+    spec = SPECS["neumann_pressure"]
+    with pytest.raises(lbm.LbmError) as e:
+        spec.gpu(algo="aa", storage="f32")
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    with pytest.raises(lbm.LbmError):
+        spec.gpu(algo="npol", storage="f32", tile=(1, 64))
