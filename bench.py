@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tile", default="")
     ap.add_argument("--layout", default="bundle", choices=["stream", "bundle", "collision"])
-    ap.add_argument("--algo", default="nptl", choices=["lptl", "nptl", "npol", "nsol"])
+    ap.add_argument("--algo", default="nptl", choices=["lptl", "nptl", "npol", "nsol", "aa"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s", "f64"])
     return ap.parse_args()
 
@@ -149,7 +149,8 @@ def max_over_ranks(value: float, device: str) -> float:
 
 def kernel_name(args) -> str:
     t = {"f32": "float", "f64": "double", "f16s": "__half", "bf16s": "__nv_bfloat16"}[args.storage]
-    k = {"lptl": "k_two_lattice", "nptl": "k_two_lattice", "npol": "k_npol", "nsol": "k_nsol"}[args.algo]
+    k = {"lptl": "k_two_lattice", "nptl": "k_two_lattice", "npol": "k_npol", "nsol": "k_nsol",
+         "aa": "k_aa"}[args.algo]
     return f"{k}<{t}, {args.layout.upper()}, {args.algo.upper()}>"
 
 
