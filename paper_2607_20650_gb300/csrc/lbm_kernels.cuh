@@ -588,8 +588,9 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_nsol(const Step<S> a) {
 // Each slot is read and written by the same node within a phase, so no
 // synchronisation is needed. Zero-gradient outflow reads one slot from two
 // nodes and is not supported here.
-template <class S, int L>
-__device__ __forceinline__ void aa_node(const Step<S> &a, uint32_t x, uint32_t y, int lane, int phase) {
+template <class S, int L, int PHASE>
+__device__ __forceinline__ void aa_node(const Step<S> &a, uint32_t x, uint32_t y, int lane) {
+    constexpr int phase = PHASE;
     using C = typename Codec<S>::C;
     const uint32_t nx = (uint32_t)a.geo.nx, ny = (uint32_t)a.geo.ny;
     const uint32_t n = y * nx + x;
@@ -678,8 +679,24 @@ __device__ __forceinline__ void aa_node(const Step<S> &a, uint32_t x, uint32_t y
         } else if (interior) {
             lat[addr<L>(a.N, n + (uint32_t)(cy(i) * (int)nx + cx(i)), i)] = e[i];
         } else {
-            // Every fluid node (within one cell, across periodic edges) whose
-            // mapped pull reads S[x]_i receives it in the slot it pulls.
+            // The neighbour x + c_i (wrapped across periodic edges) pulls
+            // S[x]_i into slot i whenever it lies in the domain; otherwise the
+            // puller is found through the edge mapping: every fluid node
+            // within one cell whose mapped pull reads S[x]_i receives it.
+            int tx_ = (int)x + cx(i), ty_ = (int)y + cy(i);
+            bool in = true;
+            if (tx_ < 0 || tx_ >= (int)nx) {
+                if (a.geo.bw == PERIODIC) tx_ = tx_ < 0 ? tx_ + (int)nx : tx_ - (int)nx;
+                else in = false;
+            }
+            if (ty_ < 0 || ty_ >= (int)ny) {
+                if (a.geo.bs == PERIODIC) ty_ = ty_ < 0 ? ty_ + (int)ny : ty_ - (int)ny;
+                else in = false;
+            }
+            if (in) {
+                lat[addr<L>(a.N, (uint32_t)ty_ * nx + (uint32_t)tx_, i)] = e[i];
+                continue;
+            }
 #pragma unroll 1
             for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll 1
@@ -709,12 +726,12 @@ __device__ __forceinline__ void aa_node(const Step<S> &a, uint32_t x, uint32_t y
     }
 }
 
-template <class S, int L>
-__global__ void __launch_bounds__(kMaxTileThreads) k_aa(const Step<S> a, int phase) {
+template <class S, int L, int PHASE>
+__global__ void __launch_bounds__(kMaxTileThreads, PHASE == 0 ? 3 : 1) k_aa(const Step<S> a) {
     const uint32_t x = blockIdx.x * a.tx + threadIdx.x;
     const uint32_t y = blockIdx.y * a.ty + threadIdx.y;
     if (x >= (uint32_t)a.geo.nx || y >= (uint32_t)a.geo.ny) return;
-    aa_node<S, L>(a, x, y, (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u), phase);
+    aa_node<S, L, PHASE>(a, x, y, (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u));
 }
 
 // ------------------------------------------------------------ batches
@@ -1071,7 +1088,12 @@ cudaError_t step_layout(const HostArgs &h, const Step<S> &a, int phase, cudaStre
             k_nsol<S, L><<<grid, tile, sm, st>>>(a);
             break;
         }
-        case AA: k_aa<S, L><<<grid, tile, 0, st>>>(a, phase); break;
+        case AA:
+            if (phase)
+                k_aa<S, L, 1><<<grid, tile, 0, st>>>(a);
+            else
+                k_aa<S, L, 0><<<grid, tile, 0, st>>>(a);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
