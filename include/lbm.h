@@ -106,6 +106,9 @@ typedef enum {
 } lbm_bc;
 
 #define LBM_FLAG_NO_GRAPH 0x1u   /* lbm_step launches kernels one by one */
+#define LBM_FLAG_ONE_NODE_PER_THREAD 0x2u  /* NPTL, F64/F32 storage: one node per thread
+                                              (default with an even tile_y: two, rows y and
+                                              y + tile_y/2) */
 
 typedef struct lbm_params {
     int32_t nx, ny;          /* lattice size; nx*ny < 2^32 */

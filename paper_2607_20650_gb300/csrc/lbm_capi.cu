@@ -189,6 +189,7 @@ void lbm_fill_args(const lbm_params *p, const Plan &pl, char *ws, const Ops *ops
     h->ntx = pl.ntx;
     h->nty = pl.nty;
     h->block_1d = p->algo == LBM_LPTL ? ops->lptl_block(p->layout) : 0;
+    h->flags = p->flags;
     h->nx_magic = p->nx == 1 ? 0ull : (~0ull / (uint64_t)p->nx) + 1ull;
     h->links = (const uint8_t *)(ws + pl.links);
     h->pop[0] = ws + pl.pop[0];

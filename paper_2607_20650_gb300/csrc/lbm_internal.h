@@ -18,6 +18,7 @@ struct HostArgs {
     uint64_t seed;
     int tile_x, tile_y, ntx, nty;
     int block_1d;              // LPTL block size
+    uint32_t flags;            // lbm_params.flags
     uint64_t nx_magic;         // ceil(2^64 / nx) for n -> (x, y); 0 when nx == 1
     const uint8_t *links;
     void *pop[2];              // pop[1] == nullptr for one-lattice algorithms

@@ -265,26 +265,16 @@ __device__ __forceinline__ void store_node(S *dst, uint32_t n, uint32_t N, int o
     }
 }
 
-// One node of the two-lattice pull update (LPTL and NPTL). Interior nodes
-// take a path with 32-bit element offsets where each pull is one select
-// between two uniform offsets (pulled neighbour or own opposite slot); nodes
-// on the domain edge take the general mapping. lane: the thread's lane.
+// Pull, collide and store one fluid node of the two-lattice update. Interior
+// nodes take a path with 32-bit element offsets where each pull is one
+// select between two uniform offsets (pulled neighbour or own opposite slot);
+// nodes on the domain edge take the general mapping.
 template <class S, int L>
-__device__ __forceinline__ void two_lattice_node(const Step<S> &a, uint32_t x, uint32_t y, int lane) {
+__device__ __forceinline__ void two_lattice_fluid(const Step<S> &a, uint32_t x, uint32_t y, uint32_t n,
+                                                  uint32_t lk) {
     using C = typename Codec<S>::C;
     const uint32_t nx = (uint32_t)a.geo.nx, ny = (uint32_t)a.geo.ny;
-    const uint32_t n = y * nx + x;
-    const uint32_t lk = a.links[n];
     S *__restrict__ dst = a.dst;
-    const bool fluid = lk != SOLID_LINKS;
-    const unsigned F = __ballot_sync(__activemask(), fluid);
-    if (!fluid) {
-        // Solid nodes hold h = 0 and are never read. Where a solid node's
-        // record shares a DRAM sector with a fluid node's, store the zeros
-        // again so the sector is written whole (no read-modify-write).
-        if (shares_sector<S, L>(F, lane)) store_zero<S, L>(dst, a.N, n, a.off32);
-        return;
-    }
     const S *__restrict__ src = a.src;
     const bool interior = (x - 1u < nx - 2u) && (y - 1u < ny - 2u);
     C g[9];
@@ -314,6 +304,64 @@ __device__ __forceinline__ void two_lattice_node(const Step<S> &a, uint32_t x, u
     const C dnb = (x == 0 && a.geo.bw == INLET_EQ_NEUMANN) ? neighbour_drho<S, L>(a, src, n, 0) : C(0);
     collide_encode(a, x, n, g, e, dnb);
     store_node<S, L>(dst, n, a.N, a.off32, e);
+}
+
+// One node of the two-lattice pull update (LPTL and NPTL). lane: the
+// thread's lane (the zero fill below votes over the warp).
+template <class S, int L>
+__device__ __forceinline__ void two_lattice_node(const Step<S> &a, uint32_t x, uint32_t y, int lane) {
+    const uint32_t n = y * (uint32_t)a.geo.nx + x;
+    const uint32_t lk = a.links[n];
+    const bool fluid = lk != SOLID_LINKS;
+    const unsigned F = __ballot_sync(__activemask(), fluid);
+    if (!fluid) {
+        // Solid nodes hold h = 0 and are never read. Where a solid node's
+        // record shares a DRAM sector with a fluid node's, store the zeros
+        // again so the sector is written whole (no read-modify-write).
+        if (shares_sector<S, L>(F, lane)) store_zero<S, L>(a.dst, a.N, n, a.off32);
+        return;
+    }
+    two_lattice_fluid<S, L>(a, x, y, n, lk);
+}
+
+// NPTL with two nodes per thread, rows y and y + ty/2 of a tx x ty tile:
+// both link bytes, then all eighteen pulls of interior nodes are issued
+// before either collision, so one thread keeps twice the loads in flight.
+template <class S, int L>
+__global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice2(const Step<S> a) {
+    using C = typename Codec<S>::C;
+    const uint32_t nx = (uint32_t)a.geo.nx, ny = (uint32_t)a.geo.ny;
+    const uint32_t x = blockIdx.x * a.tx + threadIdx.x;
+    const uint32_t ya = blockIdx.y * a.ty + threadIdx.y, yb = ya + (uint32_t)(a.ty >> 1);
+    if (x >= nx || ya >= ny) return;
+    const int lane = (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u);
+    const bool hb = yb < ny;
+    const uint32_t na = ya * nx + x, nb = yb * nx + x;
+    const uint32_t lka = a.links[na];
+    const uint32_t lkb = hb ? (uint32_t)a.links[nb] : SOLID_LINKS;
+    const bool fa = lka != SOLID_LINKS, fb = lkb != SOLID_LINKS;
+    const unsigned act = __activemask();
+    const unsigned Fa = __ballot_sync(act, fa), Fb = __ballot_sync(act, hb && fb);
+    if (!fa && shares_sector<S, L>(Fa, lane)) store_zero<S, L>(a.dst, a.N, na, a.off32);
+    if (hb && !fb && shares_sector<S, L>(Fb, lane)) store_zero<S, L>(a.dst, a.N, nb, a.off32);
+    const bool fast_a = fa && a.off32 && (x - 1u < nx - 2u) && (ya - 1u < ny - 2u);
+    const bool fast_b = fb && a.off32 && (x - 1u < nx - 2u) && (yb - 1u < ny - 2u);
+    C ga[9], gb[9];
+    if (fast_a) pull_interior<S, L>(a.src, na, nx, a.N, lka, ga);
+    if (fast_b) pull_interior<S, L>(a.src, nb, nx, a.N, lkb, gb);
+    S e[9];
+    if (fast_a) {
+        collide_encode(a, x, na, ga, e);
+        store_node<S, L>(a.dst, na, a.N, a.off32, e);
+    } else if (fa) {
+        two_lattice_fluid<S, L>(a, x, ya, na, lka);
+    }
+    if (fast_b) {
+        collide_encode(a, x, nb, gb, e);
+        store_node<S, L>(a.dst, nb, a.N, a.off32, e);
+    } else if (fb) {
+        two_lattice_fluid<S, L>(a, x, yb, nb, lkb);
+    }
 }
 
 // LPTL (LINEAR: one node per thread over n, block size from the runtime) and
@@ -1081,7 +1129,14 @@ cudaError_t step_layout(const HostArgs &h, const Step<S> &a, int phase, cudaStre
             k_two_lattice<S, L, true><<<g, b, 0, st>>>(a);
             break;
         }
-        case NPTL: k_two_lattice<S, L, false><<<grid, tile, 0, st>>>(a); break;
+        case NPTL:
+            // Two nodes per thread pays off for 4- and 8-byte storage (measured);
+            // the 16-bit paths are issue-bound and keep one node per thread.
+            if (sizeof(S) >= 4 && h.tile_y >= 2 && !(h.tile_y & 1) && !(h.flags & 2u))
+                k_two_lattice2<S, L><<<grid, dim3(h.tile_x, h.tile_y / 2), 0, st>>>(a);
+            else
+                k_two_lattice<S, L, false><<<grid, tile, 0, st>>>(a);
+            break;
         case NPOL: k_npol<S, L><<<grid, tile, 0, st>>>(a); break;
         case NSOL: {
             const size_t sm = sizeof(C) * 9 * h.tile_x * h.tile_y + h.tile_x * h.tile_y;
