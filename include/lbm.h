@@ -109,6 +109,8 @@ typedef enum {
 #define LBM_FLAG_ONE_NODE_PER_THREAD 0x2u  /* NPTL, F64/F32 storage: one node per thread
                                               (default with an even tile_y: two, rows y and
                                               y + tile_y/2) */
+#define LBM_FLAG_NO_STAGING 0x4u  /* NPTL, collision layout: no shared-memory staging of
+                                     row spans (default when tile_x % 32 == 0) */
 
 typedef struct lbm_params {
     int32_t nx, ny;          /* lattice size; nx*ny < 2^32 */

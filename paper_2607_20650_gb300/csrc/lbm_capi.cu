@@ -188,6 +188,7 @@ void lbm_fill_args(const lbm_params *p, const Plan &pl, char *ws, const Ops *ops
     h->tile_y = pl.ty;
     h->ntx = pl.ntx;
     h->nty = pl.nty;
+    ops->prepare();
     h->block_1d = p->algo == LBM_LPTL ? ops->lptl_block(p->layout) : 0;
     h->flags = p->flags;
     h->nx_magic = p->nx == 1 ? 0ull : (~0ull / (uint64_t)p->nx) + 1ull;

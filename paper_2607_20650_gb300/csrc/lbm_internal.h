@@ -56,6 +56,7 @@ struct Ops {
     // Moments buffer (compute type) -> FP32 device arrays.
     cudaError_t (*moments_f32)(const HostArgs &, float *r, float *u, float *v, cudaStream_t);
     int (*lptl_block)(int layout);  // occupancy-chosen LPTL block size
+    void (*prepare)();              // one-time kernel attributes (called at create)
     // Batches: one persistent launch over the packed tile list.
     // kind = layout * 4 + algo shared by every case, or -1 for a mixed batch.
     cudaError_t (*batch_step)(int kind, const void *cases, const void *tiles, uint32_t ntiles, int grid,

@@ -36,6 +36,7 @@ struct Step {
     int tx, ty, ntx;
     uint64_t nx_magic;
     int off32;  // 9N < 2^32: element offsets fit 32 bits
+    int aos16;  // nx % 16 == 0: warp segments of 32 records start on 16-byte boundaries
 };
 
 // Host: FP64 constants rounded once to the compute type.
@@ -92,6 +93,7 @@ Step<S> make_step(const HostArgs &h, const StepCall &c) {
     a.ntx = h.ntx;
     a.nx_magic = h.nx_magic;
     a.off32 = (9 * h.N) < (int64_t(1) << 32) ? 1 : 0;
+    a.aos16 = (h.nx % 16 == 0) ? 1 : 0;
     return a;
 }
 
@@ -362,6 +364,96 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice2(const Step<S> 
     } else if (fb) {
         two_lattice_fluid<S, L>(a, x, yb, nb, lkb);
     }
+}
+
+// Collision layout (9 contiguous values per node), NPTL: a warp owns 32
+// consecutive nodes of a row. For warps of 32 fluid nodes away from the domain
+// edges, the three source row spans (nodes x0-1 .. x0+32 of rows y+1, y, y-1)
+// are staged in shared memory with 16-byte loads, the pulls read shared
+// memory, and the 32 output records are written back with 16-byte stores.
+// Other warps use the per-node path.
+template <class S>
+struct AosSpan {
+    static constexpr int R = 9 * (int)sizeof(S);                    // record bytes
+    static constexpr int CHUNKS = (34 * R + 15) / 16 + 1;           // 16-byte chunks per row span
+    static constexpr int ROW_BYTES = CHUNKS * 16;
+    static constexpr int WARP_BYTES = 3 * ROW_BYTES;
+};
+
+template <class S>
+__global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice_aos(const Step<S> a) {
+    using C = typename Codec<S>::C;
+    using SP = AosSpan<S>;
+    extern __shared__ __align__(16) unsigned char smem_aos[];
+    const uint32_t nx = (uint32_t)a.geo.nx, ny = (uint32_t)a.geo.ny;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t x = blockIdx.x * a.tx + threadIdx.x;
+    const uint32_t y = blockIdx.y * a.ty + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const uint32_t n = y * nx + x;
+    const uint32_t lk = a.links[n];
+    const bool fluid = lk != SOLID_LINKS;
+    const unsigned act = __activemask();
+    const unsigned F = __ballot_sync(act, fluid);
+    const uint32_t x0 = x - (uint32_t)lane;   // first node of this warp's row segment
+    // Staging pays off for warps of fluid nodes only (measured): with solid
+    // nodes in the warp the spans carry unused records and the stores stay scalar.
+    const bool staged = F == 0xffffffffu && a.off32 && a.aos16 && x0 >= 1u && x0 + 33u <= nx &&
+                        y >= 1u && y + 2u <= ny;
+    if (!staged) {
+        if (!fluid) {
+            if (shares_sector<S, COLLISION>(F, lane)) store_zero<S, COLLISION>(a.dst, a.N, n, a.off32);
+            return;
+        }
+        two_lattice_fluid<S, COLLISION>(a, x, y, n, lk);
+        return;
+    }
+    unsigned char *wbuf = smem_aos + (size_t)warp * SP::WARP_BYTES;
+    const uint32_t n0 = y * nx + x0;
+    const unsigned char *srcb = reinterpret_cast<const unsigned char *>(a.src);
+    int shift[3];   // bytes from each staged span start to record (n0 - 1 - c_y nx)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {       // r = c_y + 1: source row y - c_y
+        const uint64_t first = (uint64_t)SP::R * (uint64_t)(n0 - 1u - (uint32_t)((r - 1) * (int)nx));
+        const uint64_t base = first & ~(uint64_t)15;
+        shift[r] = (int)(first - base);
+        const uint4 *g4 = reinterpret_cast<const uint4 *>(srcb + base);
+        uint4 *s4 = reinterpret_cast<uint4 *>(wbuf + r * SP::ROW_BYTES);
+#pragma unroll
+        for (int k = lane; k < SP::CHUNKS; k += 32) s4[k] = __ldg(g4 + k);
+    }
+    __syncwarp();
+    C g[9];
+    if (fluid) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const S *pp = reinterpret_cast<const S *>(wbuf + (cy(i) + 1) * SP::ROW_BYTES + shift[cy(i) + 1]) +
+                          (lane + 1 - cx(i)) * 9 + i;
+            const S *pb = reinterpret_cast<const S *>(wbuf + SP::ROW_BYTES + shift[1]) + (lane + 1) * 9 + opp(i);
+            g[i] = Codec<S>::dec(((lk >> link_bit(i)) & 1u) ? *pb : *pp);
+        }
+    }
+    S e[9];
+    if (fluid) collide_encode(a, x, n, g, e);
+    if (F != 0xffffffffu) {
+        if (fluid) {
+            store_node<S, COLLISION>(a.dst, n, a.N, a.off32, e);
+        } else if (shares_sector<S, COLLISION>(F, lane)) {
+            store_zero<S, COLLISION>(a.dst, a.N, n, a.off32);
+        }
+        return;
+    }
+    __syncwarp();   // every lane has read its inputs; reuse the first span for the output
+    S *out = reinterpret_cast<S *>(wbuf);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out[lane * 9 + i] = e[i];
+    __syncwarp();
+    uint4 *d4 = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(a.dst) + (uint64_t)SP::R * n0);
+    const uint4 *o4 = reinterpret_cast<const uint4 *>(wbuf);
+    constexpr int OUT_CHUNKS = 32 * SP::R / 16;
+#pragma unroll
+    for (int k = lane; k < OUT_CHUNKS; k += 32) d4[k] = o4[k];
 }
 
 // LPTL (LINEAR: one node per thread over n, block size from the runtime) and
@@ -1130,6 +1222,11 @@ cudaError_t step_layout(const HostArgs &h, const Step<S> &a, int phase, cudaStre
             break;
         }
         case NPTL:
+            if (L == COLLISION && h.tile_x % 32 == 0 && !(h.flags & 4u)) {
+                const size_t sm = (size_t)AosSpan<S>::WARP_BYTES * ((h.tile_x * h.tile_y + 31) / 32);
+                k_two_lattice_aos<S><<<grid, tile, sm, st>>>(a);
+                break;
+            }
             // Two nodes per thread pays off for 4- and 8-byte storage (measured);
             // the 16-bit paths are issue-bound and keep one node per thread.
             if (sizeof(S) >= 4 && h.tile_y >= 2 && !(h.tile_y & 1) && !(h.flags & 2u))
@@ -1247,6 +1344,19 @@ int op_lptl_block(int layout) {
     }
 }
 
+// Allow the staged collision-layout kernel more than the default 48 KB of
+// dynamic shared memory (FP64: 7.4 KB per warp). Called at lattice creation.
+template <class S>
+void op_prepare() {
+    static const bool done = [] {
+        cudaFuncSetAttribute(k_two_lattice_aos<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             AosSpan<S>::WARP_BYTES * (kMaxTileThreads / 32));
+        cudaGetLastError();
+        return true;
+    }();
+    (void)done;
+}
+
 template <class S>
 Ops make_ops() {
     Ops o;
@@ -1259,6 +1369,7 @@ Ops make_ops() {
     o.force = op_force<S>;
     o.moments_f32 = op_moments_f32<S>;
     o.lptl_block = op_lptl_block<S>;
+    o.prepare = op_prepare<S>;
     o.batch_step = op_batch_step<S>;
     o.batch_grid = op_batch_grid<S>;
     o.batch_case = op_batch_case<S>;

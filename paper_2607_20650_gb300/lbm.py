@@ -23,6 +23,7 @@ ROUNDINGS = {"rne": 0, "sr": 1}
 PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG, INLET_EQ_NEUMANN, OUTLET_PRESSURE = range(8)
 LBM_FLAG_NO_GRAPH = 1
 LBM_FLAG_ONE_NODE_PER_THREAD = 2
+LBM_FLAG_NO_STAGING = 4
 LBM_AUTO = -1
 
 
