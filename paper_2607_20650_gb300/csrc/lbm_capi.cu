@@ -413,6 +413,28 @@ extern "C" lbm_status lbm_wait(lbm_lattice *L, double timeout_s) {
     return lbm_sync(L);
 }
 
+// ------------------------------------------------------------ host loops
+// Run fn(begin, end) over [0, count) on up to 16 host threads (large arrays
+// only; the conversions below are independent per element).
+template <class Fn>
+static void parallel_for(int64_t count, Fn fn) {
+    const int64_t grain = 1 << 20;
+    int nt = (int)std::min<int64_t>(16, std::max<int64_t>(1, count / grain));
+    const unsigned hw = std::thread::hardware_concurrency();
+    if (hw > 0) nt = std::min<int>(nt, (int)hw);
+    if (nt <= 1) {
+        fn((int64_t)0, count);
+        return;
+    }
+    std::vector<std::thread> th;
+    const int64_t step = (count + nt - 1) / nt;
+    for (int t = 0; t < nt; ++t) {
+        const int64_t b = t * step, e = std::min(count, b + step);
+        if (b < e) th.emplace_back(fn, b, e);
+    }
+    for (auto &x : th) x.join();
+}
+
 // ------------------------------------------------------------ read-out
 extern "C" lbm_status lbm_read_moments(lbm_lattice *L, double *rho, double *ux, double *uy) {
     if (!L) return lbm_fail(LBM_EINVAL, "lattice is NULL");
@@ -428,7 +450,10 @@ extern "C" lbm_status lbm_read_moments(lbm_lattice *L, double *rho, double *ux, 
             memcpy(dst[k], buf.data() + (size_t)k * N * 8, (size_t)N * 8);
         } else {
             const float *f = (const float *)(buf.data() + (size_t)k * N * 4);
-            for (int64_t n = 0; n < N; ++n) dst[k][n] = f[n];
+            double *d = dst[k];
+            parallel_for(N, [f, d](int64_t b, int64_t e) {
+                for (int64_t n = b; n < e; ++n) d[n] = f[n];
+            });
         }
     }
     return check_err(L);
@@ -510,13 +535,15 @@ lbm_status lbm_pops_to_host(const unsigned char *raw, int storage, int layout, i
                             int32_t as) {
     for (int i = 0; i < 9; ++i) {
         const int slot = rev ? 8 - i : i;
-        for (int64_t n = 0; n < N; ++n) {
-            const double v = raw_get(raw, storage, layout_addr(layout, N, n, slot));
-            if (as == LBM_F64)
-                ((double *)host)[(int64_t)i * N + n] = v;
-            else
-                ((float *)host)[(int64_t)i * N + n] = (float)v;
-        }
+        parallel_for(N, [=](int64_t b, int64_t e) {
+            for (int64_t n = b; n < e; ++n) {
+                const double v = raw_get(raw, storage, layout_addr(layout, N, n, slot));
+                if (as == LBM_F64)
+                    ((double *)host)[(int64_t)i * N + n] = v;
+                else
+                    ((float *)host)[(int64_t)i * N + n] = (float)v;
+            }
+        });
     }
     return LBM_OK;
 }
@@ -541,13 +568,17 @@ extern "C" lbm_status lbm_write_populations(lbm_lattice *L, const void *host, in
     const int64_t N = L->pl.N;
     std::vector<unsigned char> raw(9 * (size_t)N * L->ops->elem);
     const int rev = L->p.algo == LBM_NSOL || L->p.algo == LBM_AA;
+    unsigned char *rawp = raw.data();
+    const int storage = L->p.storage, layout = L->p.layout;
     for (int i = 0; i < 9; ++i) {
         const int slot = rev ? 8 - i : i;
-        for (int64_t n = 0; n < N; ++n) {
-            const double v = as == LBM_F64 ? ((const double *)host)[(int64_t)i * N + n]
-                                           : (double)((const float *)host)[(int64_t)i * N + n];
-            raw_set(raw.data(), L->p.storage, layout_addr(L->p.layout, N, n, slot), v);
-        }
+        parallel_for(N, [=](int64_t b, int64_t e) {
+            for (int64_t n = b; n < e; ++n) {
+                const double v = as == LBM_F64 ? ((const double *)host)[(int64_t)i * N + n]
+                                               : (double)((const float *)host)[(int64_t)i * N + n];
+                raw_set(rawp, storage, layout_addr(layout, N, n, slot), v);
+            }
+        });
     }
     CK(cudaStreamSynchronize(L->stream));
     CK(cudaMemcpy(L->h.pop[L->cur], raw.data(), raw.size(), cudaMemcpyHostToDevice));

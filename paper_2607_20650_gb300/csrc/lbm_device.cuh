@@ -175,11 +175,9 @@ __host__ __device__ __forceinline__ int map_pull(const Geo &g, int x, int y, int
 // ------------------------------------------------------------ collision
 template <class C> struct Consts {
     C omega;              // 1/tau
-    C c1;                 // 1 - omega
     C hfx, hfy;           // F/2
     C fx, fy, sF, dF;     // F, fx+fy, fx-fy
     C w0, w1, w4;         // 1/36, 1/9, 4/9
-    C ow0, ow1, ow4;      // omega * w
     C kw0, kw1, kw4;      // (1 - omega/2) * w
     C zh5, zh8, zh2;      // Zou-He: 2/3 Ux, Ux/6 + Uy/2, Ux/6 - Uy/2
     C drho_out;           // pressure outlet: rho_out - 1
@@ -214,7 +212,7 @@ __device__ __forceinline__ void zou_he_pressure(const Consts<C> &k, C *g) {
 // Moments, Eq. (2) equilibrium in deviation form and Eq. (1) BGK relaxation
 // with the Guo source, in one fixed operation order:
 //   P_i   = drho - 3/2 u^2 + cu_i (3 + 9/2 cu_i)          (h_i^eq = w_i P_i)
-//   h*_i  = (1 - omega) g_i + (omega w_i) P_i
+//   h*_i  = g_i + omega (w_i P_i - g_i)                    (w P - g in one fma)
 //           + (1 - omega/2) w_i [cF_i (3 + 9 cu_i) - 3 u.F]
 // with cu_i = c_i.u, cF_i = c_i.F. g (pulled h values) is replaced by h*.
 template <class C>
@@ -236,9 +234,9 @@ __device__ __forceinline__ void collide(const Consts<C> &k, C *g, C &drho, C &ux
     const C m3uF = A::mul(C(-3), A::fma(ux, k.fx, A::mul(uy, k.fy)));
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const C ow = i == 4 ? k.ow4 : ((i & 1) ? k.ow1 : k.ow0);
+        const C w = i == 4 ? k.w4 : ((i & 1) ? k.w1 : k.w0);
         const C P = A::fma(cu[i], A::fma(C(4.5), cu[i], C(3)), base);
-        C o = A::fma(ow, P, A::mul(k.c1, g[i]));
+        C o = A::fma(k.omega, A::fma(w, P, -g[i]), g[i]);
         if (k.force) {
             const C kw = i == 4 ? k.kw4 : ((i & 1) ? k.kw1 : k.kw0);
             o = A::fma(kw, A::fma(cF[i], A::fma(C(9), cu[i], C(3)), m3uF), o);

@@ -48,10 +48,6 @@ Step<S> make_step(const HostArgs &h, const StepCall &c) {
     a.N = (uint32_t)h.N;
     Consts<C> &k = a.k;
     k.omega = (C)h.omega;
-    k.c1 = (C)(1.0 - h.omega);
-    k.ow0 = (C)(h.omega / 36.0);
-    k.ow1 = (C)(h.omega / 9.0);
-    k.ow4 = (C)(4.0 * h.omega / 9.0);
     k.hfx = (C)(0.5 * h.fx);
     k.hfy = (C)(0.5 * h.fy);
     k.fx = (C)h.fx;
@@ -1095,10 +1091,12 @@ __global__ void k_publish(const Step<S> a, S *hw, int rev) {
 }
 
 // Moments from a stored state: rho = 1 + sum h, v = sum h c (- F/2 for a
-// post-collision state, since the collision adds F to sum f c).
+// post-collision state, since the collision adds F to sum f c), in the
+// arithmetic type (used for the moments reported after lbm_init).
 template <class S, int L>
 __global__ void k_state_moments(const Step<S> a, int rev, int post) {
     using C = typename Codec<S>::C;
+    using A = Ar<C>;
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= a.N) return;
     C *m = (C *)a.mom;
@@ -1108,21 +1106,23 @@ __global__ void k_state_moments(const Step<S> a, int rev, int post) {
         m[2 * a.N + n] = C(0);
         return;
     }
-    double r = 0.0, jx = 0.0, jy = 0.0;
+    C h[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = ldp<S, L>(a.src, a.N, n, rev ? opp(i) : i);
+    C r = C(0), jx = C(0), jy = C(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const double h = (double)ldp<S, L>(a.src, a.N, n, rev ? opp(i) : i);
-        r += h;
-        jx += cx(i) * h;
-        jy += cy(i) * h;
+        r = A::add(r, h[i]);
+        if (cx(i) != 0) jx = cx(i) > 0 ? A::add(jx, h[i]) : A::sub(jx, h[i]);
+        if (cy(i) != 0) jy = cy(i) > 0 ? A::add(jy, h[i]) : A::sub(jy, h[i]);
     }
     if (post) {
-        jx -= 0.5 * (double)a.k.fx;
-        jy -= 0.5 * (double)a.k.fy;
+        jx = A::sub(jx, a.k.hfx);
+        jy = A::sub(jy, a.k.hfy);
     }
-    m[n] = (C)(1.0 + r);
-    m[a.N + n] = (C)jx;
-    m[2 * a.N + n] = (C)jy;
+    m[n] = A::add(C(1), r);
+    m[a.N + n] = jx;
+    m[2 * a.N + n] = jy;
 }
 
 // Deterministic FP64 block reduction (fixed grid and tree).
