@@ -68,8 +68,8 @@ __global__ void k_quantize(int sr, uint64_t seed, uint32_t t, const float *in, S
 
 cudaError_t launch_links(int nx, int ny, int bw, int be, int bs, int bn, const uint8_t *mask,
                          uint8_t *links, cudaStream_t st) {
-    const uint32_t N = (uint32_t)nx * (uint32_t)ny;
-    k_links<<<(N + 255) / 256, 256, 0, st>>>(Geo{nx, ny, bw, be, bs, bn}, mask, links);
+    const uint64_t N = (uint64_t)nx * (uint64_t)ny;
+    k_links<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(Geo{nx, ny, bw, be, bs, bn}, mask, links);
     return cudaGetLastError();
 }
 
