@@ -33,7 +33,7 @@ __global__ void k_links(Geo g, const uint8_t *mask, uint8_t *links) {
 
 __global__ void k_count_fluid(const uint8_t *links, uint32_t N, unsigned long long *out) {
     unsigned long long c = 0;
-    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x)
+    for (uint64_t n = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (uint64_t)gridDim.x * blockDim.x)
         c += links[n] != SOLID_LINKS;
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(out, c);

@@ -1143,7 +1143,9 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[W], double *parti
 template <class S, int L>
 __global__ void __launch_bounds__(kReduceThreads) k_mass(const Step<S> a, int rev, double *partials) {
     double acc[1] = {0.0};
-    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < a.N; n += gridDim.x * blockDim.x) {
+    for (uint64_t n64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; n64 < a.N;
+         n64 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t n = (uint32_t)n64;
         if (a.links[n] == SOLID_LINKS) continue;
         double r = 1.0;
 #pragma unroll
@@ -1158,7 +1160,9 @@ __global__ void __launch_bounds__(kReduceThreads) k_force(const Step<S> a, int r
                                                           double *partials) {
     double acc[2] = {0.0, 0.0};
     const int nx = a.geo.nx, ny = a.geo.ny;
-    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < a.N; n += gridDim.x * blockDim.x) {
+    for (uint64_t n64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; n64 < a.N;
+         n64 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t n = (uint32_t)n64;
         if (a.links[n] == SOLID_LINKS) continue;
         const int y = a.nx_magic ? (int)__umul64hi((unsigned long long)n, a.nx_magic) : (int)n;
         const int x = (int)n - y * nx;
