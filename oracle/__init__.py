@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
+_SRC3 = os.path.join(_HERE, "lbm3_oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liblbm_oracle.so")
 
@@ -41,15 +42,24 @@ class _Params(ctypes.Structure):
     ]
 
 
+class _Params3(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("tau", ctypes.c_double), ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+        ("fz", ctypes.c_double),
+        ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32), ("bc_z", ctypes.c_int32),
+    ]
+
+
 def build(force: bool = False) -> str:
     """Compile lbm_oracle.c with gcc (OpenMP, no FP contraction) if stale."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC3))):
         return _LIB
     os.makedirs(_LIB_DIR, exist_ok=True)
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-           "-std=c11", _SRC, "-o", tmp, "-lm"]
+           "-std=c11", _SRC, _SRC3, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -74,6 +84,15 @@ def _load():
         lib.oracle_mass.restype = ctypes.c_double
         lib.oracle_force.argtypes = [P(_Params), u8, u8, d, d]
         lib.oracle_omp_threads.restype = ctypes.c_int
+        P3 = P(_Params3)
+        lib.oracle3_directions.argtypes = [P(ctypes.c_int32), d]
+        lib.oracle3_equilibrium.argtypes = [ctypes.c_double] * 4 + [d]
+        lib.oracle3_effective_solid.argtypes = [P3, u8, u8]
+        lib.oracle3_init.argtypes = [P3, u8, d, d, d, d, d]
+        lib.oracle3_run.argtypes = [P3, u8, d, ctypes.c_int64, d, d, d, d]
+        lib.oracle3_run.restype = ctypes.c_int
+        lib.oracle3_mass.argtypes = [P3, u8, d]
+        lib.oracle3_mass.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -178,3 +197,73 @@ class Lattice:
 
     def field(self, a: np.ndarray) -> np.ndarray:
         return a.reshape(self.case.ny, self.case.nx)
+
+
+# ------------------------------------------------------------ D3Q19
+
+@dataclass
+class Case3:
+    """A D3Q19 lattice: size, tau, force, per-axis faces (PERIODIC or WALL)."""
+    nx: int
+    ny: int
+    nz: int
+    tau: float
+    fx: float = 0.0
+    fy: float = 0.0
+    fz: float = 0.0
+    bc_x: int = PERIODIC
+    bc_y: int = PERIODIC
+    bc_z: int = PERIODIC
+
+    def _c(self):
+        return _Params3(self.nx, self.ny, self.nz, self.tau, self.fx, self.fy, self.fz,
+                        self.bc_x, self.bc_y, self.bc_z)
+
+
+def directions3():
+    """(19 x 3) integer velocities and 19 weights of the D3Q19 set."""
+    c = np.zeros(57, dtype=np.int32)
+    w = np.zeros(19)
+    _load().oracle3_directions(c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(w))
+    return c.reshape(19, 3), w
+
+
+def equilibrium3(drho, ux, uy, uz) -> np.ndarray:
+    out = np.zeros(19)
+    _load().oracle3_equilibrium(drho, ux, uy, uz, _dp(out))
+    return out
+
+
+class Lattice3:
+    """D3Q19 oracle state: canonical h[i, n], n = (z*ny + y)*nx + x."""
+
+    def __init__(self, case: Case3, mask=None, rho=None, ux=None, uy=None, uz=None):
+        self.case = case
+        N = case.nx * case.ny * case.nz
+        if mask is None:
+            mask = np.zeros(N, np.uint8)
+        mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        self.solid = np.zeros_like(mask)
+        _load().oracle3_effective_solid(ctypes.byref(case._c()), _u8(mask), _u8(self.solid))
+        self.h = np.zeros((19, N))
+        arr = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+               for a in (rho, ux, uy, uz)]
+        _load().oracle3_init(ctypes.byref(case._c()), _u8(self.solid), *[_dp(a) for a in arr],
+                             _dp(self.h))
+        self.steps = 0
+
+    def set_h(self, h):
+        self.h = np.ascontiguousarray(h, dtype=np.float64).reshape(19, -1).copy()
+
+    def run(self, nsteps: int):
+        N = self.h.shape[1]
+        self.rho, self.ux, self.uy, self.uz = (np.empty(N) for _ in range(4))
+        rc = _load().oracle3_run(ctypes.byref(self.case._c()), _u8(self.solid), _dp(self.h),
+                                 int(nsteps), _dp(self.rho), _dp(self.ux), _dp(self.uy), _dp(self.uz))
+        if rc != 0:
+            raise MemoryError("oracle3_run: out of host memory")
+        self.steps += nsteps
+        return self
+
+    def mass(self) -> float:
+        return float(_load().oracle3_mass(ctypes.byref(self.case._c()), _u8(self.solid), _dp(self.h)))

@@ -1,0 +1,116 @@
+"""Pins for the D3Q19 oracle (the 3-D extension of the method).
+
+The strongest pin is a projection: summing the D3Q19 populations of a lattice
+that is invariant along one axis over the velocity component of that axis
+gives D2Q9 populations with the D2Q9 weights, and the BGK update with Guo
+forcing and bounce-back commutes with that sum. So a y-invariant (or
+z-invariant) D3Q19 run must reproduce the D2Q9 oracle, which is itself
+pinned by exact-rational brute force."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2607_20650_gb300 import geometry as G
+
+C3, W3 = O.directions3()
+
+
+def test_direction_set():
+    assert C3.shape == (19, 3)
+    assert (C3[::-1] == -C3).all()                      # opposite(i) = 18 - i
+    assert (C3[9] == 0).all() and W3[9] == pytest.approx(1 / 3)
+    assert abs(W3.sum() - 1) < 1e-15
+    q = (C3 ** 2).sum(axis=1)
+    assert set(q) == {0, 1, 2}
+    assert np.allclose(W3[q == 1], 1 / 18) and np.allclose(W3[q == 2], 1 / 36)
+
+
+@pytest.mark.parametrize("drho,u", [(0.0, (0.0, 0.0, 0.0)), (0.02, (0.05, -0.03, 0.01)),
+                                    (-0.1, (-0.1, 0.2, -0.05))])
+def test_equilibrium_moments_3d(drho, u):
+    h = O.equilibrium3(drho, *u)
+    f = h + W3
+    rho = 1 + drho
+    tol = 5e-16 * (1 + abs(rho))
+    assert abs(f.sum() - rho) < tol
+    for a in range(3):
+        assert abs((f * C3[:, a]).sum() - u[a]) < tol
+        for b in range(3):
+            exp = rho / 3 * (a == b) + u[a] * u[b]
+            assert abs((f * C3[:, a] * C3[:, b]).sum() - exp) < tol
+
+
+def test_pure_streaming_3d_is_exact_shift():
+    nx, ny, nz, T = 6, 5, 4, 3
+    rng = np.random.default_rng(1)
+    h0 = rng.normal(0, 0.01, size=(19, nx * ny * nz))
+    lat = O.Lattice3(O.Case3(nx, ny, nz, math.inf))
+    lat.set_h(h0)
+    lat.run(T)
+    for i in range(19):
+        exp = np.roll(h0[i].reshape(nz, ny, nx), (T * C3[i, 2], T * C3[i, 1], T * C3[i, 0]), axis=(0, 1, 2))
+        assert np.array_equal(lat.h[i].reshape(nz, ny, nx), exp)
+
+
+def test_mass_conserved_3d():
+    nx, ny, nz = 10, 9, 8
+    rng = np.random.default_rng(2)
+    mask = (rng.random(nx * ny * nz) < 0.2).astype(np.uint8)
+    lat = O.Lattice3(O.Case3(nx, ny, nz, 0.8, fx=1e-4, fz=-2e-5), mask,
+                     rho=1 + 1e-2 * rng.random(nx * ny * nz), ux=1e-2 * rng.random(nx * ny * nz))
+    m0 = lat.mass()
+    lat.run(40)
+    assert abs(lat.mass() - m0) / m0 < 1e-14
+
+
+def _project(h3, nx, ny, nz, axis):
+    """Sum D3Q19 populations over the velocity component along `axis` of a
+    lattice invariant along that axis; returns D2Q9 h on the other two axes."""
+    keep = [a for a in range(3) if a != axis]                  # (first, second) -> (x2, y2)
+    h3 = h3.reshape(19, nz, ny, nx)
+    slab = h3.take(0, axis=3 - axis)                            # one layer along the axis
+    out = np.zeros((9,) + slab.shape[1:])
+    for i in range(19):
+        c2x, c2y = C3[i, keep[0]], C3[i, keep[1]]
+        out[(c2x + 1) + 3 * (c2y + 1)] += slab[i]
+    return out                                                  # 2-D arrays indexed [y2][x2]
+
+
+@pytest.mark.parametrize("axis", [1, 2])
+def test_invariant_axis_reduces_to_d2q9(axis):
+    n1, n2 = 14, 9                       # the two kept axes
+    rng = np.random.default_rng(axis)
+    mask2 = (rng.random((n2, n1)) < 0.15).astype(np.uint8)
+    rho2 = 1 + 1e-2 * rng.random((n2, n1))
+    u2 = 1e-2 * rng.random((2, n2, n1))
+    bc2 = O.WALL
+    if axis == 2:                        # z-invariant: kept (x, y)
+        nx, ny, nz = n1, n2, 2
+        tile = lambda a: np.broadcast_to(a, (nz, ny, nx))
+        case3 = O.Case3(nx, ny, nz, 0.7, fx=2e-4, fy=-1e-4, bc_x=O.PERIODIC, bc_y=bc2)
+        uu = dict(ux=tile(u2[0]).ravel(), uy=tile(u2[1]).ravel())
+    else:                                # y-invariant: kept (x, z)
+        nx, ny, nz = n1, 3, n2
+        tile = lambda a: np.broadcast_to(a[:, None, :], (nz, ny, nx))
+        case3 = O.Case3(nx, ny, nz, 0.7, fx=2e-4, fz=-1e-4, bc_x=O.PERIODIC, bc_z=bc2)
+        uu = dict(ux=tile(u2[0]).ravel(), uz=tile(u2[1]).ravel())
+    lat3 = O.Lattice3(case3, tile(mask2).ravel(), rho=tile(rho2).ravel(), **uu).run(25)
+    case2 = O.Case(n1, n2, 0.7, fx=2e-4, fy=-1e-4, bc_s=bc2, bc_n=bc2)
+    lat2 = O.Lattice(case2, mask2, rho=rho2, ux=u2[0], uy=u2[1]).run(25)
+    proj = _project(lat3.h, nx, ny, nz, axis).reshape(9, -1)
+    np.testing.assert_allclose(proj, lat2.h, rtol=0, atol=5e-16)
+
+
+def test_plane_poiseuille_3d_slip_closed_form():
+    """Walls on the z faces, force along x: the steady profile is the
+    parabola plus the BGK bounce-back slip g (16 L - 3) / (24 nu)."""
+    H, tau, g = 8, 0.8, 1e-6
+    nu = (tau - 0.5) / 3
+    lat = O.Lattice3(O.Case3(2, 2, H, tau, fx=g, bc_z=O.WALL)).run(int(60 * H * H / nu))
+    ux = lat.ux.reshape(H, 2, 2)[:, 0, 0]
+    z = np.arange(H) + 0.5
+    par = g / (2 * nu) * z * (H - z)
+    slip = g * (16 * (tau - 0.5) ** 2 - 3) / (24 * nu)
+    assert np.max(np.abs(ux - par - slip)) / par.max() < 1e-10
