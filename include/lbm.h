@@ -270,6 +270,61 @@ lbm_status lbm_batch_read_populations(lbm_batch *B, int32_t c, void *host, int32
 lbm_status lbm_batch_get_info(lbm_batch *B, int64_t *items, int32_t *grid, int64_t *cells);
 void lbm_batch_destroy(lbm_batch *B);
 
+/* ---------------------------------------------------------------- D3Q19
+ * Three-dimensional lattices (Sec. 6 names the 3-D extension as future
+ * work) with the method of Sec. 3.1: Eq. 1 BGK with the Eq. 2 incompressible
+ * equilibrium (v = sum f c) on the 19 velocities of {-1,0,1}^3 with
+ * |c|^2 <= 2, numbered lexicographically in (c_z, c_y, c_x): opposite(i) =
+ * 18 - i, rest i = 9, weights 1/3, 1/18 (faces), 1/36 (edges). Node index
+ * n = (z ny + y) nx + x; h = f - w is stored as in 2-D.
+ * Layouts (lbm_layout): STREAM h[i N + n]; COLLISION h[19 n + i]; BUNDLE
+ * groups the directions with the same (c_y, c_z), i.e. the same source row:
+ * {0}, {1,2,3}, {4}, {5,6,7}, {8,9,10}, {11,12,13}, {14}, {15,16,17}, {18},
+ * a group of size s starting at direction b stored at b N + s n + (i - b).
+ * Algorithms: LPTL and NPTL (3-D tiles tile_x * tile_y * tile_z <= 512,
+ * 0,0,0 = 32 x 4 x 2; tile_z <= 64); two lattices. Faces per axis: PERIODIC or WALL
+ * (half-way bounce-back); solid mask nodes bounce back; a fluid node whose
+ * 18 pulls all bounce is treated as solid. Storage, rounding, Guo force,
+ * graphs and errors as in 2-D. Workspace: 2 x 19 N elements, 4 N bytes of
+ * links, 4 N compute-type moments, small scratch.                         */
+typedef struct lbm3_params {
+    int32_t nx, ny, nz;      /* lattice size; nx*ny*nz < 2^32 */
+    double tau;              /* relaxation time, > 1/2 */
+    double force[3];         /* Guo body force */
+    int32_t bc_x, bc_y, bc_z;   /* LBM_BC_PERIODIC or LBM_BC_WALL, both faces of the axis */
+    int32_t layout, algo, storage, rounding;   /* algo: LBM_LPTL or LBM_NPTL */
+    uint64_t seed;
+    int32_t tile_x, tile_y, tile_z;
+    uint32_t flags;          /* LBM_FLAG_NO_GRAPH */
+} lbm3_params;
+
+typedef struct lbm3_lattice lbm3_lattice;
+
+lbm_status lbm3_workspace_bytes(const lbm3_params *p, size_t *bytes);
+/* mask_host: N bytes, nonzero = solid (host, read during the call); the
+ * workspace (256-byte aligned device memory of lbm3_workspace_bytes) and
+ * the stream stay the caller's. Initial state: rho = 1, v = 0. */
+lbm_status lbm3_create(const lbm3_params *p, const uint8_t *mask_host, void *d_workspace, size_t bytes,
+                       void *cuda_stream, lbm3_lattice **out);
+/* Equilibrium from host arrays of N doubles (each may be NULL: rho 1, v 0).
+ * Synchronous; resets the update count. */
+lbm_status lbm3_init(lbm3_lattice *L, const double *rho, const double *ux, const double *uy,
+                     const double *uz);
+/* Enqueue nsteps updates; with want_moments the last writes rho, v. */
+lbm_status lbm3_step(lbm3_lattice *L, int64_t nsteps, uint32_t want_moments);
+lbm_status lbm3_sync(lbm3_lattice *L);
+/* Host arrays of N doubles (any may be NULL); solid nodes read rho 1, v 0. */
+lbm_status lbm3_read_moments(lbm3_lattice *L, double *rho, double *ux, double *uy, double *uz);
+/* Canonical host array [i N + n] (19 N values of type as). */
+lbm_status lbm3_read_populations(lbm3_lattice *L, void *host, int32_t as);
+lbm_status lbm3_write_populations(lbm3_lattice *L, const void *host, int32_t as);
+/* Total mass sum over fluid nodes of sum_i f_i, accumulated in FP64. */
+lbm_status lbm3_mass(lbm3_lattice *L, double *out);
+/* cells, fluid_cells, steps, tile (tile_y = tile_y * tile_z), bytes per update. */
+lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out);
+void lbm3_destroy(lbm3_lattice *L);
+int64_t lbm3_layout_index(int32_t layout, int64_t N, int64_t n, int32_t i);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,688 @@
+// D3Q19 lattices (the paper's 3-D future work, Sec. 6) with the method of
+// Sec. 3.1: two-lattice pull (LPTL: one node per thread over n; NPTL: 3-D
+// tiles), the three layouts generalised (stream, bundle = directions sharing
+// a source row, collision), periodic or half-way wall faces, bounce-back at
+// solid nodes, Guo force, FP64/FP32/FP16/BF16 shifted storage, on-the-fly
+// moments, FP64 mass, CUDA graphs. C ABI: the lbm3_* calls of include/lbm.h.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm3_device.cuh"
+#include "lbm_capi_internal.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace d3 {
+
+struct Geo3 {
+    int nx, ny, nz;
+    int bx, by, bz;   // per axis: PERIODIC or WALL
+};
+
+// Source node of the value pulled by (x, y, z) in direction i, or bounce.
+__host__ __device__ __forceinline__ bool map3(const Geo3 &g, int x, int y, int z, int i, uint32_t &src) {
+    int s[3] = {x - cx(i), y - cy(i), z - cz(i)};
+    const int ext[3] = {g.nx, g.ny, g.nz};
+    const int bc[3] = {g.bx, g.by, g.bz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (s[a] < 0 || s[a] >= ext[a]) {
+            if (bc[a] != PERIODIC) return false;
+            s[a] = s[a] < 0 ? s[a] + ext[a] : s[a] - ext[a];
+        }
+    }
+    src = ((uint32_t)s[2] * (uint32_t)g.ny + (uint32_t)s[1]) * (uint32_t)g.nx + (uint32_t)s[0];
+    return true;
+}
+
+template <class S>
+struct Step3 {
+    using C = typename Codec<S>::C;
+    Geo3 g;
+    uint32_t N;
+    Consts3<C> k;
+    const uint32_t *links;
+    const S *src;
+    S *dst;
+    C *mom;
+    unsigned int *err;
+    const long long *tctr;
+    int toff;
+    int sr;
+    uint64_t seed;
+    int tx, ty, tz;
+    uint64_t nx_magic, nxy_magic;   // ceil(2^64 / nx), ceil(2^64 / (nx ny)); 0 for 1
+};
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, uint64_t magic) {
+    return magic ? (uint32_t)__umul64hi((unsigned long long)n, magic) : n;
+}
+
+__global__ void k3_links(Geo3 g, const uint8_t *mask, uint32_t *links) {
+    const uint64_t N64 = (uint64_t)g.nx * g.ny * g.nz;
+    const uint64_t n64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n64 >= N64) return;
+    const uint32_t n = (uint32_t)n64;
+    if (mask[n]) {
+        links[n] = SOLID;
+        return;
+    }
+    const uint32_t nxy = (uint32_t)g.nx * (uint32_t)g.ny;
+    const int z = (int)(n / nxy), r = (int)(n - (uint32_t)z * nxy);
+    const int y = r / g.nx, x = r - y * g.nx;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (i == REST) continue;
+        uint32_t s;
+        if (!map3(g, x, y, z, i, s) || mask[s]) bits |= 1u << bit(i);
+    }
+    links[n] = bits;   // SOLID when every pull bounces (isolated node)
+}
+
+__global__ void k3_count(const uint32_t *links, uint32_t N, unsigned long long *out) {
+    unsigned long long c = 0;
+    for (uint64_t n = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (uint64_t)gridDim.x * blockDim.x)
+        c += links[n] != SOLID;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
+}
+
+template <class S, int L>
+__device__ __forceinline__ void node3(const Step3<S> &a, uint32_t x, uint32_t y, uint32_t z) {
+    using C = typename Codec<S>::C;
+    using A = Ar<C>;
+    const uint32_t nx = (uint32_t)a.g.nx, ny = (uint32_t)a.g.ny, nz = (uint32_t)a.g.nz;
+    const uint32_t n = (z * ny + y) * nx + x;
+    const uint32_t lk = a.links[n];
+    if (lk == SOLID) return;
+    const S *__restrict__ src = a.src;
+    const bool interior = (x - 1u < nx - 2u) && (y - 1u < ny - 2u) && (z - 1u < nz - 2u);
+    C g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        uint32_t s = n;
+        int j = i;
+        if (i != REST) {
+            if ((lk >> bit(i)) & 1u) {
+                j = opp(i);
+            } else if (interior) {
+                s = n - (uint32_t)((cz(i) * (int)ny + cy(i)) * (int)nx + cx(i));
+            } else {
+                map3(a.g, (int)x, (int)y, (int)z, i, s);
+            }
+        }
+        g[i] = Codec<S>::dec(src[addr<L>(a.N, s, j)]);
+    }
+    C drho, ux, uy, uz;
+    collide3(a.k, g, drho, ux, uy, uz);
+    if (!isfinite(drho)) atomicOr(a.err, 1u);
+    if (a.mom) {
+        a.mom[n] = A::add(C(1), drho);
+        a.mom[a.N + n] = ux;
+        a.mom[2 * (size_t)a.N + n] = uy;
+        a.mom[3 * (size_t)a.N + n] = uz;
+    }
+    const bool sr = Codec<S>::narrow && a.sr;
+    uint32_t nk = 0;
+    if (sr) nk = node_key(step_key(a.seed, (uint32_t)(*a.tctr + a.toff)), n);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) a.dst[addr<L>(a.N, n, i)] = Codec<S>::enc(g[i], sr, sr ? pop_rand(nk, i) : 0u);
+}
+
+template <class S, int L, bool LINEAR>
+__global__ void __launch_bounds__(512) k3_step(const Step3<S> a) {
+    uint32_t x, y, z;
+    if (LINEAR) {
+        const uint64_t n64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (n64 >= a.N) return;
+        const uint32_t n = (uint32_t)n64;
+        z = fdiv(n, a.nxy_magic);
+        const uint32_t r = n - z * (uint32_t)a.g.nx * (uint32_t)a.g.ny;
+        y = fdiv(r, a.nx_magic);
+        x = r - y * (uint32_t)a.g.nx;
+    } else {
+        x = blockIdx.x * a.tx + threadIdx.x;
+        y = blockIdx.y * a.ty + threadIdx.y;
+        z = blockIdx.z * a.tz + threadIdx.z;
+        if (x >= (uint32_t)a.g.nx || y >= (uint32_t)a.g.ny || z >= (uint32_t)a.g.nz) return;
+    }
+    node3<S, L>(a, x, y, z);
+}
+
+template <class S, int L>
+__global__ void k3_init(const Step3<S> a, const double *rho, const double *ux, const double *uy,
+                        const double *uz, uint32_t n0, uint32_t count) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const uint32_t n = n0 + t;
+    if (a.links[n] == SOLID) return;
+    const double dr = rho ? rho[t] - 1.0 : 0.0;
+    const double v[3] = {ux ? ux[t] : 0.0, uy ? uy[t] : 0.0, uz ? uz[t] : 0.0};
+    const double usq = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const double w = sq(i) == 0 ? 1.0 / 3.0 : (sq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+        const double cu = cx(i) * v[0] + cy(i) * v[1] + cz(i) * v[2];
+        const double h = w * (dr + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+        a.dst[addr<L>(a.N, n, i)] = Codec<S>::enc((typename Codec<S>::C)h, false, 0u);
+    }
+}
+
+template <class S, int L>
+__global__ void k3_state_moments(const Step3<S> a) {
+    using C = typename Codec<S>::C;
+    using A = Ar<C>;
+    const uint64_t n64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n64 >= a.N) return;
+    const uint32_t n = (uint32_t)n64;
+    C *m = a.mom;
+    if (a.links[n] == SOLID) {
+        m[n] = C(1);
+        m[a.N + n] = C(0);
+        m[2 * (size_t)a.N + n] = C(0);
+        m[3 * (size_t)a.N + n] = C(0);
+        return;
+    }
+    C r = C(0), j[3] = {C(0), C(0), C(0)};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const C h = Codec<S>::dec(a.src[addr<L>(a.N, n, i)]);
+        r = A::add(r, h);
+        if (cx(i)) j[0] = cx(i) > 0 ? A::add(j[0], h) : A::sub(j[0], h);
+        if (cy(i)) j[1] = cy(i) > 0 ? A::add(j[1], h) : A::sub(j[1], h);
+        if (cz(i)) j[2] = cz(i) > 0 ? A::add(j[2], h) : A::sub(j[2], h);
+    }
+    m[n] = A::add(C(1), r);
+    m[a.N + n] = j[0];
+    m[2 * (size_t)a.N + n] = j[1];
+    m[3 * (size_t)a.N + n] = j[2];
+}
+
+template <class S, int L>
+__global__ void __launch_bounds__(kReduceThreads) k3_mass(const Step3<S> a, double *partials) {
+    __shared__ double red[kReduceThreads];
+    double acc = 0.0;
+    for (uint64_t n64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; n64 < a.N;
+         n64 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t n = (uint32_t)n64;
+        if (a.links[n] == SOLID) continue;
+        double r = 1.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) r += (double)Codec<S>::dec(a.src[addr<L>(a.N, n, i)]);
+        acc += r;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = kReduceThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+template <class C>
+__global__ void k3_sum(const double *partials, int nb, double *out) {
+    if (threadIdx.x || blockIdx.x) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partials[b];
+    *out = s;
+}
+
+}  // namespace d3
+}  // namespace lbm
+
+using namespace lbm;
+using namespace lbm::d3;
+
+// ------------------------------------------------------------ host side
+namespace {
+
+struct Plan3 {
+    int64_t N = 0;
+    int tx = 0, ty = 1, tz = 1, ntx = 0, nty = 0, ntz = 0;
+    size_t elem = 0, comp = 0;
+    size_t pop[2] = {0, 0}, links = 0, mom = 0, mom_bytes = 0, partials = 0, misc = 0, total = 0;
+};
+
+size_t elem_of(int storage) { return storage == LBM_F64 ? 8 : storage == LBM_F32 ? 4 : 2; }
+size_t comp_of(int storage) { return storage == LBM_F64 ? 8 : 4; }
+
+lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
+    if (!p) return lbm_fail(LBM_EINVAL, "params is NULL");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return lbm_fail(LBM_EINVAL, "nx, ny, nz must be >= 1");
+    const uint64_t N = (uint64_t)p->nx * p->ny * p->nz;
+    if (N >= (1ull << 32)) return lbm_fail(LBM_EUNSUPPORTED, "nx*ny*nz must be < 2^32");
+    if (!(p->tau > 0.5)) return lbm_fail(LBM_EINVAL, "tau must be > 1/2");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(p->force[a])) return lbm_fail(LBM_EINVAL, "force must be finite");
+    const int bc[3] = {p->bc_x, p->bc_y, p->bc_z};
+    for (int a = 0; a < 3; ++a)
+        if (bc[a] != LBM_BC_PERIODIC && bc[a] != LBM_BC_WALL)
+            return lbm_fail(LBM_EINVAL, "D3Q19 faces are PERIODIC or WALL");
+    if (p->layout < 0 || p->layout > 2) return lbm_fail(LBM_EINVAL, "bad layout");
+    if (p->algo != LBM_LPTL && p->algo != LBM_NPTL) return lbm_fail(LBM_EUNSUPPORTED, "D3Q19: LPTL or NPTL");
+    if (p->storage < 0 || p->storage > 3) return lbm_fail(LBM_EINVAL, "bad storage");
+    if (p->rounding < 0 || p->rounding > 1) return lbm_fail(LBM_EINVAL, "bad rounding");
+    *pl = Plan3();
+    pl->N = (int64_t)N;
+    if (p->algo == LBM_NPTL) {
+        int tx = p->tile_x, ty = p->tile_y, tz = p->tile_z;
+        if (tx == 0 && ty == 0 && tz == 0) { tx = 32; ty = 4; tz = 2; }
+        if (tx < 1 || ty < 1 || tz < 1 || tz > 64 || (int64_t)tx * ty * tz > 512)
+            return lbm_fail(LBM_EINVAL, "tile must be positive, tile_z <= 64, tile_x*tile_y*tile_z <= 512");
+        pl->tx = tx; pl->ty = ty; pl->tz = tz;
+        pl->ntx = (p->nx + tx - 1) / tx;
+        pl->nty = (p->ny + ty - 1) / ty;
+        pl->ntz = (p->nz + tz - 1) / tz;
+        if (pl->nty > 65535 || pl->ntz > 65535) return lbm_fail(LBM_EUNSUPPORTED, "too many tiles in y or z");
+    }
+    pl->elem = elem_of(p->storage);
+    pl->comp = comp_of(p->storage);
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = (off + b + 255) / 256 * 256; return o; };
+    pl->pop[0] = take(19 * (size_t)N * pl->elem);
+    pl->pop[1] = take(19 * (size_t)N * pl->elem);
+    pl->links = take(4 * (size_t)N);
+    pl->mom_bytes = std::max(4 * (size_t)N * pl->comp, 4 * sizeof(double) * (size_t)std::min<uint64_t>(N, 1 << 16));
+    pl->mom = take(pl->mom_bytes);
+    pl->partials = take(sizeof(double) * (kReduceBlocks + 4));
+    pl->misc = take(256);
+    pl->total = off;
+    return LBM_OK;
+}
+
+uint64_t magic(uint64_t d) { return d <= 1 ? 0ull : (~0ull / d) + 1ull; }
+
+}  // namespace
+
+struct lbm3_lattice {
+    lbm3_params p;
+    Plan3 pl;
+    char *ws;
+    cudaStream_t stream, cap;
+    int cur;
+    int64_t steps;
+    int64_t fluid;
+    int block_1d;
+    cudaGraphExec_t graph[2];
+};
+
+template <class S>
+static Step3<S> make3(const lbm3_lattice *L, int src, int toff, int mom) {
+    using C = typename Codec<S>::C;
+    Step3<S> a;
+    const lbm3_params &p = L->p;
+    a.g = Geo3{p.nx, p.ny, p.nz, p.bc_x, p.bc_y, p.bc_z};
+    a.N = (uint32_t)L->pl.N;
+    const double om = 1.0 / p.tau, kf = 1.0 - 0.5 * om;
+    a.k.omega = (C)om;
+    for (int d = 0; d < 3; ++d) {
+        a.k.hf[d] = (C)(0.5 * p.force[d]);
+        a.k.f[d] = (C)p.force[d];
+    }
+    a.k.w0 = (C)(1.0 / 3.0);
+    a.k.w1 = (C)(1.0 / 18.0);
+    a.k.w2 = (C)(1.0 / 36.0);
+    a.k.kw0 = (C)(kf / 3.0);
+    a.k.kw1 = (C)(kf / 18.0);
+    a.k.kw2 = (C)(kf / 36.0);
+    a.k.force = (p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0) ? 1 : 0;
+    a.links = (const uint32_t *)(L->ws + L->pl.links);
+    a.src = (const S *)(L->ws + L->pl.pop[src]);
+    a.dst = (S *)(L->ws + L->pl.pop[src ^ 1]);
+    a.mom = mom ? (C *)(L->ws + L->pl.mom) : nullptr;
+    a.err = (unsigned int *)(L->ws + L->pl.misc);
+    a.tctr = (const long long *)(L->ws + L->pl.misc + 64);
+    a.toff = toff;
+    a.sr = p.rounding;
+    a.seed = p.seed;
+    a.tx = L->pl.tx;
+    a.ty = L->pl.ty;
+    a.tz = L->pl.tz;
+    a.nx_magic = magic((uint64_t)p.nx);
+    a.nxy_magic = magic((uint64_t)p.nx * (uint64_t)p.ny);
+    return a;
+}
+
+#define LBM3_DISPATCH(L_, ...)                                                                  \
+    switch ((L_)->p.storage) {                                                                   \
+        case LBM_F64: { using S = double; __VA_ARGS__; break; }                                         \
+        case LBM_F32: { using S = float; __VA_ARGS__; break; }                                          \
+        case LBM_F16S: { using S = __half; __VA_ARGS__; break; }                                        \
+        default: { using S = __nv_bfloat16; __VA_ARGS__; break; }                                       \
+    }
+
+template <class S>
+static cudaError_t step3(const lbm3_lattice *L, cudaStream_t st, int src, int toff, int mom) {
+    const Step3<S> a = make3<S>(L, src, toff, mom);
+    const int lay = L->p.layout;
+    if (L->p.algo == LBM_LPTL) {
+        const unsigned g = (unsigned)((L->pl.N + L->block_1d - 1) / L->block_1d);
+        if (lay == LBM_LAYOUT_STREAM) k3_step<S, STREAM, true><<<g, L->block_1d, 0, st>>>(a);
+        else if (lay == LBM_LAYOUT_BUNDLE) k3_step<S, BUNDLE, true><<<g, L->block_1d, 0, st>>>(a);
+        else k3_step<S, COLLISION, true><<<g, L->block_1d, 0, st>>>(a);
+    } else {
+        const dim3 grid(L->pl.ntx, L->pl.nty, L->pl.ntz), tile(L->pl.tx, L->pl.ty, L->pl.tz);
+        if (lay == LBM_LAYOUT_STREAM) k3_step<S, STREAM, false><<<grid, tile, 0, st>>>(a);
+        else if (lay == LBM_LAYOUT_BUNDLE) k3_step<S, BUNDLE, false><<<grid, tile, 0, st>>>(a);
+        else k3_step<S, COLLISION, false><<<grid, tile, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t launch3(lbm3_lattice *L, cudaStream_t st, int64_t count, int want_moments) {
+    int cur = L->cur;
+    for (int64_t k = 0; k < count; ++k) {
+        cudaError_t e = cudaSuccess;
+        const int mom = (want_moments && k == count - 1) ? 1 : 0;
+        LBM3_DISPATCH(L, e = step3<S>(L, st, cur, (int)k, mom));
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    return launch_bump_counter((long long *)(L->ws + L->pl.misc + 64), count, st);
+}
+
+#define CK3(call)                                                 \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return lbm_cuda_fail(e_, #call);   \
+    } while (0)
+
+extern "C" lbm_status lbm3_workspace_bytes(const lbm3_params *p, size_t *bytes) {
+    if (!bytes) return lbm_fail(LBM_EINVAL, "bytes is NULL");
+    Plan3 pl;
+    lbm_status s = plan3(p, &pl);
+    if (s == LBM_OK) *bytes = pl.total;
+    return s;
+}
+
+extern "C" int64_t lbm3_layout_index(int32_t layout, int64_t N, int64_t n, int32_t i) {
+    if (layout < 0 || layout > 2 || N < 1 || n < 0 || n >= N || i < 0 || i > 18) return -1;
+    if (layout == LBM_LAYOUT_STREAM) return d3::addr<STREAM>(N, n, i);
+    if (layout == LBM_LAYOUT_BUNDLE) return d3::addr<BUNDLE>(N, n, i);
+    return d3::addr<COLLISION>(N, n, i);
+}
+
+template <class S>
+static int block_of(int layout) {
+    auto pick = [](const void *k) {
+        int mg = 0, b = 256;
+        if (cudaOccupancyMaxPotentialBlockSize(&mg, &b, k, 0, 512) != cudaSuccess) {
+            cudaGetLastError();
+            b = 256;
+        }
+        return b;
+    };
+    if (layout == LBM_LAYOUT_STREAM) return pick((const void *)k3_step<S, STREAM, true>);
+    if (layout == LBM_LAYOUT_BUNDLE) return pick((const void *)k3_step<S, BUNDLE, true>);
+    return pick((const void *)k3_step<S, COLLISION, true>);
+}
+
+extern "C" lbm_status lbm3_init(lbm3_lattice *L, const double *rho, const double *ux, const double *uy,
+                                const double *uz) {
+    if (!L) return lbm_fail(LBM_EINVAL, "lattice is NULL");
+    const cudaStream_t st = L->stream;
+    const Plan3 &pl = L->pl;
+    CK3(cudaStreamSynchronize(st));
+    CK3(cudaMemsetAsync(L->ws + pl.pop[0], 0, 19 * (size_t)pl.N * pl.elem, st));
+    CK3(cudaMemsetAsync(L->ws + pl.pop[1], 0, 19 * (size_t)pl.N * pl.elem, st));
+    CK3(cudaMemsetAsync(L->ws + pl.misc, 0, 256, st));
+    L->cur = 0;
+    L->steps = 0;
+    if (rho || ux || uy || uz) {
+        const int64_t chunk = std::min<int64_t>(pl.N, (int64_t)(pl.mom_bytes / (4 * sizeof(double))));
+        double *d = (double *)(L->ws + pl.mom);
+        const double *in[4] = {rho, ux, uy, uz};
+        for (int64_t n0 = 0; n0 < pl.N; n0 += chunk) {
+            const int64_t c = std::min<int64_t>(chunk, pl.N - n0);
+            double *dv[4];
+            for (int k = 0; k < 4; ++k) {
+                dv[k] = in[k] ? d + k * chunk : nullptr;
+                if (in[k]) CK3(cudaMemcpyAsync(dv[k], in[k] + n0, c * sizeof(double), cudaMemcpyHostToDevice, st));
+            }
+            const unsigned g = (unsigned)((c + 255) / 256);
+            LBM3_DISPATCH(L, {
+                const Step3<S> a = make3<S>(L, 1, 0, 0);   // dst = lattice 0
+                if (L->p.layout == LBM_LAYOUT_STREAM)
+                    k3_init<S, STREAM><<<g, 256, 0, st>>>(a, dv[0], dv[1], dv[2], dv[3], (uint32_t)n0, (uint32_t)c);
+                else if (L->p.layout == LBM_LAYOUT_BUNDLE)
+                    k3_init<S, BUNDLE><<<g, 256, 0, st>>>(a, dv[0], dv[1], dv[2], dv[3], (uint32_t)n0, (uint32_t)c);
+                else
+                    k3_init<S, COLLISION><<<g, 256, 0, st>>>(a, dv[0], dv[1], dv[2], dv[3], (uint32_t)n0, (uint32_t)c);
+            });
+            CK3(cudaGetLastError());
+            CK3(cudaStreamSynchronize(st));
+        }
+    }
+    const unsigned g = (unsigned)((pl.N + 255) / 256);
+    LBM3_DISPATCH(L, {
+        Step3<S> a = make3<S>(L, 0, 0, 1);
+        if (L->p.layout == LBM_LAYOUT_STREAM) k3_state_moments<S, STREAM><<<g, 256, 0, st>>>(a);
+        else if (L->p.layout == LBM_LAYOUT_BUNDLE) k3_state_moments<S, BUNDLE><<<g, 256, 0, st>>>(a);
+        else k3_state_moments<S, COLLISION><<<g, 256, 0, st>>>(a);
+    });
+    CK3(cudaGetLastError());
+    CK3(cudaStreamSynchronize(st));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm3_create(const lbm3_params *p, const uint8_t *mask_host, void *d_workspace,
+                                  size_t bytes, void *cuda_stream, lbm3_lattice **out) {
+    if (!out) return lbm_fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    Plan3 pl;
+    lbm_status s = plan3(p, &pl);
+    if (s != LBM_OK) return s;
+    if (!d_workspace || ((uintptr_t)d_workspace) % 256)
+        return lbm_fail(LBM_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    if (bytes < pl.total) return lbm_fail(LBM_ENOMEM, "workspace too small: %zu given, %zu needed", bytes, pl.total);
+    if (!mask_host) return lbm_fail(LBM_EINVAL, "mask is NULL");
+    lbm3_lattice *L = new lbm3_lattice();
+    L->p = *p;
+    L->pl = pl;
+    L->ws = (char *)d_workspace;
+    L->stream = (cudaStream_t)cuda_stream;
+    LBM3_DISPATCH(L, L->block_1d = block_of<S>(p->layout));
+    cudaError_t e = cudaStreamCreateWithFlags(&L->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete L;
+        return lbm_cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    uint8_t *dmask = (uint8_t *)(L->ws + pl.mom);   // staged in the moments region (>= N bytes)
+    unsigned long long *dcount = (unsigned long long *)(L->ws + pl.partials);
+    unsigned long long fluid = 0;
+    const Geo3 g{p->nx, p->ny, p->nz, p->bc_x, p->bc_y, p->bc_z};
+    e = cudaMemcpyAsync(dmask, mask_host, (size_t)pl.N, cudaMemcpyHostToDevice, L->stream);
+    if (e == cudaSuccess) {
+        k3_links<<<(unsigned)((pl.N + 255) / 256), 256, 0, L->stream>>>(g, dmask, (uint32_t *)(L->ws + pl.links));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(dcount, 0, sizeof(*dcount), L->stream);
+    if (e == cudaSuccess) {
+        k3_count<<<1024, 256, 0, L->stream>>>((const uint32_t *)(L->ws + pl.links), (uint32_t)pl.N, dcount);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&fluid, dcount, sizeof(fluid), cudaMemcpyDeviceToHost, L->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(L->cap);
+        delete L;
+        return lbm_cuda_fail(e, "lbm3_create");
+    }
+    L->fluid = (int64_t)fluid;
+    s = lbm3_init(L, nullptr, nullptr, nullptr, nullptr);
+    if (s != LBM_OK) {
+        cudaStreamDestroy(L->cap);
+        delete L;
+        return s;
+    }
+    *out = L;
+    return LBM_OK;
+}
+
+extern "C" void lbm3_destroy(lbm3_lattice *L) {
+    if (!L) return;
+    cudaStreamSynchronize(L->stream);
+    for (auto &gx : L->graph)
+        if (gx) cudaGraphExecDestroy(gx);
+    cudaStreamDestroy(L->cap);
+    delete L;
+}
+
+extern "C" lbm_status lbm3_step(lbm3_lattice *L, int64_t nsteps, uint32_t want_moments) {
+    if (!L) return lbm_fail(LBM_EINVAL, "lattice is NULL");
+    if (nsteps < 0) return lbm_fail(LBM_EINVAL, "nsteps must be >= 0");
+    const int64_t G = 64;
+    int64_t left = nsteps;
+    while (!(L->p.flags & LBM_FLAG_NO_GRAPH) && left > G) {
+        cudaGraphExec_t &ex = L->graph[L->cur];
+        if (!ex) {
+            cudaGraph_t gr = nullptr;
+            CK3(cudaStreamBeginCapture(L->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = launch3(L, L->cap, G, 0);
+            cudaError_t e2 = cudaStreamEndCapture(L->cap, &gr);
+            if (e != cudaSuccess) {
+                if (gr) cudaGraphDestroy(gr);
+                return lbm_cuda_fail(e, "capturing D3Q19 updates");
+            }
+            if (e2 != cudaSuccess) return lbm_cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ex, gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) return lbm_cuda_fail(e, "cudaGraphInstantiate");
+        }
+        CK3(cudaGraphLaunch(ex, L->stream));
+        L->steps += G;
+        left -= G;
+    }
+    if (left > 0) {
+        CK3(launch3(L, L->stream, left, want_moments ? 1 : 0));
+        if (left & 1) L->cur ^= 1;
+        L->steps += left;
+    }
+    return LBM_OK;
+}
+
+static lbm_status check3(lbm3_lattice *L) {
+    unsigned int flag = 0;
+    CK3(cudaMemcpy(&flag, L->ws + L->pl.misc, sizeof(flag), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK3(cudaMemset(L->ws + L->pl.misc, 0, sizeof(flag)));
+        return lbm_fail(LBM_EDIVERGED, "non-finite density after %lld updates", (long long)L->steps);
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm3_sync(lbm3_lattice *L) {
+    if (!L) return lbm_fail(LBM_EINVAL, "lattice is NULL");
+    CK3(cudaStreamSynchronize(L->stream));
+    return check3(L);
+}
+
+extern "C" lbm_status lbm3_read_moments(lbm3_lattice *L, double *rho, double *ux, double *uy, double *uz) {
+    if (!L) return lbm_fail(LBM_EINVAL, "lattice is NULL");
+    const int64_t N = L->pl.N;
+    std::vector<unsigned char> buf(4 * (size_t)N * L->pl.comp);
+    CK3(cudaStreamSynchronize(L->stream));
+    CK3(cudaMemcpy(buf.data(), L->ws + L->pl.mom, buf.size(), cudaMemcpyDeviceToHost));
+    double *dst[4] = {rho, ux, uy, uz};
+    for (int k = 0; k < 4; ++k) {
+        if (!dst[k]) continue;
+        if (L->pl.comp == 8) {
+            memcpy(dst[k], buf.data() + (size_t)k * N * 8, (size_t)N * 8);
+        } else {
+            const float *f = (const float *)(buf.data() + (size_t)k * N * 4);
+            for (int64_t n = 0; n < N; ++n) dst[k][n] = f[n];
+        }
+    }
+    return check3(L);
+}
+
+static double get_raw(const unsigned char *raw, int storage, int64_t k) {
+    switch (storage) {
+        case LBM_F64: return ((const double *)raw)[k];
+        case LBM_F32: return ((const float *)raw)[k];
+        case LBM_F16S: return __half2float(((const __half *)raw)[k]);
+        default: return __bfloat162float(((const __nv_bfloat16 *)raw)[k]);
+    }
+}
+
+static void set_raw(unsigned char *raw, int storage, int64_t k, double v) {
+    switch (storage) {
+        case LBM_F64: ((double *)raw)[k] = v; break;
+        case LBM_F32: ((float *)raw)[k] = (float)v; break;
+        case LBM_F16S: ((__half *)raw)[k] = __float2half_rn((float)v); break;
+        default: ((__nv_bfloat16 *)raw)[k] = __float2bfloat16_rn((float)v); break;
+    }
+}
+
+extern "C" lbm_status lbm3_read_populations(lbm3_lattice *L, void *host, int32_t as) {
+    if (!L || !host) return lbm_fail(LBM_EINVAL, "NULL argument");
+    if (as != LBM_F64 && as != LBM_F32) return lbm_fail(LBM_EINVAL, "as must be LBM_F64 or LBM_F32");
+    const int64_t N = L->pl.N;
+    std::vector<unsigned char> raw(19 * (size_t)N * L->pl.elem);
+    CK3(cudaStreamSynchronize(L->stream));
+    CK3(cudaMemcpy(raw.data(), L->ws + L->pl.pop[L->cur], raw.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 19; ++i)
+        for (int64_t n = 0; n < N; ++n) {
+            const double v = get_raw(raw.data(), L->p.storage, lbm3_layout_index(L->p.layout, N, n, i));
+            if (as == LBM_F64) ((double *)host)[(int64_t)i * N + n] = v;
+            else ((float *)host)[(int64_t)i * N + n] = (float)v;
+        }
+    return check3(L);
+}
+
+extern "C" lbm_status lbm3_write_populations(lbm3_lattice *L, const void *host, int32_t as) {
+    if (!L || !host) return lbm_fail(LBM_EINVAL, "NULL argument");
+    if (as != LBM_F64 && as != LBM_F32) return lbm_fail(LBM_EINVAL, "as must be LBM_F64 or LBM_F32");
+    const int64_t N = L->pl.N;
+    std::vector<unsigned char> raw(19 * (size_t)N * L->pl.elem);
+    for (int i = 0; i < 19; ++i)
+        for (int64_t n = 0; n < N; ++n) {
+            const double v = as == LBM_F64 ? ((const double *)host)[(int64_t)i * N + n]
+                                           : (double)((const float *)host)[(int64_t)i * N + n];
+            set_raw(raw.data(), L->p.storage, lbm3_layout_index(L->p.layout, N, n, i), v);
+        }
+    CK3(cudaStreamSynchronize(L->stream));
+    CK3(cudaMemcpy(L->ws + L->pl.pop[L->cur], raw.data(), raw.size(), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm3_mass(lbm3_lattice *L, double *out) {
+    if (!L || !out) return lbm_fail(LBM_EINVAL, "NULL argument");
+    double *partials = (double *)(L->ws + L->pl.partials);
+    LBM3_DISPATCH(L, {
+        const Step3<S> a = make3<S>(L, L->cur, 0, 0);
+        if (L->p.layout == LBM_LAYOUT_STREAM) k3_mass<S, STREAM><<<kReduceBlocks, kReduceThreads, 0, L->stream>>>(a, partials);
+        else if (L->p.layout == LBM_LAYOUT_BUNDLE) k3_mass<S, BUNDLE><<<kReduceBlocks, kReduceThreads, 0, L->stream>>>(a, partials);
+        else k3_mass<S, COLLISION><<<kReduceBlocks, kReduceThreads, 0, L->stream>>>(a, partials);
+    });
+    CK3(cudaGetLastError());
+    k3_sum<double><<<1, 32, 0, L->stream>>>(partials, kReduceBlocks, partials + kReduceBlocks);
+    CK3(cudaGetLastError());
+    CK3(cudaMemcpyAsync(out, partials + kReduceBlocks, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    CK3(cudaStreamSynchronize(L->stream));
+    return check3(L);
+}
+
+extern "C" lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out) {
+    if (!L || !out) return lbm_fail(LBM_EINVAL, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->cells = L->pl.N;
+    out->fluid_cells = L->fluid;
+    out->steps = L->steps;
+    out->tile_x = L->p.algo == LBM_LPTL ? L->block_1d : L->pl.tx;
+    out->tile_y = L->p.algo == LBM_LPTL ? 1 : L->pl.ty * L->pl.tz;
+    out->bytes_per_update = (double)L->fluid * 38.0 * (double)L->pl.elem + 4.0 * (double)L->pl.N;
+    out->workspace_bytes = L->pl.total;
+    return LBM_OK;
+}

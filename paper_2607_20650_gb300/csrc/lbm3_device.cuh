@@ -1,0 +1,100 @@
+// D3Q19 building blocks: the three-dimensional extension the paper lists as
+// future work (Sec. 6), with the method of Sec. 3.1 (Eq. 1 BGK, Eq. 2
+// incompressible equilibrium with v = sum f c) on the 19 velocities of
+// {-1,0,1}^3 with |c|^2 <= 2, ordered lexicographically in (c_z, c_y, c_x):
+// opposite(i) = 18 - i, rest at i = 9, weights 1/3, 1/18 (faces), 1/36 (edges).
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+namespace d3 {
+
+constexpr int Q = 19;
+constexpr int REST = 9;
+constexpr uint32_t SOLID = 0x3FFFFu;  // all 18 pulls bounce: solid (or isolated) node
+
+__host__ __device__ constexpr int cx(int i) {
+    return i == 0 || i == 4 || i == 14 || i == 18 ? 0
+         : (i == 1 || i == 5 || i == 8 || i == 11 || i == 15) ? -1
+         : (i == 3 || i == 7 || i == 10 || i == 13 || i == 17) ? 1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 0 || (i >= 5 && i <= 7) || i == 14) ? -1 : ((i == 4 || (i >= 11 && i <= 13) || i == 18) ? 1 : 0);
+}
+__host__ __device__ constexpr int cz(int i) { return i <= 4 ? -1 : (i >= 14 ? 1 : 0); }
+__host__ __device__ constexpr int opp(int i) { return 18 - i; }
+__host__ __device__ constexpr int bit(int i) { return i < REST ? i : i - 1; }
+__host__ __device__ constexpr int sq(int i) { return cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i); }
+
+// Bundles: directions with the same (c_y, c_z) (the same source row), in
+// order; first direction and size of the bundle that holds direction i.
+__host__ __device__ constexpr int bundle_first(int i) {
+    return i == 0 ? 0 : i <= 3 ? 1 : i == 4 ? 4 : i <= 7 ? 5 : i <= 10 ? 8 : i <= 13 ? 11 : i == 14 ? 14 : i <= 17 ? 15 : 18;
+}
+__host__ __device__ constexpr int bundle_size(int i) { return (i == 0 || i == 4 || i == 14 || i == 18) ? 1 : 3; }
+
+// Element offset of population i of node n (N nodes): stream i N + n,
+// collision 19 n + i, bundle first N + size n + (i - first).
+template <int L>
+__host__ __device__ __forceinline__ int64_t addr(int64_t N, int64_t n, int i) {
+    if (L == STREAM) return (int64_t)i * N + n;
+    if (L == COLLISION) return n * 19 + i;
+    return (int64_t)bundle_first(i) * N + (int64_t)bundle_size(i) * n + (i - bundle_first(i));
+}
+
+template <class C> struct Consts3 {
+    C omega;
+    C hf[3];        // F/2
+    C f[3];         // F
+    C w0, w1, w2;   // 1/3, 1/18, 1/36
+    C kw0, kw1, kw2;  // (1 - omega/2) w
+    int force;
+};
+
+// Moments, Eq. 2 equilibrium (deviation form) and Eq. 1 BGK relaxation with
+// the Guo source in one fixed operation order (shared by every D3Q19 kernel):
+//   P_i  = drho - 3/2 u^2 + cu_i (3 + 9/2 cu_i),  h*_i = g_i + omega (w_i P_i - g_i)
+//          + (1 - omega/2) w_i [cF_i (3 + 9 cu_i) - 3 u.F]
+template <class C>
+__device__ __forceinline__ void collide3(const Consts3<C> &k, C *g, C &drho, C &ux, C &uy, C &uz) {
+    using A = Ar<C>;
+    C r = g[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) r = A::add(r, g[i]);
+    drho = r;
+    C j[3] = {C(0), C(0), C(0)};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (cx(i) > 0) j[0] = A::add(j[0], g[i]);
+        if (cx(i) < 0) j[0] = A::sub(j[0], g[i]);
+        if (cy(i) > 0) j[1] = A::add(j[1], g[i]);
+        if (cy(i) < 0) j[1] = A::sub(j[1], g[i]);
+        if (cz(i) > 0) j[2] = A::add(j[2], g[i]);
+        if (cz(i) < 0) j[2] = A::sub(j[2], g[i]);
+    }
+    ux = A::add(j[0], k.hf[0]);
+    uy = A::add(j[1], k.hf[1]);
+    uz = A::add(j[2], k.hf[2]);
+    const C usq = A::fma(ux, ux, A::fma(uy, uy, A::mul(uz, uz)));
+    const C base = A::fma(C(-1.5), usq, drho);
+    const C m3uF = A::mul(C(-3), A::fma(ux, k.f[0], A::fma(uy, k.f[1], A::mul(uz, k.f[2]))));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        C cu = C(0), cF = C(0);
+        if (cx(i)) { cu = cx(i) > 0 ? A::add(cu, ux) : A::sub(cu, ux); cF = cx(i) > 0 ? A::add(cF, k.f[0]) : A::sub(cF, k.f[0]); }
+        if (cy(i)) { cu = cy(i) > 0 ? A::add(cu, uy) : A::sub(cu, uy); cF = cy(i) > 0 ? A::add(cF, k.f[1]) : A::sub(cF, k.f[1]); }
+        if (cz(i)) { cu = cz(i) > 0 ? A::add(cu, uz) : A::sub(cu, uz); cF = cz(i) > 0 ? A::add(cF, k.f[2]) : A::sub(cF, k.f[2]); }
+        const C w = sq(i) == 0 ? k.w0 : (sq(i) == 1 ? k.w1 : k.w2);
+        const C P = A::fma(cu, A::fma(C(4.5), cu, C(3)), base);
+        C o = A::fma(k.omega, A::fma(w, P, -g[i]), g[i]);
+        if (k.force) {
+            const C kw = sq(i) == 0 ? k.kw0 : (sq(i) == 1 ? k.kw1 : k.kw2);
+            o = A::fma(kw, A::fma(cF, A::fma(C(9), cu, C(3)), m3uF), o);
+        }
+        g[i] = o;
+    }
+}
+
+}  // namespace d3
+}  // namespace lbm

@@ -285,3 +285,37 @@ def batch_channels(ncases: int = 256, seed: int = 4, wmin: int = 64, wmax: int =
                             meta={"kind": ["cylinder", "square", "plate"][int(kind[c])],
                                   "size": s}))
     return out
+
+
+# ------------------------------------------------------------ D3Q19 inputs
+
+def porous_spheres(nx: int, ny: int, nz: int, seed: int, rmin: float = 4.0, rmax: float = 12.0,
+                   solid_fraction: float = 0.3) -> np.ndarray:
+    """3-D counterpart of porous_discs: random overlapping spheres on a
+    periodic box until the solid fraction is reached; mask[z, y, x]."""
+    m = np.zeros((nz, ny, nx), np.uint8)
+    rng = SplitMix64(seed, 5)
+    target = solid_fraction * nx * ny * nz
+    solid = 0
+    while solid < target:
+        batch = rng.uniform(4 * 256).reshape(256, 4)
+        for u, v, s, w in batch:
+            xc, yc, zc = u * nx, v * ny, s * nz
+            r = rmin + (rmax - rmin) * w
+            xs = np.arange(int(math.floor(xc - r)), int(math.ceil(xc + r)) + 1)
+            ys = np.arange(int(math.floor(yc - r)), int(math.ceil(yc + r)) + 1)
+            zs = np.arange(int(math.floor(zc - r)), int(math.ceil(zc + r)) + 1)
+            inside = ((xs[None, None, :] - xc) ** 2 + (ys[None, :, None] - yc) ** 2
+                      + (zs[:, None, None] - zc) ** 2) <= r * r
+            ix = np.ix_(zs % nz, ys % ny, xs % nx)
+            before = int(m[ix].sum())
+            m[ix] |= inside.astype(np.uint8)
+            solid += int(m[ix].sum()) - before
+            if solid >= target:
+                break
+    return m
+
+
+def ball(nx: int, ny: int, nz: int, xc: float, yc: float, zc: float, r: float) -> np.ndarray:
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx]
+    return (((x - xc) ** 2 + (y - yc) ** 2 + (z - zc) ** 2) <= r * r).astype(np.uint8)

@@ -66,6 +66,20 @@ class lbm_tuning(ctypes.Structure):
     ]
 
 
+class lbm3_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+        ("force", ctypes.c_double * 3),
+        ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32), ("bc_z", ctypes.c_int32),
+        ("layout", ctypes.c_int32), ("algo", ctypes.c_int32),
+        ("storage", ctypes.c_int32), ("rounding", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
 # Every symbol include/lbm.h declares, with (restype, argtypes).
 _P = ctypes.POINTER
 _vp, _i32, _i64, _u32, _u64, _dbl, _sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
@@ -101,6 +115,18 @@ SIGNATURES = {
     "lbm_batch_read_populations": (_i32, [_vp, _i32, _vp, _i32]),
     "lbm_batch_get_info": (_i32, [_vp, _P(_i64), _P(_i32), _P(_i64)]),
     "lbm_batch_destroy": (None, [_vp]),
+    "lbm3_workspace_bytes": (_i32, [_P(lbm3_params), _P(_sz)]),
+    "lbm3_create": (_i32, [_P(lbm3_params), _vp, _vp, _sz, _vp, _P(_vp)]),
+    "lbm3_init": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "lbm3_step": (_i32, [_vp, _i64, _u32]),
+    "lbm3_sync": (_i32, [_vp]),
+    "lbm3_read_moments": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "lbm3_read_populations": (_i32, [_vp, _vp, _i32]),
+    "lbm3_write_populations": (_i32, [_vp, _vp, _i32]),
+    "lbm3_mass": (_i32, [_vp, _P(_dbl)]),
+    "lbm3_get_info": (_i32, [_vp, _P(lbm_info)]),
+    "lbm3_destroy": (None, [_vp]),
+    "lbm3_layout_index": (_i64, [_i32, _i64, _i64, _i32]),
 }
 
 _lib = None
@@ -348,6 +374,94 @@ def lbm_batch_destroy(h):
 
 # ------------------------------------------------------------ convenience
 
+# ------------------------------------------------------------ D3Q19
+
+def make_params3(nx, ny, nz, tau, *, force=(0.0, 0.0, 0.0), bc=(PERIODIC,) * 3, layout="stream",
+                 algo="nptl", storage="f32", rounding="rne", seed=0, tile=(0, 0, 0),
+                 flags=0) -> lbm3_params:
+    """bc = (x, y, z), each PERIODIC or WALL."""
+    p = lbm3_params()
+    p.nx, p.ny, p.nz, p.tau = int(nx), int(ny), int(nz), float(tau)
+    for a in range(3):
+        p.force[a] = float(force[a])
+    p.bc_x, p.bc_y, p.bc_z = bc
+    p.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+    p.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    p.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
+    p.rounding = ROUNDINGS[rounding] if isinstance(rounding, str) else int(rounding)
+    p.seed = int(seed)
+    p.tile_x, p.tile_y, p.tile_z = tile
+    p.flags = int(flags)
+    return p
+
+
+def lbm3_workspace_bytes(p: lbm3_params) -> int:
+    b = ctypes.c_size_t()
+    _check(load().lbm3_workspace_bytes(ctypes.byref(p), ctypes.byref(b)), "lbm3_workspace_bytes")
+    return b.value
+
+
+def lbm3_create(p: lbm3_params, mask: np.ndarray, workspace, nbytes: int, stream: int):
+    m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    h = ctypes.c_void_p()
+    _check(load().lbm3_create(ctypes.byref(p), m.ctypes.data, _ptr(workspace), nbytes, stream,
+                              ctypes.byref(h)), "lbm3_create")
+    return h
+
+
+def lbm3_init(h, rho=None, ux=None, uy=None, uz=None):
+    arrs = [_f64(a) for a in (rho, ux, uy, uz)]
+    _check(load().lbm3_init(h, *[_ptr(a) for a in arrs]), "lbm3_init")
+
+
+def lbm3_step(h, nsteps: int, want_moments: bool = False):
+    _check(load().lbm3_step(h, int(nsteps), 1 if want_moments else 0), "lbm3_step")
+
+
+def lbm3_sync(h):
+    _check(load().lbm3_sync(h), "lbm3_sync")
+
+
+def lbm3_read_moments(h, N: int):
+    out = [np.empty(N) for _ in range(4)]
+    _check(load().lbm3_read_moments(h, *[a.ctypes.data for a in out]), "lbm3_read_moments")
+    return out
+
+
+def lbm3_read_populations(h, N: int, as_: str = "f64") -> np.ndarray:
+    out = np.empty((19, N), dtype=np.float64 if as_ == "f64" else np.float32)
+    _check(load().lbm3_read_populations(h, out.ctypes.data, STORAGES[as_]), "lbm3_read_populations")
+    return out
+
+
+def lbm3_write_populations(h, pops: np.ndarray):
+    a = np.ascontiguousarray(pops)
+    as_ = "f64" if a.dtype == np.float64 else "f32"
+    a = a.astype(np.float64 if as_ == "f64" else np.float32, copy=False)
+    _check(load().lbm3_write_populations(h, a.ctypes.data, STORAGES[as_]), "lbm3_write_populations")
+
+
+def lbm3_mass(h) -> float:
+    out = ctypes.c_double()
+    _check(load().lbm3_mass(h, ctypes.byref(out)), "lbm3_mass")
+    return out.value
+
+
+def lbm3_get_info(h) -> dict:
+    i = lbm_info()
+    _check(load().lbm3_get_info(h, ctypes.byref(i)), "lbm3_get_info")
+    return {f: getattr(i, f) for f, _ in lbm_info._fields_ if f != "reserved"}
+
+
+def lbm3_destroy(h):
+    load().lbm3_destroy(h)
+
+
+def lbm3_layout_index(layout, N: int, n: int, i: int) -> int:
+    lay = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+    return int(load().lbm3_layout_index(lay, int(N), int(n), int(i)))
+
+
 def _torch():
     import torch
     return torch
@@ -454,6 +568,61 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Lattice3:
+    """One D3Q19 lattice on the current CUDA device; workspace owned by a torch tensor."""
+
+    def __init__(self, nx, ny, nz, tau, mask=None, stream=None, **kw):
+        torch = _torch()
+        self.params = make_params3(nx, ny, nz, tau, **kw)
+        self.shape = (int(nz), int(ny), int(nx))
+        self.N = int(nx) * int(ny) * int(nz)
+        nbytes = lbm3_workspace_bytes(self.params)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.torch_stream = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = self.torch_stream.cuda_stream
+        if mask is None:
+            mask = np.zeros(self.N, np.uint8)
+        self.h = lbm3_create(self.params, mask, self.workspace, nbytes, self.stream)
+
+    def init(self, rho=None, ux=None, uy=None, uz=None):
+        lbm3_init(self.h, rho, ux, uy, uz)
+        return self
+
+    def step(self, n: int, moments: bool = False):
+        lbm3_step(self.h, n, moments)
+        return self
+
+    def sync(self):
+        lbm3_sync(self.h)
+        return self
+
+    def moments(self):
+        return lbm3_read_moments(self.h, self.N)
+
+    def populations(self, as_: str = "f64") -> np.ndarray:
+        return lbm3_read_populations(self.h, self.N, as_)
+
+    def write_populations(self, pops):
+        lbm3_write_populations(self.h, pops)
+
+    def mass(self) -> float:
+        return lbm3_mass(self.h)
+
+    def info(self) -> dict:
+        return lbm3_get_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm3_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -24,7 +24,7 @@ def declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*[\s\*]+(lbm_[A-Za-z0-9_]+)\s*\(",
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*[\s\*]+(lbm3?_[A-Za-z0-9_]+)\s*\(",
                              text, flags=re.M):
             names.add(m.group(1))
     return names
@@ -33,7 +33,7 @@ def declared_functions():
 def test_header_declares_the_abi():
     names = declared_functions()
     for core in ("lbm_create", "lbm_step", "lbm_read_moments", "lbm_force", "lbm_mass",
-                 "lbm_batch_create", "lbm_batch_step"):
+                 "lbm_batch_create", "lbm_batch_step", "lbm3_create", "lbm3_step", "lbm3_mass"):
         assert core in names
 
 
@@ -130,3 +130,43 @@ def test_aa_rejects_outflow_without_gpu(lib):
     one = lbm.lbm_workspace_bytes(lbm.make_params(100, 60, 0.8, algo="aa"))
     two = lbm.lbm_workspace_bytes(lbm.make_params(100, 60, 0.8, algo="nptl"))
     assert one < two - 9 * 100 * 60 * 4 + 4096          # one lattice, no buffer grid
+
+
+def test_d3q19_layout_maps_are_bijections_grouped_by_source_row(lib):
+    """Bundle layout in 3-D: the directions that pull from one source row
+    (equal c_y and c_z, derived here from the oracle's velocity table) are
+    stored side by side per node, groups in direction order."""
+    from oracle import directions3
+    c, _ = directions3()
+    for nx, ny, nz in [(1, 1, 1), (3, 2, 2), (5, 3, 4)]:
+        N = nx * ny * nz
+        n = np.arange(N)
+        groups = {}
+        for i in range(19):
+            groups.setdefault((int(c[i, 1]), int(c[i, 2])), []).append(i)
+        first = {i: g[0] for g in groups.values() for i in g}
+        size = {i: len(g) for g in groups.values() for i in g}
+        for name in ("stream", "bundle", "collision"):
+            offs = np.array([[lbm.lbm3_layout_index(name, N, k, i) for k in range(N)] for i in range(19)])
+            assert sorted(offs.ravel().tolist()) == list(range(19 * N)), name
+            for i in range(19):
+                if name == "stream":
+                    exp = i * N + n
+                elif name == "collision":
+                    exp = 19 * n + i
+                else:
+                    exp = first[i] * N + size[i] * n + (i - first[i])
+                assert (offs[i] == exp).all(), (name, i)
+    assert lbm.lbm3_layout_index("bundle", 4, 0, 19) == -1
+
+
+def test_d3q19_params_checked_without_gpu(lib):
+    ok = lbm.lbm3_workspace_bytes(lbm.make_params3(16, 8, 4, 0.8, storage="f32"))
+    assert ok >= 2 * 19 * 16 * 8 * 4 * 4
+    for bad in (dict(tau=0.5), dict(bc=(lbm.FREESLIP, lbm.PERIODIC, lbm.PERIODIC)),
+                dict(algo="npol"), dict(tile=(32, 8, 4))):
+        kw = dict(tau=0.8)
+        kw.update(bad)
+        tau = kw.pop("tau")
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm3_workspace_bytes(lbm.make_params3(16, 8, 4, tau, **kw))

@@ -1,0 +1,297 @@
+"""D3Q19 lattices (the 3-D extension of Sec. 6) through the lbm3_* C ABI,
+against the FP64 D3Q19 oracle.
+
+Bars:
+  * FP64 GPU vs FP64 oracle: relative L-inf <= 1e-12 on populations and
+    velocities, 1e-14 on density (rounding order only).
+  * Every layout x algorithm x tile shape: bit-identical at equal storage.
+  * omega = 0: bit-exact cyclic shift by T c_i.
+  * A z-invariant D3Q19 flow summed over c_z is the D2Q9 update: checked
+    against the 2-D oracle.
+  * Full size (4.6 M nodes, FP32): sampled nodes against the oracle run on
+    their 3x3x3 neighbourhood, which determines one update exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2607_20650_gb300 import geometry as G
+from tests.gpu_helpers import rel_linf
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2607_20650_gb300 import lbm  # noqa: E402
+
+LAYOUTS = ("stream", "bundle", "collision")
+ALGOS = ("lptl", "nptl")
+P, W = lbm.PERIODIC, lbm.WALL
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2607_20650_gb300 import build
+    build.build()
+    lbm.load()
+
+
+class Spec3:
+    def __init__(self, nx, ny, nz, tau, mask, bc, force=(0.0, 0.0, 0.0), seed=1, amp=0.02):
+        self.nx, self.ny, self.nz, self.tau = nx, ny, nz, tau
+        self.mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        self.bc, self.force = bc, force
+        N = nx * ny * nz
+        r = G.SplitMix64(seed, 11)
+        solid = self.mask > 0
+        self.rho0 = np.where(solid, 1.0, 1.0 + r.uniform(N, -0.01, 0.01))
+        self.u0 = [np.where(solid, 0.0, r.uniform(N, -amp, amp)) for _ in range(3)]
+
+    def oracle(self):
+        c = O.Case3(self.nx, self.ny, self.nz, self.tau, *self.force, *self.bc)
+        return O.Lattice3(c, self.mask, self.rho0, *self.u0)
+
+    def gpu(self, **kw):
+        lat = lbm.Lattice3(self.nx, self.ny, self.nz, self.tau, self.mask, force=self.force,
+                           bc=self.bc, **kw)
+        lat.init(self.rho0, *self.u0)
+        return lat
+
+
+def specs():
+    out = {}
+    nx, ny, nz = 37, 21, 13
+    out["porous"] = Spec3(nx, ny, nz, 0.7, G.porous_spheres(nx, ny, nz, 5, 2.0, 5.0, 0.25), (P, P, P),
+                          force=(1e-5, 2e-6, -1e-6))
+    nx, ny, nz = 45, 19, 11
+    out["duct"] = Spec3(nx, ny, nz, 0.9, G.ball(nx, ny, nz, 12.0, 9.0, 5.0, 3.5), (P, W, W),
+                        force=(1e-5, 0.0, 0.0), seed=2)
+    nx, ny, nz = 33, 5, 3
+    m = np.zeros((nz, ny, nx), np.uint8)
+    m[1, 2, 7] = 1
+    out["ragged"] = Spec3(nx, ny, nz, 0.6, m, (W, P, W), seed=3)
+    return out
+
+
+SPECS = specs()
+
+
+@pytest.mark.parametrize("case", list(SPECS))
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("algo", ALGOS)
+def test_fp64_matches_oracle3(case, layout, algo):
+    spec = SPECS[case]
+    T = 40
+    ref = spec.oracle().run(T)
+    lat = spec.gpu(layout=layout, algo=algo, storage="f64")
+    lat.step(T, moments=True).sync()
+    h = lat.populations("f64")
+    rho, ux, uy, uz = lat.moments()
+    fl = ref.solid == 0
+    assert rel_linf(h, ref.h, fl) <= 1e-12
+    assert rel_linf(rho, ref.rho, fl) <= 1e-14
+    assert rel_linf(np.stack([ux, uy, uz]), np.stack([ref.ux, ref.uy, ref.uz]), fl) <= 1e-12
+    assert np.all(h[:, ~fl] == 0.0)
+    assert np.all(rho[~fl] == 1.0) and np.all(ux[~fl] == 0.0) and np.all(uz[~fl] == 0.0)
+    assert abs(lat.mass() - np.sum(1.0 + ref.h[:, fl].sum(axis=0))) <= 1e-13 * fl.sum()
+    info = lat.info()
+    assert info["fluid_cells"] == int(fl.sum()) and info["steps"] == T
+    lat.close()
+
+
+@pytest.mark.parametrize("storage,rounding", [("f64", "rne"), ("f32", "rne"), ("f16s", "rne"),
+                                              ("f16s", "sr"), ("bf16s", "rne"), ("bf16s", "sr")])
+def test_all_layouts_algorithms_and_tiles_bit_identical(storage, rounding):
+    spec = SPECS["porous"]
+    T = 70   # one graph of 64 updates plus single launches
+    base = None
+    for layout in LAYOUTS:
+        for algo, tile in (("lptl", (0, 0, 0)), ("nptl", (32, 4, 2)), ("nptl", (8, 8, 8)),
+                           ("nptl", (16, 2, 1))):
+            lat = spec.gpu(layout=layout, algo=algo, tile=tile, storage=storage, rounding=rounding,
+                           seed=99)
+            lat.step(T, moments=True).sync()
+            got = (lat.populations("f64"), *lat.moments())
+            lat.close()
+            if base is None:
+                base = got
+            else:
+                for a, b in zip(got, base):
+                    assert np.array_equal(a, b, equal_nan=False), (layout, algo, tile)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_pure_streaming_is_bit_exact_shift3(layout, algo, storage):
+    nx, ny, nz, T = 23, 9, 7, 5
+    N = nx * ny * nz
+    rng = np.random.default_rng(4)
+    h0 = rng.normal(0.0, 0.01, size=(19, N))
+    if storage == "f32":
+        h0 = h0.astype(np.float32).astype(np.float64)
+    lat = lbm.Lattice3(nx, ny, nz, math.inf, None, layout=layout, algo=algo, storage=storage,
+                       tile=(8, 4, 2))
+    lat.write_populations(h0)
+    lat.step(T).sync()
+    h = lat.populations("f64")
+    c, _ = O.directions3()
+    for i in range(19):
+        exp = np.roll(h0[i].reshape(nz, ny, nx), (T * c[i, 2], T * c[i, 1], T * c[i, 0]),
+                      axis=(0, 1, 2)).ravel()
+        assert np.array_equal(h[i], exp), i
+    lat.close()
+
+
+def test_fp32_close_to_oracle3():
+    """FP32 arithmetic and storage after 200 updates: relative L-inf error on
+    rho and v below 1e-5, the bar the 2-D path meets."""
+    spec = SPECS["duct"]
+    T = 200
+    ref = spec.oracle().run(T)
+    lat = spec.gpu(layout="bundle", algo="nptl", storage="f32")
+    lat.step(T, moments=True).sync()
+    rho, ux, uy, uz = lat.moments()
+    fl = ref.solid == 0
+    assert rel_linf(rho, ref.rho, fl) <= 1e-5
+    assert rel_linf(np.stack([ux, uy, uz]), np.stack([ref.ux, ref.uy, ref.uz]), fl) <= 1e-5
+    lat.close()
+
+
+def test_z_invariant_flow_projects_to_d2q9_oracle():
+    """Summing a z-invariant D3Q19 state over c_z gives D2Q9 populations with
+    the D2Q9 weights (4/9, 1/9, 1/36), and one D3Q19 update of the state is
+    one D2Q9 update of the sum: checked against the 2-D oracle."""
+    nx, ny, nz, T = 29, 17, 4, 30
+    m2 = G.disc(nx, ny, 10.0, 8.0, 3.0)
+    r = G.SplitMix64(8, 3)
+    ux0 = np.where(m2.ravel() > 0, 0.0, r.uniform(nx * ny, -0.02, 0.02))
+    uy0 = np.where(m2.ravel() > 0, 0.0, r.uniform(nx * ny, -0.02, 0.02))
+    force = (2e-5, -1e-5)
+    ref = O.Lattice(O.Case(nx, ny, 0.8, fx=force[0], fy=force[1], bc_w=P, bc_e=P, bc_s=W, bc_n=W),
+                    m2, ux=ux0, uy=uy0).run(T)
+    m3 = np.broadcast_to(m2.reshape(1, ny, nx), (nz, ny, nx)).copy()
+    lat = lbm.Lattice3(nx, ny, nz, 0.8, m3, force=(*force, 0.0), bc=(P, W, P), storage="f64",
+                       layout="bundle", algo="nptl")
+    lat.init(None, np.tile(ux0, nz), np.tile(uy0, nz), None)
+    lat.step(T, moments=True).sync()
+    h3 = lat.populations("f64").reshape(19, nz, ny * nx)
+    c, _ = O.directions3()
+    h2 = np.zeros((9, ny * nx))
+    for i in range(19):
+        j = (c[i, 1] + 1) * 3 + (c[i, 0] + 1)   # D2Q9 index of (c_x, c_y)
+        h2[j] += h3[i, 0]
+    assert np.all(h3 == h3[:, :1])                # stays z-invariant, bit for bit
+    fl = ref.solid == 0
+    assert rel_linf(h2, ref.h, fl) <= 1e-12
+    rho, ux, uy, uz = lat.moments()
+    assert rel_linf(ux[: nx * ny], ref.ux, fl) <= 1e-12
+    # v_z sums the c_z = +1 values minus the c_z = -1 ones in direction order:
+    # equal pairs cancel only up to the rounding of the partial sums
+    assert np.max(np.abs(uz)) <= 1e-14 * np.max(np.abs(ux))
+    lat.close()
+
+
+def _effective_solid(mask3, bc):
+    """Solid mask plus fluid nodes whose 18 pulls all bounce (any size; numpy)."""
+    c, _ = O.directions3()
+    solid = mask3 > 0
+    nz, ny, nx = mask3.shape
+    open_ = np.zeros_like(solid)
+    for i in range(19):
+        if i == 9:
+            continue
+        src = np.roll(solid, (c[i, 2], c[i, 1], c[i, 0]), axis=(0, 1, 2))  # solid[r - c_i]
+        ok = ~src
+        for a, (ext, shape_axis) in enumerate(((nx, 2), (ny, 1), (nz, 0))):
+            if bc[a] == W and c[i, a] != 0:
+                edge = [slice(None)] * 3
+                edge[shape_axis] = 0 if c[i, a] > 0 else ext - 1
+                ok[tuple(edge)] = False
+        open_ |= ok
+    return solid | ~open_
+
+
+def test_full_size_sampled_nodes_match_oracle_neighbourhood():
+    """4.6 M-node porous box, FP32 bundle NPTL: after 3 updates, one further
+    update of sampled nodes equals the oracle's update of their 3x3x3
+    neighbourhood (decoded FP32 state, effective solid flags of the whole
+    lattice) within FP32 rounding; NPTL, LPTL and the collision layout agree
+    bit for bit at this size."""
+    nx, ny, nz = 192, 160, 150
+    N = nx * ny * nz
+    mask = G.porous_spheres(nx, ny, nz, 7, 3.0, 9.0, 0.3)
+    bc = (P, P, W)
+    force = (1e-5, 0.0, 0.0)
+    kw = dict(force=force, bc=bc, storage="f32")
+    lat = lbm.Lattice3(nx, ny, nz, 0.8, mask, layout="bundle", algo="nptl", **kw)
+    r = G.SplitMix64(12, 1)
+    u0 = [np.where(mask.ravel() > 0, 0.0, r.uniform(N, -0.03, 0.03)) for _ in range(3)]
+    lat.init(None, *u0).step(3).sync()
+    h3 = lat.populations("f64")
+    lat.step(1, moments=True).sync()
+    h4 = lat.populations("f64")
+    other = {}
+    for layout, algo in (("bundle", "lptl"), ("collision", "nptl"), ("stream", "nptl")):
+        o = lbm.Lattice3(nx, ny, nz, 0.8, mask, layout=layout, algo=algo, **kw)
+        o.init(None, *u0).step(4).sync()
+        other[(layout, algo)] = o.populations("f32")
+        o.close()
+    for key, v in other.items():
+        assert np.array_equal(v.astype(np.float64), h4), key
+    eff = _effective_solid(mask, bc)
+    rs = G.SplitMix64(13, 2)
+    xs, ys, zs = rs.integers(64, 0, nx - 1), rs.integers(64, 0, ny - 1), rs.integers(64, 0, nz - 1)
+    checked = 0
+    for x, y, z in zip(xs, ys, zs):
+        x, y, z = int(x), int(y), int(z)
+        if eff[z, y, x]:
+            continue
+        zi = [(z + d) for d in (-1, 0, 1)]
+        if any(q < 0 or q >= nz for q in zi):
+            continue   # the oracle box would wrap a wall axis: sample interior planes only
+        yi = [(y + d) % ny for d in (-1, 0, 1)]
+        xi = [(x + d) % nx for d in (-1, 0, 1)]
+        sub_m = eff[np.ix_(zi, yi, xi)].astype(np.uint8)
+        idx = (np.array(zi)[:, None, None] * ny + np.array(yi)[None, :, None]) * nx + np.array(xi)[None, None, :]
+        sub_h = h3[:, idx.ravel()]
+        ref = O.Lattice3(O.Case3(3, 3, 3, 0.8, *force, P, P, P), sub_m)
+        ref.set_h(sub_h)
+        ref.run(1)
+        n = (z * ny + y) * nx + x
+        got, exp = h4[:, n], ref.h[:, 13]
+        assert np.max(np.abs(got - exp)) <= 2e-6 * max(np.max(np.abs(exp)), 1e-3), (x, y, z)
+        checked += 1
+    assert checked >= 20
+    lat.close()
+
+
+def test_graphs_match_single_launches3():
+    spec = SPECS["duct"]
+    a = spec.gpu(layout="stream", algo="nptl", storage="f32")
+    b = spec.gpu(layout="stream", algo="nptl", storage="f32", flags=lbm.LBM_FLAG_NO_GRAPH)
+    a.step(130).step(3, moments=True).sync()
+    b.step(133, moments=True).sync()
+    assert np.array_equal(a.populations("f32"), b.populations("f32"))
+    assert all(np.array_equal(u, v) for u, v in zip(a.moments(), b.moments()))
+    a.close()
+    b.close()
+
+
+def test_divergence_is_reported3():
+    spec = SPECS["ragged"]
+    lat = lbm.Lattice3(spec.nx, spec.ny, spec.nz, 0.51, spec.mask, bc=spec.bc, storage="f32",
+                       layout="collision", algo="lptl")
+    h = np.zeros((19, spec.nx * spec.ny * spec.nz))
+    h[3, 5] = np.inf
+    lat.write_populations(h)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.step(2).sync()
+    assert e.value.status == lbm.LBM_EDIVERGED
+    lat.write_populations(np.zeros_like(h))   # the report cleared the flag; the lattice stays usable
+    lat.step(1).sync()
+    lat.close()
