@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--layout", default="bundle", choices=["stream", "bundle", "collision"])
     ap.add_argument("--algo", default="nptl", choices=["lptl", "nptl", "npol", "nsol", "aa"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s", "f64"])
+    ap.add_argument("--lattice", default="d2q9", choices=["d2q9", "d3q19"],
+                    help="d3q19: time only the 3-D extension on an n3^3 sphere packing")
+    ap.add_argument("--n3", type=int, default=384)
+    ap.add_argument("--geo3", default="porous", choices=["porous", "fluid"])
     return ap.parse_args()
 
 
@@ -135,6 +139,15 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def smi_id(torch, local: int) -> str:
+    """nvidia-smi id (UUID) of the CUDA device the process uses."""
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = str(getattr(props, "uuid", local))
+    if gpu_id and not gpu_id.startswith("GPU-") and "-" in gpu_id:
+        gpu_id = "GPU-" + gpu_id
+    return gpu_id
 
 
 def max_over_ranks(value: float, device: str) -> float:
@@ -267,12 +280,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    props = torch.cuda.get_device_properties(local)
-    gpu_id = str(getattr(props, "uuid", local))
-    if gpu_id and not gpu_id.startswith("GPU-") and "-" in gpu_id:
-        gpu_id = "GPU-" + gpu_id
     barrier()
-    clk = Clocks(gpu_id)
+    clk = Clocks(smi_id(torch, local))
     dt = time_steps(lat, args.steps, torch)
     clocks = clk.stop()
     barrier()
@@ -312,6 +321,7 @@ def run_ours(args):
     if not args.no_variants:
         result["variants"] = variants(args, mask, torch, world)
         result["batched"] = batched(args, torch)
+        result["d3q19"] = d3q19(args, torch)
     result["e2e"] = e2e(args, mask, torch)
     if rank == 0 and not args.no_cpu and world == 1:
         result["cpu_baseline"] = cpu_sample()
@@ -356,6 +366,94 @@ def variants(args, mask, torch, world):
                      "frac_of_measured_hbm": info["bytes_per_update"] / (dt / k) / 1e9 / hbm,
                      "bytes_per_update": info["bytes_per_update"],
                      "workspace_GB": info["workspace_bytes"] / 1e9, "steps": k}
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_d3q19(args):
+    """One JSON line for the 3-D extension alone (profiling and sweeps):
+    n3^3 periodic sphere packing or all-fluid box, --layout/--algo/--storage,
+    --tile as AxBxC (default 128x1x1)."""
+    import torch
+    from paper_2607_20650_gb300 import build, geometry as G, lbm
+    build.build()
+    lbm.load()
+    n = args.n3
+    N = n ** 3
+    tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else (128, 1, 1)
+    mask = G.porous_spheres(n, n, n, 3, 4.0, 12.0, 0.3)
+    if args.geo3 == "fluid":
+        mask = np.zeros_like(mask)
+    stream = torch.cuda.Stream()
+    lat = lbm.Lattice3(n, n, n, 0.8, mask, stream=stream, force=(1e-6, 0.0, 0.0), layout=args.layout,
+                       algo=args.algo, storage=args.storage, tile=tile)
+    info = lat.info()
+    lat.step(args.warmup).sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    clk = Clocks(smi_id(torch, torch.cuda.current_device()))
+    e0.record(stream)
+    lbm.lbm3_step(lat.h, args.steps, False)
+    e1.record(stream)
+    e1.synchronize()
+    clocks = clk.stop()
+    lat.sync()
+    dt = e0.elapsed_time(e1) / 1e3
+    hbm, peak_kind = peaks()
+    achieved = info["bytes_per_update"] / (dt / args.steps) / 1e9
+    print(json.dumps({
+        "metric": "D3Q19 BGK MLUPS", "value": N * args.steps / dt / 1e6, "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+        "data": "synthetic",
+        "config": {"workload": f"{n}^3 {args.geo3} box (spheres r 4-12, phi 0.3, seed 3), periodic, "
+                               f"g_x 1e-6, tau 0.8", "layout": args.layout, "algo": args.algo,
+                   "tile": "x".join(map(str, tile)), "fluid_nodes": info["fluid_cells"]},
+        "gpu_launches": launches_for(args.steps),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": info["bytes_per_update"]},
+        "clocks": clocks}))
+    lat.close()
+
+
+def d3q19(args, torch):
+    """The 3-D extension: a 384^3 periodic box of random overlapping spheres
+    (radii 4-12, solid fraction 0.3, seed 3; tau 0.8, g_x = 1e-6) and the
+    same box all fluid, through the lbm3_* C ABI. Algorithmic bytes per
+    update: fluid nodes x 2 x 19 x sizeof(storage) + 4 link bytes per node."""
+    from paper_2607_20650_gb300 import geometry as G, lbm
+    n = 384
+    N = n ** 3
+    k = max(20, min(args.steps, 200))
+    porous = G.porous_spheres(n, n, n, 3, 4.0, 12.0, 0.3)
+    hbm, _ = peaks()
+    out = {"workload": f"{n}^3 periodic box, spheres r 4-12, solid fraction {porous.mean():.3f}"}
+    for name, geo, kw in [("f32_bundle_nptl_128x1x1_porous", "porous", dict(storage="f32", layout="bundle")),
+                          ("f32_bundle_nptl_128x1x1_allfluid", "fluid", dict(storage="f32", layout="bundle")),
+                          ("f32_stream_nptl_128x1x1_porous", "porous", dict(storage="f32", layout="stream")),
+                          ("f32_collision_nptl_128x1x1_porous", "porous", dict(storage="f32", layout="collision")),
+                          ("f16s_rne_bundle_nptl_128x1x1_porous", "porous", dict(storage="f16s", layout="bundle"))]:
+        m = porous if geo == "porous" else np.zeros_like(porous)
+        stream = torch.cuda.Stream()
+        lat = lbm.Lattice3(n, n, n, 0.8, m, stream=stream, force=(1e-6, 0.0, 0.0), algo="nptl",
+                           tile=(128, 1, 1), **kw)
+        info = lat.info()
+        lat.step(args.warmup).sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lbm.lbm3_step(lat.h, k, False)
+        e1.record(stream)
+        e1.synchronize()
+        lat.sync()
+        dt = e0.elapsed_time(e1) / 1e3
+        gbs = info["bytes_per_update"] / (dt / k) / 1e9
+        out[name] = {"MLUPS": N * k / dt / 1e6, "ms_per_step": dt / k * 1e3, "GBps_algorithmic": gbs,
+                     "frac_of_measured_hbm": gbs / hbm, "bytes_per_update": info["bytes_per_update"],
+                     "fluid_nodes": info["fluid_cells"], "steps": k}
         lat.close()
         del lat
         torch.cuda.empty_cache()
@@ -464,6 +562,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.lattice == "d3q19":
+        run_d3q19(args)
     else:
         run_ours(args)
 

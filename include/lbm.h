@@ -111,6 +111,8 @@ typedef enum {
                                               y + tile_y/2) */
 #define LBM_FLAG_NO_STAGING 0x4u  /* NPTL, collision layout: no shared-memory staging of
                                      row spans (default when tile_x % 32 == 0) */
+#define LBM_FLAG_WIDE_OFFSETS 0x8u  /* D3Q19: 64-bit addressing for every pull, the path
+                                       lattices too large for 32-bit offset tables take */
 
 typedef struct lbm_params {
     int32_t nx, ny;          /* lattice size; nx*ny < 2^32 */
@@ -282,7 +284,7 @@ void lbm_batch_destroy(lbm_batch *B);
  * {0}, {1,2,3}, {4}, {5,6,7}, {8,9,10}, {11,12,13}, {14}, {15,16,17}, {18},
  * a group of size s starting at direction b stored at b N + s n + (i - b).
  * Algorithms: LPTL and NPTL (3-D tiles tile_x * tile_y * tile_z <= 512,
- * 0,0,0 = 32 x 4 x 2; tile_z <= 64); two lattices. Faces per axis: PERIODIC or WALL
+ * 0,0,0 = 128 x 1 x 1; tile_z <= 64); two lattices. Faces per axis: PERIODIC or WALL
  * (half-way bounce-back); solid mask nodes bounce back; a fluid node whose
  * 18 pulls all bounce is treated as solid. Storage, rounding, Guo force,
  * graphs and errors as in 2-D. Workspace: 2 x 19 N elements, 4 N bytes of
@@ -295,7 +297,7 @@ typedef struct lbm3_params {
     int32_t layout, algo, storage, rounding;   /* algo: LBM_LPTL or LBM_NPTL */
     uint64_t seed;
     int32_t tile_x, tile_y, tile_z;
-    uint32_t flags;          /* LBM_FLAG_NO_GRAPH */
+    uint32_t flags;          /* LBM_FLAG_NO_GRAPH, LBM_FLAG_WIDE_OFFSETS */
 } lbm3_params;
 
 typedef struct lbm3_lattice lbm3_lattice;

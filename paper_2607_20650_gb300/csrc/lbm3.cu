@@ -60,7 +60,18 @@ struct Step3 {
     uint64_t seed;
     int tx, ty, tz;
     uint64_t nx_magic, nxy_magic;   // ceil(2^64 / nx), ceil(2^64 / (nx ny)); 0 for 1
+    int zero_fill;                  // lanes of a warp hold consecutive nodes
+    // 32-bit element offsets from the base of direction i at node n (base =
+    // lattice + mult3(i) n): own slot, interior pull, bounced pull.
+    int32_t os[Q], op[Q], ob[Q];
 };
+
+// Node stride of direction i's array in a layout: 1 (stream; one-direction
+// bundles), 3 (three-direction bundles), 19 (collision).
+template <int L>
+__host__ __device__ constexpr uint32_t mult3(int i) {
+    return L == STREAM ? 1u : (L == COLLISION ? 19u : (uint32_t)bundle_size(i));
+}
 
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, uint64_t magic) {
     return magic ? (uint32_t)__umul64hi((unsigned long long)n, magic) : n;
@@ -96,17 +107,51 @@ __global__ void k3_count(const uint32_t *links, uint32_t N, unsigned long long *
     if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
 }
 
+#ifndef LBM3_ST_HINT
+#define LBM3_ST_HINT 0   // 0 plain stores (measured fastest here), 1 streaming (.cs), 2 .cs for BUNDLE
+#endif
 template <class S, int L>
-__device__ __forceinline__ void node3(const Step3<S> &a, uint32_t x, uint32_t y, uint32_t z) {
-    using C = typename Codec<S>::C;
-    using A = Ar<C>;
+__device__ __forceinline__ void st3(S *p, S v) {
+    if (LBM3_ST_HINT == 1 || (LBM3_ST_HINT == 2 && L == BUNDLE))
+        __stcs(p, v);
+    else
+        *p = v;
+}
+
+// Pulled values of fluid node n at (x, y, z) with link word lk: the
+// neighbour's value, or the node's own opposite slot for a bounced link.
+template <class S, int L, bool OFF32>
+__device__ __forceinline__ void pull3(const Step3<S> &a, uint32_t x, uint32_t y, uint32_t z, uint32_t n,
+                                      uint32_t lk, typename Codec<S>::C *g) {
     const uint32_t nx = (uint32_t)a.g.nx, ny = (uint32_t)a.g.ny, nz = (uint32_t)a.g.nz;
-    const uint32_t n = (z * ny + y) * nx + x;
-    const uint32_t lk = a.links[n];
-    if (lk == SOLID) return;
     const S *__restrict__ src = a.src;
     const bool interior = (x - 1u < nx - 2u) && (y - 1u < ny - 2u) && (z - 1u < nz - 2u);
-    C g[Q];
+    if (OFF32) {
+        // Node-index corrections of a pull that leaves the box through a
+        // periodic face (walls bounce, so their corrections go unused):
+        // c = +1 pulls from coordinate -1 at the low face, c = -1 from the
+        // extent at the high face.
+        const int N = (int)a.N, nxy = (int)(nx * ny);
+        const int xlo = x == 0 ? (int)nx : 0, xhi = x == nx - 1 ? -(int)nx : 0;
+        const int ylo = y == 0 ? nxy : 0, yhi = y == ny - 1 ? -nxy : 0;
+        const int zlo = z == 0 ? N : 0, zhi = z == nz - 1 ? -N : 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const S *b = src + mult3<L>(i) * n;
+            int o;
+            if (i == REST) {
+                o = a.os[i];
+            } else if ((lk >> bit(i)) & 1u) {
+                o = a.ob[i];
+            } else {
+                const int w = (cx(i) > 0 ? xlo : cx(i) < 0 ? xhi : 0) + (cy(i) > 0 ? ylo : cy(i) < 0 ? yhi : 0) +
+                              (cz(i) > 0 ? zlo : cz(i) < 0 ? zhi : 0);
+                o = a.op[i] + (int)mult3<L>(i) * w;
+            }
+            g[i] = Codec<S>::dec(b[o]);
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         uint32_t s = n;
@@ -122,6 +167,13 @@ __device__ __forceinline__ void node3(const Step3<S> &a, uint32_t x, uint32_t y,
         }
         g[i] = Codec<S>::dec(src[addr<L>(a.N, s, j)]);
     }
+}
+
+// Collision, moments and the encoded stores of node n.
+template <class S, int L, bool OFF32>
+__device__ __forceinline__ void finish3(const Step3<S> &a, uint32_t n, typename Codec<S>::C *g) {
+    using C = typename Codec<S>::C;
+    using A = Ar<C>;
     C drho, ux, uy, uz;
     collide3(a.k, g, drho, ux, uy, uz);
     if (!isfinite(drho)) atomicOr(a.err, 1u);
@@ -135,27 +187,74 @@ __device__ __forceinline__ void node3(const Step3<S> &a, uint32_t x, uint32_t y,
     uint32_t nk = 0;
     if (sr) nk = node_key(step_key(a.seed, (uint32_t)(*a.tctr + a.toff)), n);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) a.dst[addr<L>(a.N, n, i)] = Codec<S>::enc(g[i], sr, sr ? pop_rand(nk, i) : 0u);
+    for (int i = 0; i < Q; ++i) {
+        S *p = OFF32 ? a.dst + (mult3<L>(i) * n + (uint32_t)a.os[i]) : a.dst + addr<L>(a.N, n, i);
+        st3<S, L>(p, Codec<S>::enc(g[i], sr, sr ? pop_rand(nk, i) : 0u));
+    }
 }
 
-template <class S, int L, bool LINEAR>
+// Solid nodes hold zeros in both lattices and are not rewritten, except
+// where their slots share a 32-byte sector with a fluid node's slots: there
+// zeros complete the sector so that it is written whole instead of being
+// read, merged and written back. F: ballot of fluid lanes, lanes holding
+// consecutive nodes. Stream: aligned groups of 32/sizeof(S) nodes; bundle:
+// those groups (single-direction bundles) and the lanes within
+// ceil(32 / (3 sizeof(S))) (three-direction bundles); collision: +-1 lane.
+template <class S, int L>
+__device__ __forceinline__ bool shares3(unsigned F, int lane) {
+    constexpr int G = (int)(32 / sizeof(S)) < 32 ? (int)(32 / sizeof(S)) : 32;
+    const unsigned grp = G >= 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(G - 1));
+    constexpr int k = L == COLLISION ? 1 : (int)((32 + 3 * sizeof(S) - 1) / (3 * sizeof(S)));
+    const int lo = lane - k < 0 ? 0 : lane - k;
+    const int hi = lane + k > 31 ? 31 : lane + k;
+    const int w = hi - lo + 1;
+    const unsigned near = w >= 32 ? 0xffffffffu : ((1u << w) - 1u) << lo;
+    const unsigned m = L == STREAM ? grp : (L == BUNDLE ? (grp | near) : near);
+    return (F & m) != 0u;
+}
+
+template <class S, int L>
+__device__ __forceinline__ void zero3(const Step3<S> &a, uint32_t n) {
+    const S z = Codec<S>::enc(typename Codec<S>::C(0), false, 0u);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st3<S, L>(a.dst + addr<L>(a.N, n, i), z);
+}
+
+// LINEAR: one node per thread over n (LPTL); otherwise 3-D tiles (NPTL).
+// OFF32: 19 N fits 31 bits, pulls of interior nodes use the offset tables.
+template <class S, int L, bool LINEAR, bool OFF32>
 __global__ void __launch_bounds__(512) k3_step(const Step3<S> a) {
+    using C = typename Codec<S>::C;
+    const uint32_t nx = (uint32_t)a.g.nx, ny = (uint32_t)a.g.ny, nz = (uint32_t)a.g.nz;
     uint32_t x, y, z;
     if (LINEAR) {
         const uint64_t n64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
         if (n64 >= a.N) return;
         const uint32_t n = (uint32_t)n64;
         z = fdiv(n, a.nxy_magic);
-        const uint32_t r = n - z * (uint32_t)a.g.nx * (uint32_t)a.g.ny;
+        const uint32_t r = n - z * nx * ny;
         y = fdiv(r, a.nx_magic);
-        x = r - y * (uint32_t)a.g.nx;
+        x = r - y * nx;
     } else {
         x = blockIdx.x * a.tx + threadIdx.x;
         y = blockIdx.y * a.ty + threadIdx.y;
         z = blockIdx.z * a.tz + threadIdx.z;
-        if (x >= (uint32_t)a.g.nx || y >= (uint32_t)a.g.ny || z >= (uint32_t)a.g.nz) return;
+        if (x >= nx || y >= ny || z >= nz) return;
     }
-    node3<S, L>(a, x, y, z);
+    const uint32_t n = (z * ny + y) * nx + x;
+    const uint32_t lk = a.links[n];
+    const bool f = lk != SOLID;
+#ifndef LBM3_NO_ZERO_FILL
+    if (a.zero_fill) {
+        const int lane = (int)(((threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x) & 31u);
+        const unsigned F = __ballot_sync(__activemask(), f);
+        if (!f && shares3<S, L>(F, lane)) zero3<S, L>(a, n);
+    }
+#endif
+    if (!f) return;
+    C g[Q];
+    pull3<S, L, OFF32>(a, x, y, z, n, lk, g);
+    finish3<S, L, OFF32>(a, n, g);
 }
 
 template <class S, int L>
@@ -276,7 +375,7 @@ lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
     pl->N = (int64_t)N;
     if (p->algo == LBM_NPTL) {
         int tx = p->tile_x, ty = p->tile_y, tz = p->tile_z;
-        if (tx == 0 && ty == 0 && tz == 0) { tx = 32; ty = 4; tz = 2; }
+        if (tx == 0 && ty == 0 && tz == 0) { tx = 128; ty = 1; tz = 1; }
         if (tx < 1 || ty < 1 || tz < 1 || tz > 64 || (int64_t)tx * ty * tz > 512)
             return lbm_fail(LBM_EINVAL, "tile must be positive, tile_z <= 64, tile_x*tile_y*tile_z <= 512");
         pl->tx = tx; pl->ty = ty; pl->tz = tz;
@@ -302,6 +401,25 @@ lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
 
 uint64_t magic(uint64_t d) { return d <= 1 ? 0ull : (~0ull / d) + 1ull; }
 
+// Element offsets of the kernels' 32-bit tables: own slot, bounced pull and
+// interior pull plus the largest periodic-face correction, per direction.
+bool offsets_fit(const lbm3_params *p, int64_t N) {
+    const int64_t nx = p->nx, nxy = (int64_t)p->nx * p->ny, lim = (1ll << 31) - 64;
+    for (int i = 0; i < 19; ++i) {
+        const int ax = std::abs(lbm::d3::cx(i)), ay = std::abs(lbm::d3::cy(i)), az = std::abs(lbm::d3::cz(i));
+        const int64_t d = lbm::d3::cz(i) * nxy + lbm::d3::cy(i) * nx + lbm::d3::cx(i);
+        int64_t self, mul;
+        if (p->layout == LBM_LAYOUT_STREAM) { self = i * N; mul = 1; }
+        else if (p->layout == LBM_LAYOUT_COLLISION) { self = i; mul = 19; }
+        else { self = lbm::d3::bundle_first(i) * N + (i - lbm::d3::bundle_first(i)); mul = lbm::d3::bundle_size(i); }
+        const int64_t wrap = mul * (az * N + ay * nxy + ax * nx);
+        const int64_t pull = self - mul * d;
+        if (self > lim || pull + wrap > lim || pull - wrap < -lim) return false;
+        if (mul * N > lim) return false;   // mult * n itself stays 32-bit
+    }
+    return true;
+}
+
 }  // namespace
 
 struct lbm3_lattice {
@@ -313,6 +431,7 @@ struct lbm3_lattice {
     int64_t steps;
     int64_t fluid;
     int block_1d;
+    int off32;   // 32-bit offset tables usable (19 N and the pull shifts fit 31 bits)
     cudaGraphExec_t graph[2];
 };
 
@@ -336,6 +455,25 @@ static Step3<S> make3(const lbm3_lattice *L, int src, int toff, int mom) {
     a.k.kw1 = (C)(kf / 18.0);
     a.k.kw2 = (C)(kf / 36.0);
     a.k.force = (p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0) ? 1 : 0;
+    for (int i = 0; i < Q; ++i)
+        a.k.cF[i] = (C)(d3::cx(i) * p.force[0] + d3::cy(i) * p.force[1] + d3::cz(i) * p.force[2]);
+    {
+        const int64_t N = L->pl.N, nx = p.nx, nxy = (int64_t)p.nx * p.ny;
+        for (int i = 0; i < Q; ++i) {
+            const int64_t d = d3::cz(i) * nxy + d3::cy(i) * nx + d3::cx(i);   // node shift of the pull
+            int64_t self, mul;
+            if (p.layout == LBM_LAYOUT_STREAM) { self = i * N; mul = 1; }
+            else if (p.layout == LBM_LAYOUT_COLLISION) { self = i; mul = 19; }
+            else { self = bundle_first(i) * N + (i - bundle_first(i)); mul = bundle_size(i); }
+            const int j = d3::opp(i);
+            const int64_t selfj = p.layout == LBM_LAYOUT_STREAM ? j * N
+                                : p.layout == LBM_LAYOUT_COLLISION ? j
+                                : bundle_first(j) * N + (j - bundle_first(j));
+            a.os[i] = (int32_t)self;
+            a.op[i] = (int32_t)(self - mul * d);
+            a.ob[i] = (int32_t)selfj;
+        }
+    }
     a.links = (const uint32_t *)(L->ws + L->pl.links);
     a.src = (const S *)(L->ws + L->pl.pop[src]);
     a.dst = (S *)(L->ws + L->pl.pop[src ^ 1]);
@@ -350,6 +488,8 @@ static Step3<S> make3(const lbm3_lattice *L, int src, int toff, int mom) {
     a.tz = L->pl.tz;
     a.nx_magic = magic((uint64_t)p.nx);
     a.nxy_magic = magic((uint64_t)p.nx * (uint64_t)p.ny);
+    // measured: +7 % for the stream layout on a porous box, -3 % for the bundle layout
+    a.zero_fill = (p.layout != LBM_LAYOUT_BUNDLE && (p.algo == LBM_LPTL || L->pl.tx % 32 == 0)) ? 1 : 0;
     return a;
 }
 
@@ -361,20 +501,25 @@ static Step3<S> make3(const lbm3_lattice *L, int src, int toff, int mom) {
         default: { using S = __nv_bfloat16; __VA_ARGS__; break; }                                       \
     }
 
+template <class S, bool LINEAR, bool OFF32>
+static void launch3k(const lbm3_lattice *L, const Step3<S> &a, dim3 grid, dim3 block, cudaStream_t st) {
+    const int lay = L->p.layout;
+    if (lay == LBM_LAYOUT_STREAM) k3_step<S, STREAM, LINEAR, OFF32><<<grid, block, 0, st>>>(a);
+    else if (lay == LBM_LAYOUT_BUNDLE) k3_step<S, BUNDLE, LINEAR, OFF32><<<grid, block, 0, st>>>(a);
+    else k3_step<S, COLLISION, LINEAR, OFF32><<<grid, block, 0, st>>>(a);
+}
+
 template <class S>
 static cudaError_t step3(const lbm3_lattice *L, cudaStream_t st, int src, int toff, int mom) {
     const Step3<S> a = make3<S>(L, src, toff, mom);
-    const int lay = L->p.layout;
     if (L->p.algo == LBM_LPTL) {
-        const unsigned g = (unsigned)((L->pl.N + L->block_1d - 1) / L->block_1d);
-        if (lay == LBM_LAYOUT_STREAM) k3_step<S, STREAM, true><<<g, L->block_1d, 0, st>>>(a);
-        else if (lay == LBM_LAYOUT_BUNDLE) k3_step<S, BUNDLE, true><<<g, L->block_1d, 0, st>>>(a);
-        else k3_step<S, COLLISION, true><<<g, L->block_1d, 0, st>>>(a);
+        const dim3 g((unsigned)((L->pl.N + L->block_1d - 1) / L->block_1d)), b(L->block_1d);
+        if (L->off32) launch3k<S, true, true>(L, a, g, b, st);
+        else launch3k<S, true, false>(L, a, g, b, st);
     } else {
-        const dim3 grid(L->pl.ntx, L->pl.nty, L->pl.ntz), tile(L->pl.tx, L->pl.ty, L->pl.tz);
-        if (lay == LBM_LAYOUT_STREAM) k3_step<S, STREAM, false><<<grid, tile, 0, st>>>(a);
-        else if (lay == LBM_LAYOUT_BUNDLE) k3_step<S, BUNDLE, false><<<grid, tile, 0, st>>>(a);
-        else k3_step<S, COLLISION, false><<<grid, tile, 0, st>>>(a);
+        const dim3 g(L->pl.ntx, L->pl.nty, L->pl.ntz), b(L->pl.tx, L->pl.ty, L->pl.tz);
+        if (L->off32) launch3k<S, false, true>(L, a, g, b, st);
+        else launch3k<S, false, false>(L, a, g, b, st);
     }
     return cudaGetLastError();
 }
@@ -422,9 +567,9 @@ static int block_of(int layout) {
         }
         return b;
     };
-    if (layout == LBM_LAYOUT_STREAM) return pick((const void *)k3_step<S, STREAM, true>);
-    if (layout == LBM_LAYOUT_BUNDLE) return pick((const void *)k3_step<S, BUNDLE, true>);
-    return pick((const void *)k3_step<S, COLLISION, true>);
+    if (layout == LBM_LAYOUT_STREAM) return pick((const void *)k3_step<S, STREAM, true, true>);
+    if (layout == LBM_LAYOUT_BUNDLE) return pick((const void *)k3_step<S, BUNDLE, true, true>);
+    return pick((const void *)k3_step<S, COLLISION, true, true>);
 }
 
 extern "C" lbm_status lbm3_init(lbm3_lattice *L, const double *rho, const double *ux, const double *uy,
@@ -492,6 +637,7 @@ extern "C" lbm_status lbm3_create(const lbm3_params *p, const uint8_t *mask_host
     L->ws = (char *)d_workspace;
     L->stream = (cudaStream_t)cuda_stream;
     LBM3_DISPATCH(L, L->block_1d = block_of<S>(p->layout));
+    L->off32 = (offsets_fit(p, pl.N) && !(p->flags & LBM_FLAG_WIDE_OFFSETS)) ? 1 : 0;
     cudaError_t e = cudaStreamCreateWithFlags(&L->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete L;

@@ -47,6 +47,7 @@ template <class C> struct Consts3 {
     C omega;
     C hf[3];        // F/2
     C f[3];         // F
+    C cF[Q];        // c_i . F
     C w0, w1, w2;   // 1/3, 1/18, 1/36
     C kw0, kw1, kw2;  // (1 - omega/2) w
     int force;
@@ -56,6 +57,7 @@ template <class C> struct Consts3 {
 // the Guo source in one fixed operation order (shared by every D3Q19 kernel):
 //   P_i  = drho - 3/2 u^2 + cu_i (3 + 9/2 cu_i),  h*_i = g_i + omega (w_i P_i - g_i)
 //          + (1 - omega/2) w_i [cF_i (3 + 9 cu_i) - 3 u.F]
+// with cu_i formed from the one or two nonzero components of c_i.
 template <class C>
 __device__ __forceinline__ void collide3(const Consts3<C> &k, C *g, C &drho, C &ux, C &uy, C &uz) {
     using A = Ar<C>;
@@ -63,15 +65,22 @@ __device__ __forceinline__ void collide3(const Consts3<C> &k, C *g, C &drho, C &
 #pragma unroll
     for (int i = 1; i < Q; ++i) r = A::add(r, g[i]);
     drho = r;
-    C j[3] = {C(0), C(0), C(0)};
+    // momentum: signed sums in direction order, starting from the first term
+    C j[3];
+    bool started[3] = {false, false, false};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (cx(i) > 0) j[0] = A::add(j[0], g[i]);
-        if (cx(i) < 0) j[0] = A::sub(j[0], g[i]);
-        if (cy(i) > 0) j[1] = A::add(j[1], g[i]);
-        if (cy(i) < 0) j[1] = A::sub(j[1], g[i]);
-        if (cz(i) > 0) j[2] = A::add(j[2], g[i]);
-        if (cz(i) < 0) j[2] = A::sub(j[2], g[i]);
+        const int c[3] = {cx(i), cy(i), cz(i)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!c[a]) continue;
+            if (!started[a]) {
+                j[a] = c[a] > 0 ? g[i] : -g[i];
+                started[a] = true;
+            } else {
+                j[a] = c[a] > 0 ? A::add(j[a], g[i]) : A::sub(j[a], g[i]);
+            }
+        }
     }
     ux = A::add(j[0], k.hf[0]);
     uy = A::add(j[1], k.hf[1]);
@@ -79,18 +88,27 @@ __device__ __forceinline__ void collide3(const Consts3<C> &k, C *g, C &drho, C &
     const C usq = A::fma(ux, ux, A::fma(uy, uy, A::mul(uz, uz)));
     const C base = A::fma(C(-1.5), usq, drho);
     const C m3uF = A::mul(C(-3), A::fma(ux, k.f[0], A::fma(uy, k.f[1], A::mul(uz, k.f[2]))));
+    const C u[3] = {ux, uy, uz};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        C cu = C(0), cF = C(0);
-        if (cx(i)) { cu = cx(i) > 0 ? A::add(cu, ux) : A::sub(cu, ux); cF = cx(i) > 0 ? A::add(cF, k.f[0]) : A::sub(cF, k.f[0]); }
-        if (cy(i)) { cu = cy(i) > 0 ? A::add(cu, uy) : A::sub(cu, uy); cF = cy(i) > 0 ? A::add(cF, k.f[1]) : A::sub(cF, k.f[1]); }
-        if (cz(i)) { cu = cz(i) > 0 ? A::add(cu, uz) : A::sub(cu, uz); cF = cz(i) > 0 ? A::add(cF, k.f[2]) : A::sub(cF, k.f[2]); }
+        const int c[3] = {cx(i), cy(i), cz(i)};
+        C cu = C(0);
+        bool any = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!c[a]) continue;
+            const C t = c[a] > 0 ? u[a] : -u[a];
+            cu = any ? A::add(cu, t) : t;
+            any = true;
+        }
         const C w = sq(i) == 0 ? k.w0 : (sq(i) == 1 ? k.w1 : k.w2);
-        const C P = A::fma(cu, A::fma(C(4.5), cu, C(3)), base);
+        const C P = any ? A::fma(cu, A::fma(C(4.5), cu, C(3)), base) : base;
         C o = A::fma(k.omega, A::fma(w, P, -g[i]), g[i]);
-        if (k.force) {
-            const C kw = sq(i) == 0 ? k.kw0 : (sq(i) == 1 ? k.kw1 : k.kw2);
-            o = A::fma(kw, A::fma(cF, A::fma(C(9), cu, C(3)), m3uF), o);
+        if (k.force && any) {
+            const C kw = sq(i) == 1 ? k.kw1 : k.kw2;
+            o = A::fma(kw, A::fma(k.cF[i], A::fma(C(9), cu, C(3)), m3uF), o);
+        } else if (k.force) {
+            o = A::fma(k.kw0, m3uF, o);
         }
         g[i] = o;
     }

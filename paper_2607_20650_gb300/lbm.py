@@ -24,6 +24,7 @@ PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG, INLET_EQ_NEUMANN, O
 LBM_FLAG_NO_GRAPH = 1
 LBM_FLAG_ONE_NODE_PER_THREAD = 2
 LBM_FLAG_NO_STAGING = 4
+LBM_FLAG_WIDE_OFFSETS = 8
 LBM_AUTO = -1
 
 

@@ -82,12 +82,13 @@ SPECS = specs()
 
 @pytest.mark.parametrize("case", list(SPECS))
 @pytest.mark.parametrize("layout", LAYOUTS)
-@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("algo", ALGOS + ("nptl_wide",))
 def test_fp64_matches_oracle3(case, layout, algo):
     spec = SPECS[case]
     T = 40
     ref = spec.oracle().run(T)
-    lat = spec.gpu(layout=layout, algo=algo, storage="f64")
+    flags = lbm.LBM_FLAG_WIDE_OFFSETS if algo == "nptl_wide" else 0
+    lat = spec.gpu(layout=layout, algo=algo.split("_")[0], storage="f64", flags=flags)
     lat.step(T, moments=True).sync()
     h = lat.populations("f64")
     rho, ux, uy, uz = lat.moments()
@@ -110,10 +111,11 @@ def test_all_layouts_algorithms_and_tiles_bit_identical(storage, rounding):
     T = 70   # one graph of 64 updates plus single launches
     base = None
     for layout in LAYOUTS:
-        for algo, tile in (("lptl", (0, 0, 0)), ("nptl", (32, 4, 2)), ("nptl", (8, 8, 8)),
-                           ("nptl", (16, 2, 1))):
+        for algo, tile, flags in (("lptl", (0, 0, 0), 0), ("nptl", (32, 4, 2), 0), ("nptl", (8, 8, 8), 0),
+                                  ("nptl", (16, 2, 1), 0), ("lptl", (0, 0, 0), lbm.LBM_FLAG_WIDE_OFFSETS),
+                                  ("nptl", (128, 1, 1), lbm.LBM_FLAG_WIDE_OFFSETS)):
             lat = spec.gpu(layout=layout, algo=algo, tile=tile, storage=storage, rounding=rounding,
-                           seed=99)
+                           seed=99, flags=flags)
             lat.step(T, moments=True).sync()
             got = (lat.populations("f64"), *lat.moments())
             lat.close()
@@ -121,7 +123,7 @@ def test_all_layouts_algorithms_and_tiles_bit_identical(storage, rounding):
                 base = got
             else:
                 for a, b in zip(got, base):
-                    assert np.array_equal(a, b, equal_nan=False), (layout, algo, tile)
+                    assert np.array_equal(a, b, equal_nan=False), (layout, algo, tile, flags)
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
