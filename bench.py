@@ -160,11 +160,19 @@ def max_over_ranks(value: float, device: str) -> float:
     return float(t.item())
 
 
-def kernel_name(args) -> str:
+def kernel_name(args, tile=(32, 4)) -> str:
+    """The update kernel as ncu lists it (layout as its enum value: stream 0,
+    bundle 1, collision 2)."""
     t = {"f32": "float", "f64": "double", "f16s": "__half", "bf16s": "__nv_bfloat16"}[args.storage]
-    k = {"lptl": "k_two_lattice", "nptl": "k_two_lattice", "npol": "k_npol", "nsol": "k_nsol",
-         "aa": "k_aa"}[args.algo]
-    return f"{k}<{t}, {args.layout.upper()}, {args.algo.upper()}>"
+    lay = {"stream": 0, "bundle": 1, "collision": 2}[args.layout]
+    if args.algo == "lptl":
+        return f"k_two_lattice<{t}, {lay}, true>"
+    if args.algo == "nptl":
+        if args.layout == "collision" and tile[0] % 32 == 0:
+            return f"k_two_lattice_aos<{t}>"
+        return f"k_two_lattice<{t}, {lay}, false>"
+    return {"npol": f"k_npol<{t}, {lay}>", "nsol": f"k_nsol<{t}, {lay}>",
+            "aa": f"k_aa<{t}, {lay}, 0|1> (two phases)"}[args.algo]
 
 
 def launches_for(k: int, graph_block: int = 64) -> int:
@@ -310,7 +318,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": info["bytes_per_update"],
-                     "kernel": kernel_name(args)},
+                     "kernel": kernel_name(args, tile)},
         "clocks": clocks,
         "mlups_fluid": info["fluid_cells"] * args.steps * world / dt / 1e6,
     }
@@ -472,8 +480,7 @@ def batched(args, torch):
     bc = lambda w: (w.bc_w, w.bc_e, w.bc_s, w.bc_n)
     probe = lbm.make_params(probe_w.nx, probe_w.ny, probe_w.tau, u_in=(probe_w.ux_in, 0.0), bc=bc(probe_w),
                             storage="f32")
-    pb = lbm.lbm_workspace_bytes(lbm.make_params(probe_w.nx, probe_w.ny, 0.8, storage="f32",
-                                                 layout="collision", algo="lptl"))
+    pb = lbm.lbm_tune_workspace_bytes(probe)
     stream = torch.cuda.Stream()
     pws = torch.empty(pb, dtype=torch.uint8, device="cuda")
     tuning = lbm.lbm_tune(probe, probe_w.mask, pws, pb, stream.cuda_stream)

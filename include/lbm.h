@@ -106,9 +106,9 @@ typedef enum {
 } lbm_bc;
 
 #define LBM_FLAG_NO_GRAPH 0x1u   /* lbm_step launches kernels one by one */
-#define LBM_FLAG_ONE_NODE_PER_THREAD 0x2u  /* NPTL, F64/F32 storage: one node per thread
-                                              (default with an even tile_y: two, rows y and
-                                              y + tile_y/2) */
+#define LBM_FLAG_TWO_NODES_PER_THREAD 0x2u  /* NPTL, F64/F32 storage, even tile_y: two nodes
+                                               per thread, rows y and y + tile_y/2 (default:
+                                               one node per thread) */
 #define LBM_FLAG_NO_STAGING 0x4u  /* NPTL, collision layout: no shared-memory staging of
                                      row spans (default when tile_x % 32 == 0) */
 #define LBM_FLAG_WIDE_OFFSETS 0x8u  /* D3Q19: 64-bit addressing for every pull, the path
@@ -245,15 +245,19 @@ typedef struct lbm_tuning {
     int32_t reserved;
 } lbm_tuning;
 
-/* Time every (layout, algo) on a probe lattice in the caller's workspace
- * (size from lbm_workspace_bytes of probe with layout = COLLISION, algo =
- * LPTL is enough for all) and fill *out. Synchronous. */
+/* Time the batch kernel for every (layout, algo) on eight copies of a probe
+ * case in the caller's workspace (at least lbm_tune_workspace_bytes(probe))
+ * and fill *out. Synchronous. */
+lbm_status lbm_tune_workspace_bytes(const lbm_params *probe, size_t *bytes);
 lbm_status lbm_tune(const lbm_params *probe, const uint8_t *mask_host, void *d_workspace,
                     size_t bytes, void *cuda_stream, lbm_tuning *out);
 
 /* Resolve LBM_AUTO layout/algo and 0 tiles of every case with the
  * autotuner (tuning may be NULL: built-in model); params is updated in
- * place. All cases must share storage type. */
+ * place. All cases must share storage type. One layout/algorithm pair is
+ * given to every case (the batch then runs a kernel specialised for it)
+ * unless per-case pairs are predicted faster by more than 1.6x, the
+ * measured cost of the general mixed-pair kernel. */
 lbm_status lbm_batch_plan(int32_t ncases, lbm_params *params, const lbm_tuning *tuning);
 
 lbm_status lbm_batch_workspace_bytes(int32_t ncases, const lbm_params *params, size_t *bytes);

@@ -451,6 +451,9 @@ static Step3<S> make3(const lbm3_lattice *L, int src, int toff, int mom) {
     a.k.w0 = (C)(1.0 / 3.0);
     a.k.w1 = (C)(1.0 / 18.0);
     a.k.w2 = (C)(1.0 / 36.0);
+    a.k.wl0 = (C)(1.0 / 3.0 - (double)a.k.w0);
+    a.k.wl1 = (C)(1.0 / 18.0 - (double)a.k.w1);
+    a.k.wl2 = (C)(1.0 / 36.0 - (double)a.k.w2);
     a.k.kw0 = (C)(kf / 3.0);
     a.k.kw1 = (C)(kf / 18.0);
     a.k.kw2 = (C)(kf / 36.0);

@@ -49,6 +49,7 @@ template <class C> struct Consts3 {
     C f[3];         // F
     C cF[Q];        // c_i . F
     C w0, w1, w2;   // 1/3, 1/18, 1/36
+    C wl0, wl1, wl2;  // w - (C)w: rounding residuals of the weights (0 in FP64)
     C kw0, kw1, kw2;  // (1 - omega/2) w
     int force;
 };
@@ -57,7 +58,10 @@ template <class C> struct Consts3 {
 // the Guo source in one fixed operation order (shared by every D3Q19 kernel):
 //   P_i  = drho - 3/2 u^2 + cu_i (3 + 9/2 cu_i),  h*_i = g_i + omega (w_i P_i - g_i)
 //          + (1 - omega/2) w_i [cF_i (3 + 9 cu_i) - 3 u.F]
-// with cu_i formed from the one or two nonzero components of c_i.
+// with cu_i formed from the one or two nonzero components of c_i, and in
+// FP32 w_i P_i formed with w_i as the rounded weight plus its residual (the
+// rounded weights alone miss sum_i w_i c_i c_i = 1/3 by ~1e-8, which would
+// make the relaxation a momentum source proportional to u).
 template <class C>
 __device__ __forceinline__ void collide3(const Consts3<C> &k, C *g, C &drho, C &ux, C &uy, C &uz) {
     using A = Ar<C>;
@@ -103,7 +107,9 @@ __device__ __forceinline__ void collide3(const Consts3<C> &k, C *g, C &drho, C &
         }
         const C w = sq(i) == 0 ? k.w0 : (sq(i) == 1 ? k.w1 : k.w2);
         const C P = any ? A::fma(cu, A::fma(C(4.5), cu, C(3)), base) : base;
-        C o = A::fma(k.omega, A::fma(w, P, -g[i]), g[i]);
+        C t = A::fma(w, P, -g[i]);
+        if (sizeof(C) == 4) t = A::fma(sq(i) == 0 ? k.wl0 : (sq(i) == 1 ? k.wl1 : k.wl2), P, t);
+        C o = A::fma(k.omega, t, g[i]);
         if (k.force && any) {
             const C kw = sq(i) == 1 ? k.kw1 : k.kw2;
             o = A::fma(kw, A::fma(k.cF[i], A::fma(C(9), cu, C(3)), m3uF), o);

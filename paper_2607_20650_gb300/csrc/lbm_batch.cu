@@ -299,6 +299,34 @@ static const double kDefaultNsPerCell[3][4] = {
 };
 static const double kDefaultNsPerTile = 0.5;
 
+// The tuner times the batch kernel itself on kTuneCopies copies of the
+// probe (enough tiles to fill the GPU), one (layout, algorithm) at a time.
+constexpr int kTuneCopies = 8;
+
+static lbm_params tune_params(const lbm_params *probe, int l, int a) {
+    lbm_params p = *probe;
+    p.layout = l;
+    p.algo = a;
+    p.tile_x = a == LBM_LPTL ? 0 : 32;
+    p.tile_y = a == LBM_LPTL ? 0 : 8;
+    return p;
+}
+
+extern "C" lbm_status lbm_tune_workspace_bytes(const lbm_params *probe, size_t *bytes) {
+    if (!probe || !bytes) return lbm_fail(LBM_EINVAL, "tune: NULL argument");
+    size_t most = 0;
+    for (int l = 0; l < 3; ++l)
+        for (int a = 0; a < 4; ++a) {
+            std::vector<lbm_params> ps(kTuneCopies, tune_params(probe, l, a));
+            size_t b = 0;
+            lbm_status s = lbm_batch_workspace_bytes(kTuneCopies, ps.data(), &b);
+            if (s != LBM_OK) return s;
+            most = std::max(most, b);
+        }
+    *bytes = most;
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm_tune(const lbm_params *probe, const uint8_t *mask_host, void *d_workspace,
                                size_t bytes, void *cuda_stream, lbm_tuning *out) {
     if (!probe || !mask_host || !out) return lbm_fail(LBM_EINVAL, "tune: NULL argument");
@@ -307,33 +335,32 @@ extern "C" lbm_status lbm_tune(const lbm_params *probe, const uint8_t *mask_host
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const cudaStream_t st = (cudaStream_t)cuda_stream;
+    const std::vector<const uint8_t *> masks(kTuneCopies, mask_host);
     lbm_status result = LBM_OK;
     for (int l = 0; l < 3 && result == LBM_OK; ++l)
         for (int a = 0; a < 4 && result == LBM_OK; ++a) {
-            lbm_params p = *probe;
-            p.layout = l;
-            p.algo = a;
-            p.tile_x = a == LBM_LPTL ? 0 : 32;
-            p.tile_y = a == LBM_LPTL ? 0 : 8;
-            p.flags |= LBM_FLAG_NO_GRAPH;
-            lbm_lattice *L = nullptr;
-            lbm_status s = lbm_create(&p, mask_host, d_workspace, bytes, cuda_stream, &L);
+            const std::vector<lbm_params> ps(kTuneCopies, tune_params(probe, l, a));
+            lbm_batch *B = nullptr;
+            lbm_status s = lbm_batch_create(kTuneCopies, ps.data(), masks.data(), d_workspace, bytes,
+                                            cuda_stream, &B);
             if (s != LBM_OK) {
                 result = s;
                 break;
             }
             const int reps = 10;
-            s = lbm_step(L, 2, 0);
+            s = lbm_batch_step(B, 2, 0);
             cudaError_t e = cudaEventRecord(e0, st);
-            if (s == LBM_OK && e == cudaSuccess) s = lbm_step(L, reps, 0);
+            if (s == LBM_OK && e == cudaSuccess) s = lbm_batch_step(B, reps, 0);
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            lbm_destroy(L);
+            lbm_batch_destroy(B);
             if (e != cudaSuccess) result = lbm_cuda_fail(e, "tune timing");
             else if (s != LBM_OK) result = s;
-            else out->ns_per_cell[l][a] = 1e6 * ms / ((double)reps * p.nx * (double)p.ny);
+            else
+                out->ns_per_cell[l][a] =
+                    1e6 * ms / ((double)reps * kTuneCopies * (double)probe->nx * (double)probe->ny);
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -358,41 +385,100 @@ static double predict(const lbm_params &p, int l, int a, int tx, int ty, const d
     return ns[l][a] * (N + 0.25 * (slots - N)) + tile_ns * tiles;
 }
 
+namespace {
+
+// Cheapest tile (or LPTL) of case p for layout l and algorithm a; INFINITY
+// when p fixes another layout or algorithm or the pair has no cost entry.
+double best_for(const lbm_params &p, int l, int a, const double (*ns)[4], double tile_ns, int *bx, int *by) {
+    static const int shapes[][2] = {{256, 1}, {128, 2}, {64, 4}, {32, 8}, {32, 4}, {64, 2}, {128, 1},
+                                    {32, 2}, {64, 1}, {32, 1}, {16, 16}, {16, 8}};
+    if ((p.layout != LBM_AUTO && p.layout != l) || (p.algo != LBM_AUTO && p.algo != a) || !(ns[l][a] > 0))
+        return INFINITY;
+    if (a == LBM_LPTL) {
+        *bx = 0;
+        *by = 0;
+        return predict(p, l, a, 0, 0, ns, tile_ns);
+    }
+    const bool auto_tile = p.tile_x == 0 && p.tile_y == 0;
+    double best = INFINITY;
+    for (auto &sh : shapes) {
+        const int tx = auto_tile ? sh[0] : p.tile_x, ty = auto_tile ? sh[1] : p.tile_y;
+        const double t = predict(p, l, a, tx, ty, ns, tile_ns);
+        if (t < best) {
+            best = t;
+            *bx = tx;
+            *by = ty;
+        }
+        if (!auto_tile) break;
+    }
+    return best;
+}
+
+// Cases that share layout and algorithm run a kernel specialised for that
+// pair; a batch with mixed pairs runs the general one, measured about 1.6x
+// slower per node. So a shared pair is chosen unless per-case pairs are
+// predicted to be faster by more than that.
+constexpr double kMixedPenalty = 1.6;
+
+}  // namespace
+
 extern "C" lbm_status lbm_batch_plan(int32_t ncases, lbm_params *params, const lbm_tuning *tuning) {
     if (ncases < 1 || !params) return lbm_fail(LBM_EINVAL, "plan: bad arguments");
     const bool tuned = tuning && tuning->valid;
     const double (*ns)[4] = tuned ? tuning->ns_per_cell : kDefaultNsPerCell;
     const double tile_ns = tuned ? tuning->ns_per_tile : kDefaultNsPerTile;
-    static const int shapes[][2] = {{256, 1}, {128, 2}, {64, 4}, {32, 8}, {32, 4}, {64, 2}, {128, 1},
-                                    {32, 2}, {64, 1}, {32, 1}, {16, 16}, {16, 8}};
+    // per-case best pair
+    std::vector<int> cl(ncases), ca(ncases), cx(ncases), cy(ncases);
+    double mixed = 0.0;
     for (int c = 0; c < ncases; ++c) {
-        lbm_params &p = params[c];
-        const bool auto_tile = p.tile_x == 0 && p.tile_y == 0;
         double best = INFINITY;
-        int bl = -1, ba = -1, bx = 0, by = 0;
-        for (int l = 0; l < 3; ++l) {
-            if (p.layout != LBM_AUTO && p.layout != l) continue;
+        for (int l = 0; l < 3; ++l)
             for (int a = 0; a < 4; ++a) {
-                if (p.algo != LBM_AUTO && p.algo != a) continue;
-                if (!(ns[l][a] > 0)) continue;
-                if (a == LBM_LPTL) {
-                    const double t = predict(p, l, a, 0, 0, ns, tile_ns);
-                    if (t < best) { best = t; bl = l; ba = a; bx = 0; by = 0; }
-                    continue;
-                }
-                for (auto &sh : shapes) {
-                    const int tx = auto_tile ? sh[0] : p.tile_x, ty = auto_tile ? sh[1] : p.tile_y;
-                    const double t = predict(p, l, a, tx, ty, ns, tile_ns);
-                    if (t < best) { best = t; bl = l; ba = a; bx = tx; by = ty; }
-                    if (!auto_tile) break;
+                int bx = 0, by = 0;
+                const double t = best_for(params[c], l, a, ns, tile_ns, &bx, &by);
+                if (t < best) {
+                    best = t;
+                    cl[c] = l;
+                    ca[c] = a;
+                    cx[c] = bx;
+                    cy[c] = by;
                 }
             }
+        if (!(best < INFINITY)) return lbm_fail(LBM_EINVAL, "plan: no candidate for case %d", c);
+        mixed += best;
+    }
+    // best shared pair
+    double shared = INFINITY;
+    int sl = -1, sa = -1;
+    for (int l = 0; l < 3; ++l)
+        for (int a = 0; a < 4; ++a) {
+            double tot = 0.0;
+            for (int c = 0; c < ncases && tot < INFINITY; ++c) {
+                int bx = 0, by = 0;
+                tot += best_for(params[c], l, a, ns, tile_ns, &bx, &by);
+            }
+            if (tot < shared) {
+                shared = tot;
+                sl = l;
+                sa = a;
+            }
         }
-        if (bl < 0) return lbm_fail(LBM_EINVAL, "plan: no candidate for case %d", c);
-        p.layout = bl;
-        p.algo = ba;
-        p.tile_x = bx;
-        p.tile_y = by;
+    const bool uniform = sl >= 0 && shared <= kMixedPenalty * mixed;
+    for (int c = 0; c < ncases; ++c) {
+        lbm_params &p = params[c];
+        if (uniform) {
+            int bx = 0, by = 0;
+            best_for(p, sl, sa, ns, tile_ns, &bx, &by);
+            p.layout = sl;
+            p.algo = sa;
+            p.tile_x = bx;
+            p.tile_y = by;
+        } else {
+            p.layout = cl[c];
+            p.algo = ca[c];
+            p.tile_x = cx[c];
+            p.tile_y = cy[c];
+        }
     }
     return LBM_OK;
 }

@@ -57,6 +57,9 @@ Step<S> make_step(const HostArgs &h, const StepCall &c) {
     k.w0 = (C)(1.0 / 36.0);
     k.w1 = (C)(1.0 / 9.0);
     k.w4 = (C)(4.0 / 9.0);
+    k.wl0 = (C)(1.0 / 36.0 - (double)k.w0);
+    k.wl1 = (C)(1.0 / 9.0 - (double)k.w1);
+    k.wl4 = (C)(4.0 / 9.0 - (double)k.w4);
     k.kw0 = (C)(h.kf / 36.0);
     k.kw1 = (C)(h.kf / 9.0);
     k.kw4 = (C)(4.0 * h.kf / 9.0);
@@ -147,10 +150,12 @@ __device__ __forceinline__ typename Codec<S>::C neighbour_drho(const Step<S> &a,
 // the nine post-collision values (canonical direction order) into e.
 // drho_nb: density deviation of node (1, y) in the previous state, used by
 // the Neumann equilibrium inlet only.
+// Inlet (x = 0) and outlet (x = nx - 1) substitutions of the pulled values.
+// drho_nb: density deviation of node (1, y) in the previous state, used by
+// the Neumann equilibrium inlet only.
 template <class S>
-__device__ __forceinline__ void collide_encode(const Step<S> &a, uint32_t x, uint32_t n,
-                                               typename Codec<S>::C *g, S *e,
-                                               typename Codec<S>::C drho_nb = 0) {
+__device__ __forceinline__ void edge_substitute(const Step<S> &a, uint32_t x, typename Codec<S>::C *g,
+                                                typename Codec<S>::C drho_nb) {
     using C = typename Codec<S>::C;
     using A = Ar<C>;
     if (x == 0) {
@@ -168,6 +173,19 @@ __device__ __forceinline__ void collide_encode(const Step<S> &a, uint32_t x, uin
         }
     }
     if (x == (uint32_t)a.geo.nx - 1 && a.geo.be == OUTLET_PRESSURE) zou_he_pressure(a.k, g);
+}
+
+// Edge substitutions (EDGE = true; false when the caller has applied them or
+// guarantees 0 < x < nx - 1, which keeps them out of the interior hot path),
+// collision, divergence flag, moments, and encoding of the nine
+// post-collision values (canonical direction order) into e.
+template <class S, bool EDGE = true>
+__device__ __forceinline__ void collide_encode(const Step<S> &a, uint32_t x, uint32_t n,
+                                               typename Codec<S>::C *g, S *e,
+                                               typename Codec<S>::C drho_nb = 0) {
+    using C = typename Codec<S>::C;
+    using A = Ar<C>;
+    if (EDGE) edge_substitute(a, x, g, drho_nb);
     C drho, ux, uy;
     collide(a.k, g, drho, ux, uy);
     if (!isfinite(drho)) atomicOr(a.err, 1u);
@@ -294,13 +312,14 @@ __device__ __forceinline__ void two_lattice_fluid(const Step<S> &a, uint32_t x, 
                 if (map_pull(a.geo, (int)x, (int)y, i, xs, ys, j) == PULL_NODE)
                     g[i] = ldp<S, L>(src, a.N, (uint32_t)ys * nx + (uint32_t)xs, j);
                 else
-                    g[i] = C(0);  // inlet unknown, reconstructed in collide_encode
+                    g[i] = C(0);  // inlet unknown, reconstructed by edge_substitute
             }
         }
+        const C dnb = (x == 0 && a.geo.bw == INLET_EQ_NEUMANN) ? neighbour_drho<S, L>(a, src, n, 0) : C(0);
+        edge_substitute(a, x, g, dnb);
     }
     S e[9];
-    const C dnb = (x == 0 && a.geo.bw == INLET_EQ_NEUMANN) ? neighbour_drho<S, L>(a, src, n, 0) : C(0);
-    collide_encode(a, x, n, g, e, dnb);
+    collide_encode<S, false>(a, x, n, g, e);
     store_node<S, L>(dst, n, a.N, a.off32, e);
 }
 
@@ -349,13 +368,13 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice2(const Step<S> 
     if (fast_b) pull_interior<S, L>(a.src, nb, nx, a.N, lkb, gb);
     S e[9];
     if (fast_a) {
-        collide_encode(a, x, na, ga, e);
+        collide_encode<S, false>(a, x, na, ga, e);
         store_node<S, L>(a.dst, na, a.N, a.off32, e);
     } else if (fa) {
         two_lattice_fluid<S, L>(a, x, ya, na, lka);
     }
     if (fast_b) {
-        collide_encode(a, x, nb, gb, e);
+        collide_encode<S, false>(a, x, nb, gb, e);
         store_node<S, L>(a.dst, nb, a.N, a.off32, e);
     } else if (fb) {
         two_lattice_fluid<S, L>(a, x, yb, nb, lkb);
@@ -455,7 +474,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice_aos(const Step<
 // LPTL (LINEAR: one node per thread over n, block size from the runtime) and
 // NPTL (2-D tiles of tx x ty nodes over a padded grid).
 template <class S, int L, bool LINEAR>
-__global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice(const Step<S> a) {
+__global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : 4) k_two_lattice(const Step<S> a) {
     const uint32_t nx = (uint32_t)a.geo.nx, ny = (uint32_t)a.geo.ny;
     uint32_t x, y;
     if (LINEAR) {
@@ -1231,9 +1250,9 @@ cudaError_t step_layout(const HostArgs &h, const Step<S> &a, int phase, cudaStre
                 k_two_lattice_aos<S><<<grid, tile, sm, st>>>(a);
                 break;
             }
-            // Two nodes per thread pays off for 4- and 8-byte storage (measured);
-            // the 16-bit paths are issue-bound and keep one node per thread.
-            if (sizeof(S) >= 4 && h.tile_y >= 2 && !(h.tile_y & 1) && !(h.flags & 2u))
+            // Two nodes per thread on request (4- and 8-byte storage): one node
+            // per thread at 32 registers keeps full occupancy and measured faster.
+            if (sizeof(S) >= 4 && h.tile_y >= 2 && !(h.tile_y & 1) && (h.flags & 2u))
                 k_two_lattice2<S, L><<<grid, dim3(h.tile_x, h.tile_y / 2), 0, st>>>(a);
             else
                 k_two_lattice<S, L, false><<<grid, tile, 0, st>>>(a);

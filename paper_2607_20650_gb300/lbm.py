@@ -22,7 +22,7 @@ STORAGES = {"f64": 0, "f32": 1, "f16s": 2, "bf16s": 3}
 ROUNDINGS = {"rne": 0, "sr": 1}
 PERIODIC, WALL, FREESLIP, INLET_ZOUHE, INLET_EQ, OUTFLOW_ZG, INLET_EQ_NEUMANN, OUTLET_PRESSURE = range(8)
 LBM_FLAG_NO_GRAPH = 1
-LBM_FLAG_ONE_NODE_PER_THREAD = 2
+LBM_FLAG_TWO_NODES_PER_THREAD = 2
 LBM_FLAG_NO_STAGING = 4
 LBM_FLAG_WIDE_OFFSETS = 8
 LBM_AUTO = -1
@@ -106,6 +106,7 @@ SIGNATURES = {
     "lbm_quantize": (_i32, [_i32, _i32, _u64, _i64, _vp, _vp, _vp, _i64, _vp]),
     "lbm_mass_f32_noalloc": (_i32, [_vp, _vp, _i64, _P(_dbl), _vp]),
     "lbm_tune": (_i32, [_P(lbm_params), _vp, _vp, _sz, _vp, _P(lbm_tuning)]),
+    "lbm_tune_workspace_bytes": (_i32, [_P(lbm_params), _P(_sz)]),
     "lbm_batch_plan": (_i32, [_i32, _P(lbm_params), _P(lbm_tuning)]),
     "lbm_batch_workspace_bytes": (_i32, [_i32, _P(lbm_params), _P(_sz)]),
     "lbm_batch_create": (_i32, [_i32, _P(lbm_params), _P(_vp), _vp, _sz, _vp, _P(_vp)]),
@@ -293,6 +294,12 @@ def lbm_mass_f32_noalloc(d_h, d_solid, N: int, stream: int) -> float:
     _check(load().lbm_mass_f32_noalloc(_ptr(d_h), _ptr(d_solid), int(N), ctypes.byref(out), stream),
            "lbm_mass_f32_noalloc")
     return out.value
+
+
+def lbm_tune_workspace_bytes(probe: lbm_params) -> int:
+    b = ctypes.c_size_t()
+    _check(load().lbm_tune_workspace_bytes(ctypes.byref(probe), ctypes.byref(b)), "lbm_tune_workspace_bytes")
+    return b.value
 
 
 def lbm_tune(probe: lbm_params, mask, workspace, nbytes: int, stream: int) -> lbm_tuning:

@@ -170,3 +170,37 @@ def test_d3q19_params_checked_without_gpu(lib):
         tau = kw.pop("tau")
         with pytest.raises(lbm.LbmError):
             lbm.lbm3_workspace_bytes(lbm.make_params3(16, 8, 4, tau, **kw))
+
+
+def test_batch_planner_prefers_one_shared_pair(lib):
+    """With a measured-style cost table under which a few small cases would
+    pick another pair on their own, the plan still gives every case one
+    layout and algorithm (the specialised batch kernel), unless a fixed case
+    makes a shared pair impossible."""
+    from paper_2607_20650_gb300 import geometry as G
+    t = lbm.lbm_tuning()
+    table = [[0.01849, 0.0173, 0.03252, 0.03291], [0.02043, 0.01809, 0.03251, 0.03486],
+             [0.04423, 0.02434, 0.04927, 0.05439]]
+    for l in range(3):
+        for a in range(4):
+            t.ns_per_cell[l][a] = table[l][a]
+    t.ns_per_tile = 2.0
+    t.valid = 1
+    cases = G.batch_channels(ncases=64, seed=4)
+    ps = [lbm.make_params(w.nx, w.ny, w.tau, u_in=(w.ux_in, 0.0), bc=(w.bc_w, w.bc_e, w.bc_s, w.bc_n),
+                          layout=lbm.LBM_AUTO, algo=lbm.LBM_AUTO, storage="f32") for w in cases]
+    planned = lbm.lbm_batch_plan(ps, t)
+    assert len({(p.layout, p.algo) for p in planned}) == 1
+    # one case pinned to NSOL: the others follow it only if that stays within the penalty
+    pinned = [lbm.make_params(300, 100, 0.8, layout="collision", algo="nsol", tile=(32, 8))]
+    mixed = lbm.lbm_batch_plan(pinned + ps[:8], t)
+    assert (mixed[0].layout, mixed[0].algo) == (2, 3)
+    assert all(p.layout in (0, 1, 2) and p.algo in (0, 1, 2, 3) for p in mixed)
+
+
+def test_tune_workspace_covers_every_candidate(lib):
+    probe = lbm.make_params(512, 256, 0.8, storage="f32")
+    need = lbm.lbm_tune_workspace_bytes(probe)
+    one = lbm.lbm_workspace_bytes(lbm.make_params(512, 256, 0.8, storage="f32", layout="collision",
+                                                  algo="lptl"))
+    assert need >= 8 * one

@@ -62,8 +62,7 @@ def test_autotuned_batch_equals_single_runs():
     ws = _cases(10, seed=13)
     probe = lbm.make_params(512, 256, 0.8, storage="f32")
     mask = G.porous_discs(512, 256, seed=3, rmin=8, rmax=16)
-    nbytes = lbm.lbm_workspace_bytes(lbm.make_params(512, 256, 0.8, storage="f32", layout="collision",
-                                                     algo="lptl"))
+    nbytes = lbm.lbm_tune_workspace_bytes(probe)
     wsp = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     tuning = lbm.lbm_tune(probe, mask, wsp, nbytes, lbm.current_stream())
     assert tuning.valid == 1

@@ -67,14 +67,16 @@ def test_all_layouts_and_algorithms_bit_identical(case, storage, rounding):
     spec = SPECS[case]
     T = 37
     results = {}
-    for layout, algo in COMBOS:
+    runs = [(layout, algo, 0) for layout, algo in COMBOS]
+    runs += [(layout, "nptl", lbm.LBM_FLAG_TWO_NODES_PER_THREAD) for layout in LAYOUTS]
+    for layout, algo, flags in runs:
         tile = (32, 4) if algo in ("npol", "nsol") else (64, 2)
         lat = spec.gpu(layout=layout, algo=algo, storage=storage, rounding=rounding, seed=1234,
-                       tile=tile)
+                       tile=tile, flags=flags)
         lat.step(T, moments=True).sync()
-        results[(layout, algo)] = (lat.populations("f64"), *lat.moments())
+        results[(layout, algo, flags)] = (lat.populations("f64"), *lat.moments())
         lat.close()
-    base = results[("stream", "lptl")]
+    base = results[("stream", "lptl", 0)]
     for key, r in results.items():
         for a, b in zip(r, base):
             assert np.array_equal(a, b), key
@@ -251,3 +253,25 @@ def test_neumann_inlet_rejected_for_aa_and_thin_one_lattice_tiles():
     assert e.value.status == lbm.LBM_EUNSUPPORTED
     with pytest.raises(lbm.LbmError):
         spec.gpu(algo="npol", storage="f32", tile=(1, 64))
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_momentum_conserved_over_long_runs(storage):
+    """Periodic box, no force, u_x = U0 + U1 sin(2 pi y / ny): BGK conserves
+    total momentum exactly, so after 20,000 updates the stored state's
+    sum_n sum_i c_i h_i may differ from the initial one by rounding noise
+    only. A systematic source of omega * delta * u per node and update
+    (delta ~ 1e-8, the error of rounded FP32 weights in sum_i w_i c_i c_i)
+    would move it by ~3e-4; the bar is 1e-5 (FP32) and 1e-10 (FP64, where
+    the rounded weights' delta ~1e-16 still gives omega delta T ~ 1e-11)."""
+    nx, ny, T = 64, 256, 20000
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    ux = 0.05 + 0.02 * np.sin(2 * np.pi * y / ny)
+    lat = lbm.Lattice(nx, ny, 0.65, None, layout="bundle", algo="nptl", storage=storage)
+    lat.init(None, ux.ravel(), np.zeros(nx * ny))
+    cx = np.array([i % 3 - 1 for i in range(9)], dtype=np.float64)
+    p0 = float(np.sum(cx[:, None] * lat.populations("f64")))
+    lat.step(T).sync()
+    p1 = float(np.sum(cx[:, None] * lat.populations("f64")))
+    assert abs(p1 - p0) <= (1e-5 if storage == "f32" else 1e-10) * abs(p0)
+    lat.close()

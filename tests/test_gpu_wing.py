@@ -108,7 +108,10 @@ def test_wing_lift_drag_precision():
         end, avg = _run(fine, 50000, 500, 10000, layout="bundle", algo="nptl", tile=(32, 4), **kw)
         out[f"{name}_fine"] = {"end": list(end), "avg": list(avg)}
     record(test="wing_lift_drag", coefficients=out, rel_err_vs_fp64_coarse=rel)
-    assert max(rel["f32"]["end"] + rel["f32"]["avg"]) <= 1e-3
+    # measured 2.0e-5 / 2.2e-5 at the end, 1.3e-6 / 3.3e-7 averaged (FP32 rounding
+    # noise; a weight-rounding momentum source showed as 5.5e-4 / 1.1e-3)
+    assert max(rel["f32"]["end"]) <= 2e-4
+    assert max(rel["f32"]["avg"]) <= 2e-5
     assert max(rel["f16s_sr"]["avg"]) <= 5e-2
     for v in out.values():
         assert np.isfinite(v["end"]).all() and np.isfinite(v["avg"]).all()
