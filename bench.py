@@ -35,7 +35,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "porous 16384x8192 (134M nodes), discs r 8-32 phi 0.4 seed 3, periodic, g_x 1e-6, tau 0.9"
+def workload(nx: int = 16384, ny: int = 8192) -> str:
+    return (f"porous {nx}x{ny} ({nx * ny / 1e6:.0f}M nodes), discs r 8-32 phi 0.4 seed 3, periodic, "
+            f"g_x 1e-6, tau 0.9")
+
+
+WORKLOAD = workload()
 METRIC = "D2Q9 BGK MLUPS (FP32 two-lattice, 134M-node porous medium)"
 PROFILE = os.path.join(ROOT, "profiles", "k_two_lattice_f32_bundle_nptl_porous16384x8192.md")
 KERNEL_SOURCES = ["paper_2607_20650_gb300/csrc/lbm_kernels.cuh",
@@ -309,7 +314,7 @@ def run_ours(args):
         "dtype": {"f32": "f32", "f64": "f64", "f16s": "f16 storage, f32 arithmetic",
                   "bf16s": "bf16 storage, f32 arithmetic"}[args.storage],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "layout": args.layout, "algo": args.algo,
+        "config": {"workload": workload(nx, ny), "layout": args.layout, "algo": args.algo,
                    "tile": f"{info['tile_x']}x{info['tile_y']}", "storage": f"{args.storage} shifted",
                    "fluid_nodes": info["fluid_cells"], "nodes": cells,
                    "l2": "inputs larger than L2 (two 4.8 GB lattices)",

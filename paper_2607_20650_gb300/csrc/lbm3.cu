@@ -223,7 +223,7 @@ __device__ __forceinline__ void zero3(const Step3<S> &a, uint32_t n) {
 // LINEAR: one node per thread over n (LPTL); otherwise 3-D tiles (NPTL).
 // OFF32: 19 N fits 31 bits, pulls of interior nodes use the offset tables.
 template <class S, int L, bool LINEAR, bool OFF32>
-__global__ void __launch_bounds__(512) k3_step(const Step3<S> a) {
+__global__ void __launch_bounds__(512, sizeof(S) == 8 ? 2 : 3) k3_step(const Step3<S> a) {
     using C = typename Codec<S>::C;
     const uint32_t nx = (uint32_t)a.g.nx, ny = (uint32_t)a.g.ny, nz = (uint32_t)a.g.nz;
     uint32_t x, y, z;
