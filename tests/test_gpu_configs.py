@@ -92,8 +92,8 @@ def test_poiseuille_256x64_fp64_stream_lptl():
 def test_karman_2048x512_fp32_all_variants():
     """FP32, 3 layouts x 4 algorithms: bit-identical to each other at 2,000
     and 10,000 updates; at 2,000 updates within 1e-5 relative L-inf of the
-    FP64 oracle on rho, and the measured velocity error is recorded and held
-    to 5e-5 (FP32 arithmetic at u/c_s ~ 0.09 over 2,000 updates)."""
+    FP64 oracle on rho and v (measured 1.2e-7 / 1.4e-6 with the weights'
+    rounding residuals in the collision; 3.5e-6 / 3.5e-5 without them)."""
     w = G.karman()
     ref = O.Lattice(_oracle_case(w), w.mask, ux=w.ux0, uy=w.uy0).run(2000)
     fl = ref.solid == 0
@@ -113,7 +113,7 @@ def test_karman_2048x512_fp32_all_variants():
             e_u = rel_linf(np.stack([ux, uy]), np.stack([ref.ux, ref.uy]), fl)
             record(test="karman", err_rho=e_rho, err_u=e_u)
             assert e_rho <= 1e-5
-            assert e_u <= 5e-5
+            assert e_u <= 1e-5
         else:
             for a, b in zip(r2k, base2k):
                 assert np.array_equal(a, b), (layout, algo, "2k")
