@@ -359,7 +359,7 @@ def variants(args, mask, torch, world):
                      ("f32_collision_nptl_64x4", dict(storage="f32", layout="collision", tile=(64, 4))),
                      ("f32_stream_npol_32x8", dict(storage="f32", algo="npol", tile=(32, 8))),
                      ("f32_stream_nsol_32x8", dict(storage="f32", algo="nsol", tile=(32, 8))),
-                     ("f32_bundle_aa_32x4", dict(storage="f32", algo="aa", layout="bundle", tile=(32, 4))),
+                     ("f32_bundle_aa_128x1", dict(storage="f32", algo="aa", layout="bundle", tile=(128, 1))),
                      ("f16s_rne_bundle_nptl_64x4", dict(storage="f16s", layout="bundle", tile=(64, 4))),
                      ("bf16s_rne_bundle_nptl_64x4", dict(storage="bf16s", layout="bundle", tile=(64, 4))),
                      ("f16s_sr_bundle_nptl_64x4", dict(storage="f16s", layout="bundle", tile=(64, 4),

@@ -105,12 +105,14 @@ __device__ __forceinline__ typename Codec<S>::C ldp(const S *base, uint32_t N, u
 #define LBM_LDG_HINT 0
 #endif
 #ifndef LBM_ST_HINT
-#define LBM_ST_HINT 2
+#define LBM_ST_HINT 0
 #endif
 // Loads of the read-only source lattice and stores of the destination
-// lattice of the two-lattice update. Stores default to evict-first
-// (st.global.cs) for the bundle layout, where it measured fastest, and to
-// plain stores elsewhere; LBM_ST_HINT=0/1 forces plain / evict-first.
+// lattice of the two-lattice update. Stores default to plain stores, which
+// measured 1 % faster than evict-first (st.global.cs) for the bundle layout
+// at 32 registers; LBM_ST_HINT=1 makes every store evict-first, 2 only the
+// bundle layout's; LBM_LDG_HINT=1 loads through the read-only path (no
+// measured difference).
 template <class S>
 __device__ __forceinline__ S ld_src(const S *p) {
 #if LBM_LDG_HINT == 1
@@ -882,7 +884,7 @@ __device__ __forceinline__ void aa_node(const Step<S> &a, uint32_t x, uint32_t y
 }
 
 template <class S, int L, int PHASE>
-__global__ void __launch_bounds__(kMaxTileThreads, PHASE == 0 ? 3 : 1) k_aa(const Step<S> a) {
+__global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : (PHASE == 0 || L == STREAM ? 3 : 4)) k_aa(const Step<S> a) {
     const uint32_t x = blockIdx.x * a.tx + threadIdx.x;
     const uint32_t y = blockIdx.y * a.ty + threadIdx.y;
     if (x >= (uint32_t)a.geo.nx || y >= (uint32_t)a.geo.ny) return;
