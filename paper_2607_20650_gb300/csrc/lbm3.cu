@@ -1,9 +1,11 @@
 // D3Q19 lattices (the paper's 3-D future work, Sec. 6) with the method of
 // Sec. 3.1: two-lattice pull (LPTL: one node per thread over n; NPTL: 3-D
-// tiles), the three layouts generalised (stream, bundle = directions sharing
-// a source row, collision), periodic or half-way wall faces, bounce-back at
-// solid nodes, Guo force, FP64/FP32/FP16/BF16 shifted storage, on-the-fly
-// moments, FP64 mass, CUDA graphs. C ABI: the lbm3_* calls of include/lbm.h.
+// tiles) and the one-lattice AA pattern (Sec. 3.3 names it, Sec. 6 lists it
+// as future work), the three layouts generalised (stream, bundle = directions
+// sharing a source row, collision), periodic or half-way wall faces,
+// bounce-back at solid nodes, Guo force, FP64/FP32/FP16/BF16 shifted storage,
+// on-the-fly moments, FP64 mass, CUDA graphs. C ABI: the lbm3_* calls of
+// include/lbm.h.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -64,6 +66,7 @@ struct Step3 {
     // 32-bit element offsets from the base of direction i at node n (base =
     // lattice + mult3(i) n): own slot, interior pull, bounced pull.
     int32_t os[Q], op[Q], ob[Q];
+    int32_t oq[Q];   // AA push: slot opp(i) of node n + c_i, from the base of direction i
 };
 
 // Node stride of direction i's array in a layout: 1 (stream; one-direction
@@ -257,6 +260,67 @@ __global__ void __launch_bounds__(512, sizeof(S) == 8 ? 2 : 3) k3_step(const Ste
     finish3<S, L, OFF32>(a, n, g);
 }
 
+// AA pattern on one array. Even updates (PHASE 0) start from the canonical
+// state (slot i of node n holds h_i(n)): each fluid node pulls as the
+// two-lattice update does and writes its result for direction i into slot
+// opp(i) of node n + c_i, the slot only this node read, or into its own slot
+// i when that neighbour is solid or beyond a wall (the next update bounces it
+// back from there). Odd updates (PHASE 1) read the node's own slots opp(i),
+// collide, and write slot i: the canonical state again. Every slot has one
+// reader and one writer per phase, and each thread reads all its slots
+// before writing any. Requires the 32-bit offset tables.
+template <class S, int L, int PHASE>
+__global__ void __launch_bounds__(512, PHASE == 0 ? (sizeof(S) == 8 ? 1 : 2) : (sizeof(S) == 8 ? 2 : 3)) k3_aa(const Step3<S> a) {
+    using C = typename Codec<S>::C;
+    const uint32_t nx = (uint32_t)a.g.nx, ny = (uint32_t)a.g.ny, nz = (uint32_t)a.g.nz;
+    const uint32_t x = blockIdx.x * a.tx + threadIdx.x;
+    const uint32_t y = blockIdx.y * a.ty + threadIdx.y;
+    const uint32_t z = blockIdx.z * a.tz + threadIdx.z;
+    if (x >= nx || y >= ny || z >= nz) return;
+    const uint32_t n = (z * ny + y) * nx + x;
+    const uint32_t lk = a.links[n];
+    if (lk == SOLID) return;
+    S *lat = a.dst;
+    C g[Q];
+    if (PHASE == 0) {
+        pull3<S, L, true>(a, x, y, z, n, lk, g);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = Codec<S>::dec(lat[mult3<L>(i) * n + (uint32_t)a.ob[i]]);
+    }
+    using A = Ar<C>;
+    C drho, ux, uy, uz;
+    collide3(a.k, g, drho, ux, uy, uz);
+    if (!isfinite(drho)) atomicOr(a.err, 1u);
+    if (a.mom) {
+        a.mom[n] = A::add(C(1), drho);
+        a.mom[a.N + n] = ux;
+        a.mom[2 * (size_t)a.N + n] = uy;
+        a.mom[3 * (size_t)a.N + n] = uz;
+    }
+    const bool sr = Codec<S>::narrow && a.sr;
+    uint32_t nk = 0;
+    if (sr) nk = node_key(step_key(a.seed, (uint32_t)(*a.tctr + a.toff)), n);
+    // push corrections for a neighbour across a periodic face
+    const int N = (int)a.N, nxy = (int)(nx * ny);
+    const int xhi = x == nx - 1 ? -(int)nx : 0, xlo = x == 0 ? (int)nx : 0;
+    const int yhi = y == ny - 1 ? -nxy : 0, ylo = y == 0 ? nxy : 0;
+    const int zhi = z == nz - 1 ? -N : 0, zlo = z == 0 ? N : 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        S *b = lat + mult3<L>(i) * n;
+        int o;
+        if (PHASE == 1 || i == REST || ((lk >> bit(opp(i))) & 1u)) {
+            o = a.os[i];
+        } else {
+            const int w = (cx(i) > 0 ? xhi : cx(i) < 0 ? xlo : 0) + (cy(i) > 0 ? yhi : cy(i) < 0 ? ylo : 0) +
+                          (cz(i) > 0 ? zhi : cz(i) < 0 ? zlo : 0);
+            o = a.oq[i] + (int)mult3<L>(i) * w;
+        }
+        st3<S, L>(b + o, Codec<S>::enc(g[i], sr, sr ? pop_rand(nk, i) : 0u));
+    }
+}
+
 template <class S, int L>
 __global__ void k3_init(const Step3<S> a, const double *rho, const double *ux, const double *uy,
                         const double *uz, uint32_t n0, uint32_t count) {
@@ -350,10 +414,13 @@ struct Plan3 {
     int tx = 0, ty = 1, tz = 1, ntx = 0, nty = 0, ntz = 0;
     size_t elem = 0, comp = 0;
     size_t pop[2] = {0, 0}, links = 0, mom = 0, mom_bytes = 0, partials = 0, misc = 0, total = 0;
+    int one = 0;   // one lattice (AA pattern)
 };
 
 size_t elem_of(int storage) { return storage == LBM_F64 ? 8 : storage == LBM_F32 ? 4 : 2; }
 size_t comp_of(int storage) { return storage == LBM_F64 ? 8 : 4; }
+
+bool offsets_fit(const lbm3_params *p, int64_t N);
 
 lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
     if (!p) return lbm_fail(LBM_EINVAL, "params is NULL");
@@ -368,12 +435,13 @@ lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
         if (bc[a] != LBM_BC_PERIODIC && bc[a] != LBM_BC_WALL)
             return lbm_fail(LBM_EINVAL, "D3Q19 faces are PERIODIC or WALL");
     if (p->layout < 0 || p->layout > 2) return lbm_fail(LBM_EINVAL, "bad layout");
-    if (p->algo != LBM_LPTL && p->algo != LBM_NPTL) return lbm_fail(LBM_EUNSUPPORTED, "D3Q19: LPTL or NPTL");
+    if (p->algo != LBM_LPTL && p->algo != LBM_NPTL && p->algo != LBM_AA)
+        return lbm_fail(LBM_EUNSUPPORTED, "D3Q19: LPTL, NPTL or AA");
     if (p->storage < 0 || p->storage > 3) return lbm_fail(LBM_EINVAL, "bad storage");
     if (p->rounding < 0 || p->rounding > 1) return lbm_fail(LBM_EINVAL, "bad rounding");
     *pl = Plan3();
     pl->N = (int64_t)N;
-    if (p->algo == LBM_NPTL) {
+    if (p->algo == LBM_NPTL || p->algo == LBM_AA) {
         int tx = p->tile_x, ty = p->tile_y, tz = p->tile_z;
         if (tx == 0 && ty == 0 && tz == 0) { tx = 128; ty = 1; tz = 1; }
         if (tx < 1 || ty < 1 || tz < 1 || tz > 64 || (int64_t)tx * ty * tz > 512)
@@ -389,7 +457,10 @@ lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off = (off + b + 255) / 256 * 256; return o; };
     pl->pop[0] = take(19 * (size_t)N * pl->elem);
-    pl->pop[1] = take(19 * (size_t)N * pl->elem);
+    pl->one = p->algo == LBM_AA ? 1 : 0;
+    if (pl->one && (!offsets_fit(p, (int64_t)N) || (p->flags & LBM_FLAG_WIDE_OFFSETS)))
+        return lbm_fail(LBM_EUNSUPPORTED, "D3Q19 AA needs 32-bit offset tables (19 N well below 2^31)");
+    pl->pop[1] = pl->one ? pl->pop[0] : take(19 * (size_t)N * pl->elem);
     pl->links = take(4 * (size_t)N);
     pl->mom_bytes = std::max(4 * (size_t)N * pl->comp, 4 * sizeof(double) * (size_t)std::min<uint64_t>(N, 1 << 16));
     pl->mom = take(pl->mom_bytes);
@@ -414,7 +485,13 @@ bool offsets_fit(const lbm3_params *p, int64_t N) {
         else { self = lbm::d3::bundle_first(i) * N + (i - lbm::d3::bundle_first(i)); mul = lbm::d3::bundle_size(i); }
         const int64_t wrap = mul * (az * N + ay * nxy + ax * nx);
         const int64_t pull = self - mul * d;
+        const int j = lbm::d3::opp(i);
+        const int64_t selfj = p->layout == LBM_LAYOUT_STREAM ? j * N
+                            : p->layout == LBM_LAYOUT_COLLISION ? j
+                            : lbm::d3::bundle_first(j) * N + (j - lbm::d3::bundle_first(j));
+        const int64_t push = selfj + mul * d;
         if (self > lim || pull + wrap > lim || pull - wrap < -lim) return false;
+        if (push + wrap > lim || push - wrap < -lim) return false;
         if (mul * N > lim) return false;   // mult * n itself stays 32-bit
     }
     return true;
@@ -475,11 +552,12 @@ static Step3<S> make3(const lbm3_lattice *L, int src, int toff, int mom) {
             a.os[i] = (int32_t)self;
             a.op[i] = (int32_t)(self - mul * d);
             a.ob[i] = (int32_t)selfj;
+            a.oq[i] = (int32_t)(selfj + mul * d);
         }
     }
     a.links = (const uint32_t *)(L->ws + L->pl.links);
-    a.src = (const S *)(L->ws + L->pl.pop[src]);
-    a.dst = (S *)(L->ws + L->pl.pop[src ^ 1]);
+    a.src = (const S *)(L->ws + L->pl.pop[L->pl.one ? 0 : src]);
+    a.dst = (S *)(L->ws + L->pl.pop[L->pl.one ? 0 : src ^ 1]);
     a.mom = mom ? (C *)(L->ws + L->pl.mom) : nullptr;
     a.err = (unsigned int *)(L->ws + L->pl.misc);
     a.tctr = (const long long *)(L->ws + L->pl.misc + 64);
@@ -512,10 +590,23 @@ static void launch3k(const lbm3_lattice *L, const Step3<S> &a, dim3 grid, dim3 b
     else k3_step<S, COLLISION, LINEAR, OFF32><<<grid, block, 0, st>>>(a);
 }
 
+template <class S, int PHASE>
+static void launch_aa(const lbm3_lattice *L, const Step3<S> &a, cudaStream_t st) {
+    const dim3 g(L->pl.ntx, L->pl.nty, L->pl.ntz), b(L->pl.tx, L->pl.ty, L->pl.tz);
+    const int lay = L->p.layout;
+    if (lay == LBM_LAYOUT_STREAM) k3_aa<S, STREAM, PHASE><<<g, b, 0, st>>>(a);
+    else if (lay == LBM_LAYOUT_BUNDLE) k3_aa<S, BUNDLE, PHASE><<<g, b, 0, st>>>(a);
+    else k3_aa<S, COLLISION, PHASE><<<g, b, 0, st>>>(a);
+}
+
+// src: the update's parity (two lattices: the source lattice; AA: the phase).
 template <class S>
 static cudaError_t step3(const lbm3_lattice *L, cudaStream_t st, int src, int toff, int mom) {
     const Step3<S> a = make3<S>(L, src, toff, mom);
-    if (L->p.algo == LBM_LPTL) {
+    if (L->p.algo == LBM_AA) {
+        if (src == 0) launch_aa<S, 0>(L, a, st);
+        else launch_aa<S, 1>(L, a, st);
+    } else if (L->p.algo == LBM_LPTL) {
         const dim3 g((unsigned)((L->pl.N + L->block_1d - 1) / L->block_1d)), b(L->block_1d);
         if (L->off32) launch3k<S, true, true>(L, a, g, b, st);
         else launch3k<S, true, false>(L, a, g, b, st);
@@ -582,7 +673,7 @@ extern "C" lbm_status lbm3_init(lbm3_lattice *L, const double *rho, const double
     const Plan3 &pl = L->pl;
     CK3(cudaStreamSynchronize(st));
     CK3(cudaMemsetAsync(L->ws + pl.pop[0], 0, 19 * (size_t)pl.N * pl.elem, st));
-    CK3(cudaMemsetAsync(L->ws + pl.pop[1], 0, 19 * (size_t)pl.N * pl.elem, st));
+    if (!pl.one) CK3(cudaMemsetAsync(L->ws + pl.pop[1], 0, 19 * (size_t)pl.N * pl.elem, st));
     CK3(cudaMemsetAsync(L->ws + pl.misc, 0, 256, st));
     L->cur = 0;
     L->steps = 0;
@@ -774,8 +865,17 @@ static void set_raw(unsigned char *raw, int storage, int64_t k, double v) {
     }
 }
 
+// AA pattern: the array holds the canonical state only after an even number
+// of updates.
+static lbm_status state_readable(const lbm3_lattice *L) {
+    if (L->pl.one && (L->steps & 1))
+        return lbm_fail(LBM_EINVAL, "AA pattern: the state is accessible after an even number of updates only");
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm3_read_populations(lbm3_lattice *L, void *host, int32_t as) {
     if (!L || !host) return lbm_fail(LBM_EINVAL, "NULL argument");
+    if (state_readable(L) != LBM_OK) return LBM_EINVAL;
     if (as != LBM_F64 && as != LBM_F32) return lbm_fail(LBM_EINVAL, "as must be LBM_F64 or LBM_F32");
     const int64_t N = L->pl.N;
     std::vector<unsigned char> raw(19 * (size_t)N * L->pl.elem);
@@ -792,6 +892,7 @@ extern "C" lbm_status lbm3_read_populations(lbm3_lattice *L, void *host, int32_t
 
 extern "C" lbm_status lbm3_write_populations(lbm3_lattice *L, const void *host, int32_t as) {
     if (!L || !host) return lbm_fail(LBM_EINVAL, "NULL argument");
+    if (state_readable(L) != LBM_OK) return LBM_EINVAL;
     if (as != LBM_F64 && as != LBM_F32) return lbm_fail(LBM_EINVAL, "as must be LBM_F64 or LBM_F32");
     const int64_t N = L->pl.N;
     std::vector<unsigned char> raw(19 * (size_t)N * L->pl.elem);
@@ -808,6 +909,7 @@ extern "C" lbm_status lbm3_write_populations(lbm3_lattice *L, const void *host, 
 
 extern "C" lbm_status lbm3_mass(lbm3_lattice *L, double *out) {
     if (!L || !out) return lbm_fail(LBM_EINVAL, "NULL argument");
+    if (state_readable(L) != LBM_OK) return LBM_EINVAL;
     double *partials = (double *)(L->ws + L->pl.partials);
     LBM3_DISPATCH(L, {
         const Step3<S> a = make3<S>(L, L->cur, 0, 0);

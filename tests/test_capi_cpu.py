@@ -204,3 +204,13 @@ def test_tune_workspace_covers_every_candidate(lib):
     one = lbm.lbm_workspace_bytes(lbm.make_params(512, 256, 0.8, storage="f32", layout="collision",
                                                   algo="lptl"))
     assert need >= 8 * one
+
+
+def test_d3q19_aa_is_one_lattice_and_needs_offset_tables(lib):
+    two = lbm.lbm3_workspace_bytes(lbm.make_params3(32, 16, 8, 0.8, algo="nptl", storage="f32"))
+    one = lbm.lbm3_workspace_bytes(lbm.make_params3(32, 16, 8, 0.8, algo="aa", storage="f32"))
+    assert one <= two - 19 * 32 * 16 * 8 * 4 + 256
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm3_workspace_bytes(lbm.make_params3(32, 16, 8, 0.8, algo="aa",
+                                                  flags=lbm.LBM_FLAG_WIDE_OFFSETS))
+    assert e.value.status == lbm.LBM_EUNSUPPORTED

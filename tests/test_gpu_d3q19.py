@@ -317,3 +317,80 @@ def test_momentum_conserved_over_long_runs3(storage):
     p1 = float(np.sum(cx[:, None] * lat.populations("f64")))
     assert abs(p1 - p0) <= (1e-5 if storage == "f32" else 1e-10) * abs(p0)
     lat.close()
+
+
+# ---------------------------------------------------------------- AA pattern
+
+@pytest.mark.parametrize("case", list(SPECS))
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_aa_fp64_matches_oracle3(case, layout):
+    spec = SPECS[case]
+    T = 40
+    ref = spec.oracle().run(T)
+    lat = spec.gpu(layout=layout, algo="aa", storage="f64", tile=(16, 4, 2))
+    lat.step(T, moments=True).sync()
+    h = lat.populations("f64")
+    rho, ux, uy, uz = lat.moments()
+    fl = ref.solid == 0
+    assert rel_linf(h, ref.h, fl) <= 1e-12
+    assert rel_linf(np.stack([ux, uy, uz]), np.stack([ref.ux, ref.uy, ref.uz]), fl) <= 1e-12
+    assert np.all(h[:, ~fl] == 0.0)
+    lat.close()
+
+
+@pytest.mark.parametrize("storage,rounding", [("f32", "rne"), ("f16s", "sr"), ("bf16s", "rne")])
+def test_aa_bit_identical_to_two_lattice(storage, rounding):
+    """After an even number of updates the AA array is the canonical state:
+    equal, bit for bit, to the two-lattice NPTL result; the moments of an odd
+    update (the pushing phase) are equal too."""
+    for case in ("porous", "duct", "ragged"):
+        spec = SPECS[case]
+        for T in (70, 37):
+            runs = {}
+            for algo, tile in (("nptl", (32, 4, 2)), ("aa", (32, 4, 2)), ("aa", (128, 1, 1))):
+                lat = spec.gpu(layout="bundle", algo=algo, tile=tile, storage=storage, rounding=rounding,
+                               seed=5)
+                lat.step(T, moments=True).sync()
+                mom = lat.moments()
+                pops = lat.populations("f64") if T % 2 == 0 else None
+                runs[(algo, tile)] = (mom, pops)
+                lat.close()
+            base = runs[("nptl", (32, 4, 2))]
+            for key, (mom, pops) in runs.items():
+                assert all(np.array_equal(a, b) for a, b in zip(mom, base[0])), (case, T, key)
+                if pops is not None:
+                    assert np.array_equal(pops, base[1]), (case, T, key)
+
+
+def test_aa_state_access_after_even_updates_only():
+    spec = SPECS["duct"]
+    lat = spec.gpu(layout="stream", algo="aa", storage="f32")
+    lat.step(3).sync()
+    with pytest.raises(lbm.LbmError) as e:
+        lat.populations()
+    assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError):
+        lat.mass()
+    lat.step(1).sync()
+    assert lat.populations().shape == (19, spec.nx * spec.ny * spec.nz)
+    assert np.isfinite(lat.mass())
+    lat.close()
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_aa_pure_streaming_is_bit_exact_shift3(layout):
+    nx, ny, nz, T = 23, 9, 7, 6
+    N = nx * ny * nz
+    rng = np.random.default_rng(5)
+    h0 = rng.normal(0.0, 0.01, size=(19, N))
+    lat = lbm.Lattice3(nx, ny, nz, math.inf, None, layout=layout, algo="aa", storage="f64",
+                       tile=(8, 4, 2))
+    lat.write_populations(h0)
+    lat.step(T).sync()
+    h = lat.populations("f64")
+    c, _ = O.directions3()
+    for i in range(19):
+        exp = np.roll(h0[i].reshape(nz, ny, nx), (T * c[i, 2], T * c[i, 1], T * c[i, 0]),
+                      axis=(0, 1, 2)).ravel()
+        assert np.array_equal(h[i], exp), i
+    lat.close()
