@@ -613,7 +613,7 @@ __device__ __forceinline__ void npol_tile(const Step<S> &a, int bx, int by, int 
 }
 
 template <class S, int L>
-__global__ void __launch_bounds__(kMaxTileThreads) k_npol(const Step<S> a) {
+__global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : 4) k_npol(const Step<S> a) {
     npol_tile<S, L>(a, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y,
                     (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u));
 }
@@ -726,7 +726,7 @@ __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int 
 }
 
 template <class S, int L>
-__global__ void __launch_bounds__(kMaxTileThreads) k_nsol(const Step<S> a) {
+__global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : 4) k_nsol(const Step<S> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     nsol_tile<S, L>(a, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y,
                     (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u), smem_raw);
