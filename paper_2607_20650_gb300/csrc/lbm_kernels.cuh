@@ -956,7 +956,7 @@ __device__ __forceinline__ void batch_item(const BatchCase<S> &bc, int algo, uin
 // cur: source lattice of two-lattice cases, which equals the buffer-grid
 // parity read by one-lattice cases (all cases start together at update 0).
 template <class S, int LK, int AK>
-__global__ void __launch_bounds__(kBatchThreads, LK < 0 ? 2 : (AK <= NPTL ? 5 : 3))
+__global__ void __launch_bounds__(kBatchThreads, LK < 0 ? 2 : (AK <= NPTL ? (sizeof(S) == 8 ? 4 : 6) : 3))
     k_batch(const BatchCase<S> *cases, const BatchTile *tiles, uint32_t ntiles, int cur, int toff,
             int want_moments) {
     using C = typename Codec<S>::C;
