@@ -93,6 +93,7 @@ def _load():
         lib.oracle3_run.restype = ctypes.c_int
         lib.oracle3_mass.argtypes = [P3, u8, d]
         lib.oracle3_mass.restype = ctypes.c_double
+        lib.oracle3_force.argtypes = [P3, u8, u8, d, d]
         _lib = lib
     return _lib
 
@@ -267,3 +268,11 @@ class Lattice3:
 
     def mass(self) -> float:
         return float(_load().oracle3_mass(ctypes.byref(self.case._c()), _u8(self.solid), _dp(self.h)))
+
+    def force(self, body: np.ndarray) -> np.ndarray:
+        """Momentum-exchange force on the body (3 components)."""
+        body = np.ascontiguousarray(body, dtype=np.uint8).reshape(-1)
+        out = np.zeros(3)
+        _load().oracle3_force(ctypes.byref(self.case._c()), _u8(self.solid), _u8(body), _dp(self.h),
+                              _dp(out))
+        return out

@@ -187,3 +187,39 @@ double oracle3_mass(const oracle3_params *p, const uint8_t *solid, const double 
     }
     return s;
 }
+
+/* Momentum-exchange force on a body (the 3-D form of the 2-D oracle's):
+ * sum over fluid nodes x and directions i with x + c_i a body node of
+ * 2 c_i f*_i(x), f* = w + h the stored post-collision populations; links
+ * across a non-periodic face are skipped. */
+void oracle3_force(const oracle3_params *p, const uint8_t *solid, const uint8_t *body, const double *h,
+                   double *F) {
+    tables();
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz;
+    const int ext[3] = {p->nx, p->ny, p->nz};
+    const int bc[3] = {p->bc_x, p->bc_y, p->bc_z};
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                const int64_t n = ((int64_t)z * p->ny + y) * p->nx + x;
+                if (solid[n]) continue;
+                for (int i = 0; i < 19; ++i) {
+                    if (i == 9) continue;
+                    int b[3] = {x + C3[i][0], y + C3[i][1], z + C3[i][2]};
+                    int inside = 1;
+                    for (int a = 0; a < 3; ++a) {
+                        if (b[a] < 0 || b[a] >= ext[a]) {
+                            if (bc[a] != F3_PERIODIC) inside = 0;
+                            b[a] = (b[a] + ext[a]) % ext[a];
+                        }
+                    }
+                    if (!inside) continue;
+                    const int64_t m = ((int64_t)b[2] * p->ny + b[1]) * p->nx + b[0];
+                    if (!body[m]) continue;
+                    const double f = W3[i] + h[(int64_t)i * N + n];
+                    for (int a = 0; a < 3; ++a) acc[a] += 2.0 * C3[i][a] * f;
+                }
+            }
+    for (int a = 0; a < 3; ++a) F[a] = acc[a];
+}

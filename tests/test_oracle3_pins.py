@@ -114,3 +114,26 @@ def test_plane_poiseuille_3d_slip_closed_form():
     par = g / (2 * nu) * z * (H - z)
     slip = g * (16 * (tau - 0.5) ** 2 - 3) / (24 * nu)
     assert np.max(np.abs(ux - par - slip)) / par.max() < 1e-10
+
+
+def test_force_balance_steady_duct_3d():
+    """Momentum exchange (3-D): at steady state the force on the walls (rows
+    of solid nodes on the z faces, everything periodic) equals the body force
+    on the fluid, g * (number of fluid nodes), per update, split equally
+    between the two walls by symmetry; the transverse components vanish."""
+    H, n, g = 8, 3, 1e-5
+    tau = 0.5 + math.sqrt(3.0) / 4.0
+    nu = (tau - 0.5) / 3
+    mask = np.zeros((H + 2, n, n), np.uint8)
+    mask[0] = 1
+    mask[-1] = 1
+    lat = O.Lattice3(O.Case3(n, n, H + 2, tau, fx=g), mask).run(int(40 * H * H / nu))
+    F = lat.force(mask)
+    total = g * n * n * H
+    assert abs(F[0] - total) / total < 1e-9
+    assert abs(F[1]) < 1e-15 and abs(F[2]) < 1e-12
+    bottom = np.zeros_like(mask)
+    bottom[0] = 1
+    Fb = lat.force(bottom)
+    assert abs(Fb[0] - total / 2) / total < 1e-9
+    assert np.all(lat.force(np.zeros_like(mask)) == 0.0)
