@@ -329,7 +329,15 @@ lbm_status lbm3_read_populations(lbm3_lattice *L, void *host, int32_t as);
 lbm_status lbm3_write_populations(lbm3_lattice *L, const void *host, int32_t as);
 /* Total mass sum over fluid nodes of sum_i f_i, accumulated in FP64. */
 lbm_status lbm3_mass(lbm3_lattice *L, double *out);
-/* cells, fluid_cells, steps, tile (tile_y = tile_y * tile_z), bytes per update. */
+/* Momentum-exchange force, as lbm_force in 3-D: sum over links from a fluid
+ * node x to x + c_i with d_body[x + c_i] != 0 (links across a wall face
+ * skipped) of 2 c_i f*_i(x), f* = w + h of the stored state; FP64, fixed
+ * order. d_body: device array of N bytes (NULL = every solid node).
+ * Synchronous; AA: after an even number of updates only. */
+lbm_status lbm3_force(lbm3_lattice *L, const uint8_t *d_body, double out[3]);
+/* cells, fluid_cells, steps, tile (tile_y = tile_y * tile_z), bytes per
+ * update; reserved = 1 when pulls use 64-bit addressing (large lattices or
+ * LBM_FLAG_WIDE_OFFSETS), 0 with the 32-bit offset tables. */
 lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out);
 void lbm3_destroy(lbm3_lattice *L);
 int64_t lbm3_layout_index(int32_t layout, int64_t N, int64_t n, int32_t i);

@@ -163,7 +163,7 @@ __device__ __forceinline__ void pull3(const Step3<S> &a, uint32_t x, uint32_t y,
             if ((lk >> bit(i)) & 1u) {
                 j = opp(i);
             } else if (interior) {
-                s = n - (uint32_t)((cz(i) * (int)ny + cy(i)) * (int)nx + cx(i));
+                s = n - (uint32_t)(((int64_t)cz(i) * ny + cy(i)) * (int64_t)nx + cx(i));
             } else {
                 map3(a.g, (int)x, (int)y, (int)z, i, s);
             }
@@ -392,6 +392,74 @@ __global__ void __launch_bounds__(kReduceThreads) k3_mass(const Step3<S> a, doub
     if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
 }
 
+// Momentum-exchange force: over fluid nodes and links into body nodes
+// (d_body[m] != 0, or solid nodes when body is NULL; links across a
+// non-periodic face are skipped), 2 c_i (w_i + h_i) of the stored state.
+// Per-block partials of the three components, FP64.
+template <class S, int L>
+__global__ void __launch_bounds__(kReduceThreads) k3_force(const Step3<S> a, const uint8_t *body,
+                                                           double *partials) {
+    __shared__ double red[3][kReduceThreads];
+    double acc[3] = {0.0, 0.0, 0.0};
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const int ext[3] = {nx, ny, nz};
+    const int bc[3] = {a.g.bx, a.g.by, a.g.bz};
+    for (uint64_t n64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; n64 < a.N;
+         n64 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t n = (uint32_t)n64;
+        if (a.links[n] == SOLID) continue;
+        const uint32_t z = fdiv(n, a.nxy_magic);
+        const uint32_t r = n - z * (uint32_t)nx * (uint32_t)ny;
+        const uint32_t y = fdiv(r, a.nx_magic);
+        const uint32_t x = r - y * (uint32_t)nx;
+        const int p[3] = {(int)x, (int)y, (int)z};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (i == REST) continue;
+            const int c[3] = {cx(i), cy(i), cz(i)};
+            int b[3];
+            bool inside = true;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                b[k] = p[k] + c[k];
+                if (b[k] < 0 || b[k] >= ext[k]) {
+                    if (bc[k] != PERIODIC) inside = false;
+                    b[k] = b[k] < 0 ? b[k] + ext[k] : b[k] - ext[k];
+                }
+            }
+            if (!inside) continue;
+            const uint32_t m = ((uint32_t)b[2] * (uint32_t)ny + (uint32_t)b[1]) * (uint32_t)nx + (uint32_t)b[0];
+            const bool hit = body ? body[m] != 0 : a.links[m] == SOLID;
+            if (!hit) continue;
+            const double w = sq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0;
+            const double f = w + (double)Codec<S>::dec(a.src[addr<L>(a.N, n, i)]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc[k] += 2.0 * c[k] * f;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = kReduceThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) partials[3 * blockIdx.x + k] = red[k][0];
+}
+
+__global__ void k3_sum3(const double *partials, int nb, double *out) {
+    if (threadIdx.x || blockIdx.x) return;
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += partials[3 * b + k];
+        out[k] = s;
+    }
+}
+
 template <class C>
 __global__ void k3_sum(const double *partials, int nb, double *out) {
     if (threadIdx.x || blockIdx.x) return;
@@ -464,7 +532,7 @@ lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
     pl->links = take(4 * (size_t)N);
     pl->mom_bytes = std::max(4 * (size_t)N * pl->comp, 4 * sizeof(double) * (size_t)std::min<uint64_t>(N, 1 << 16));
     pl->mom = take(pl->mom_bytes);
-    pl->partials = take(sizeof(double) * (kReduceBlocks + 4));
+    pl->partials = take(sizeof(double) * (3 * kReduceBlocks + 4));
     pl->misc = take(256);
     pl->total = off;
     return LBM_OK;
@@ -925,6 +993,24 @@ extern "C" lbm_status lbm3_mass(lbm3_lattice *L, double *out) {
     return check3(L);
 }
 
+extern "C" lbm_status lbm3_force(lbm3_lattice *L, const uint8_t *d_body, double out[3]) {
+    if (!L || !out) return lbm_fail(LBM_EINVAL, "NULL argument");
+    if (state_readable(L) != LBM_OK) return LBM_EINVAL;
+    double *partials = (double *)(L->ws + L->pl.partials);
+    LBM3_DISPATCH(L, {
+        const Step3<S> a = make3<S>(L, L->cur, 0, 0);
+        if (L->p.layout == LBM_LAYOUT_STREAM) k3_force<S, STREAM><<<kReduceBlocks, kReduceThreads, 0, L->stream>>>(a, d_body, partials);
+        else if (L->p.layout == LBM_LAYOUT_BUNDLE) k3_force<S, BUNDLE><<<kReduceBlocks, kReduceThreads, 0, L->stream>>>(a, d_body, partials);
+        else k3_force<S, COLLISION><<<kReduceBlocks, kReduceThreads, 0, L->stream>>>(a, d_body, partials);
+    });
+    CK3(cudaGetLastError());
+    k3_sum3<<<1, 32, 0, L->stream>>>(partials, kReduceBlocks, partials + 3 * kReduceBlocks);
+    CK3(cudaGetLastError());
+    CK3(cudaMemcpyAsync(out, partials + 3 * kReduceBlocks, 3 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    CK3(cudaStreamSynchronize(L->stream));
+    return check3(L);
+}
+
 extern "C" lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out) {
     if (!L || !out) return lbm_fail(LBM_EINVAL, "NULL argument");
     memset(out, 0, sizeof(*out));
@@ -935,5 +1021,6 @@ extern "C" lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out) {
     out->tile_y = L->p.algo == LBM_LPTL ? 1 : L->pl.ty * L->pl.tz;
     out->bytes_per_update = (double)L->fluid * 38.0 * (double)L->pl.elem + 4.0 * (double)L->pl.N;
     out->workspace_bytes = L->pl.total;
+    out->reserved = L->off32 ? 0 : 1;   // 1: the 64-bit addressing path
     return LBM_OK;
 }

@@ -126,6 +126,7 @@ SIGNATURES = {
     "lbm3_read_populations": (_i32, [_vp, _vp, _i32]),
     "lbm3_write_populations": (_i32, [_vp, _vp, _i32]),
     "lbm3_mass": (_i32, [_vp, _P(_dbl)]),
+    "lbm3_force": (_i32, [_vp, _vp, _P(_dbl)]),
     "lbm3_get_info": (_i32, [_vp, _P(lbm_info)]),
     "lbm3_destroy": (None, [_vp]),
     "lbm3_layout_index": (_i64, [_i32, _i64, _i64, _i32]),
@@ -455,10 +456,18 @@ def lbm3_mass(h) -> float:
     return out.value
 
 
+def lbm3_force(h, body=None) -> np.ndarray:
+    out = (ctypes.c_double * 3)()
+    _check(load().lbm3_force(h, _ptr(body), out), "lbm3_force")
+    return np.array([out[0], out[1], out[2]])
+
+
 def lbm3_get_info(h) -> dict:
     i = lbm_info()
     _check(load().lbm3_get_info(h, ctypes.byref(i)), "lbm3_get_info")
-    return {f: getattr(i, f) for f, _ in lbm_info._fields_ if f != "reserved"}
+    out = {f: getattr(i, f) for f, _ in lbm_info._fields_ if f != "reserved"}
+    out["wide_addressing"] = bool(i.reserved)
+    return out
 
 
 def lbm3_destroy(h):
@@ -624,6 +633,10 @@ class Lattice3:
 
     def mass(self) -> float:
         return lbm3_mass(self.h)
+
+    def force(self, body=None):
+        """body: device uint8 tensor of N bytes, or None for every solid node."""
+        return lbm3_force(self.h, body)
 
     def info(self) -> dict:
         return lbm3_get_info(self.h)

@@ -394,3 +394,116 @@ def test_aa_pure_streaming_is_bit_exact_shift3(layout):
                       axis=(0, 1, 2)).ravel()
         assert np.array_equal(h[i], exp), i
     lat.close()
+
+
+@pytest.mark.parametrize("case", ["porous", "duct"])
+@pytest.mark.parametrize("layout,algo", [("stream", "nptl"), ("bundle", "lptl"), ("collision", "nptl"),
+                                         ("bundle", "aa")])
+def test_force_matches_oracle3(case, layout, algo):
+    """FP64 momentum-exchange force on the solid mask (and on a body given as
+    a device mask) against the D3Q19 oracle after 40 updates. The force is a
+    sum over some 10^3-10^4 body links of terms 2 c_i f_i with f_i ~ w_i
+    ~ 0.06 that cancel to ~1e-2: summed in two orders (block tree on the GPU,
+    sequential in the oracle), the results may differ by ~eps * 0.1 * links
+    ~ 1e-13 absolute, so the bar is 1e-11 relative to the largest component."""
+    spec = SPECS[case]
+    T = 40
+    ref = spec.oracle().run(T)
+    lat = spec.gpu(layout=layout, algo=algo, storage="f64", tile=(16, 4, 2))
+    lat.step(T).sync()
+    body = torch.from_numpy(spec.mask.astype(np.uint8)).cuda()
+    f_gpu = lat.force(body)
+    f_ref = ref.force(spec.mask)
+    assert np.max(np.abs(f_gpu - f_ref)) <= 1e-11 * max(np.max(np.abs(f_ref)), 1e-14)
+    f_all = lat.force(None)
+    f_ref_all = ref.force(ref.solid)
+    assert np.max(np.abs(f_all - f_ref_all)) <= 1e-11 * max(np.max(np.abs(f_ref_all)), 1e-14)
+    lat.close()
+
+
+def _effective_solid_at(mask3, bc, nodes):
+    """Effective solidity (mask, or all 18 pulls bouncing) of the given
+    (z, y, x) nodes only."""
+    c, _ = O.directions3()
+    nz, ny, nx = mask3.shape
+    ext = (nx, ny, nz)
+    out = []
+    for (z, y, x) in nodes:
+        if mask3[z, y, x]:
+            out.append(True)
+            continue
+        open_ = False
+        for i in range(19):
+            if i == 9:
+                continue
+            s = [x - c[i, 0], y - c[i, 1], z - c[i, 2]]
+            ok = True
+            for a in range(3):
+                if s[a] < 0 or s[a] >= ext[a]:
+                    if bc[a] != P:
+                        ok = False
+                    s[a] %= ext[a]
+            if ok and not mask3[s[2], s[1], s[0]]:
+                open_ = True
+                break
+        out.append(not open_)
+    return np.array(out)
+
+
+def test_wide_addressing_path_at_136m_nodes():
+    """520 x 512 x 512 (136M nodes, 19 N > 2^31: 64-bit addressing), FP16
+    storage, stream layout: one update of sampled nodes equals the oracle's
+    update of their 3x3x3 neighbourhood taken from the stored state (decoded
+    exactly from the device), within one FP16 ulp."""
+    nx, ny, nz = 520, 512, 512
+    N = nx * ny * nz
+    xs, ys, zs = np.arange(nx), np.arange(ny), np.arange(nz)
+    mask = (((xs[None, None, :] // 13 + ys[None, :, None] // 11 + zs[:, None, None] // 7) % 9) == 0)
+    mask = mask.astype(np.uint8)
+    bc = (P, P, W)
+    lat = lbm.Lattice3(nx, ny, nz, 0.8, mask, force=(1e-5, 0.0, 0.0), bc=bc, storage="f16s",
+                       layout="stream", algo="nptl", tile=(128, 1, 1))
+    assert lat.info()["wide_addressing"]
+    ux = np.broadcast_to(0.03 * np.sin(2 * np.pi * ys / ny)[None, :, None], (nz, ny, nx)).ravel()
+    uz = np.broadcast_to(0.01 * np.cos(2 * np.pi * xs / nx)[None, None, :], (nz, ny, nx)).ravel()
+    lat.init(None, np.where(mask.ravel() > 0, 0.0, ux), None, np.where(mask.ravel() > 0, 0.0, uz))
+    del ux, uz
+    # samples: interior in z (the oracle box must not wrap the wall axis)
+    rs = G.SplitMix64(17, 3)
+    cand = list(zip(rs.integers(48, 1, nz - 2), rs.integers(48, 0, ny - 1), rs.integers(48, 0, nx - 1)))
+    idx = []
+    boxes = []
+    for (z, y, x) in cand:
+        z, y, x = int(z), int(y), int(x)
+        zi = [z - 1, z, z + 1]
+        yi = [(y + d) % ny for d in (-1, 0, 1)]
+        xi = [(x + d) % nx for d in (-1, 0, 1)]
+        nodes = [(a, b, c) for a in zi for b in yi for c in xi]
+        eff = _effective_solid_at(mask, bc, nodes)
+        if eff[13]:
+            continue
+        boxes.append(((z, y, x), nodes, eff))
+        idx.extend((a * ny + b) * nx + c for (a, b, c) in nodes)
+    assert len(boxes) >= 20
+    idx = torch.tensor(idx, dtype=torch.int64, device="cuda")
+    slot = torch.arange(19, device="cuda")[:, None] * N          # stream layout: i N + n
+    lattice_bytes = 19 * N * 2
+    second = (lattice_bytes + 255) // 256 * 256                   # lattice 1 follows lattice 0
+
+    def stored(which):
+        torch.cuda.synchronize()
+        raw = lat.workspace[which * second: which * second + lattice_bytes].view(torch.float16)
+        return raw[(slot + idx[None, :]).reshape(-1)].reshape(19, -1).double().cpu().numpy()
+
+    lat.step(1).sync()
+    h1 = stored(1)          # after an odd number of updates the state is in lattice 1
+    lat.step(1).sync()
+    h2 = stored(0)
+    lat.close()
+    for k, ((z, y, x), nodes, eff) in enumerate(boxes):
+        cols = slice(27 * k, 27 * k + 27)
+        ref = O.Lattice3(O.Case3(3, 3, 3, 0.8, 1e-5, 0.0, 0.0, P, P, P), eff.astype(np.uint8).reshape(3, 3, 3))
+        ref.set_h(h1[:, cols])
+        ref.run(1)
+        got, exp = h2[:, cols][:, 13], ref.h[:, 13]
+        assert np.all(np.abs(got - exp) <= 2.0 ** -10 * np.abs(exp) + 1e-7), (x, y, z)
