@@ -110,8 +110,10 @@ __global__ void k3_count(const uint32_t *links, uint32_t N, unsigned long long *
     if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
 }
 
+// Store hint: 0 plain stores (measured fastest), 1 evict-first (.cs)
+// everywhere, 2 evict-first for the bundle layout only.
 #ifndef LBM3_ST_HINT
-#define LBM3_ST_HINT 0   // 0 plain stores (measured fastest here), 1 streaming (.cs), 2 .cs for BUNDLE
+#define LBM3_ST_HINT 0
 #endif
 template <class S, int L>
 __device__ __forceinline__ void st3(S *p, S v) {
@@ -224,7 +226,9 @@ __device__ __forceinline__ void zero3(const Step3<S> &a, uint32_t n) {
 }
 
 // LINEAR: one node per thread over n (LPTL); otherwise 3-D tiles (NPTL).
-// OFF32: 19 N fits 31 bits, pulls of interior nodes use the offset tables.
+// OFF32: the offset tables fit 31 bits; every pull uses them (periodic wrap
+// as node-index corrections); otherwise 64-bit addressing with the general
+// edge mapping for nodes on the box faces.
 template <class S, int L, bool LINEAR, bool OFF32>
 __global__ void __launch_bounds__(512, sizeof(S) == 8 ? 2 : 3) k3_step(const Step3<S> a) {
     using C = typename Codec<S>::C;
@@ -460,7 +464,6 @@ __global__ void k3_sum3(const double *partials, int nb, double *out) {
     }
 }
 
-template <class C>
 __global__ void k3_sum(const double *partials, int nb, double *out) {
     if (threadIdx.x || blockIdx.x) return;
     double s = 0.0;
@@ -986,7 +989,7 @@ extern "C" lbm_status lbm3_mass(lbm3_lattice *L, double *out) {
         else k3_mass<S, COLLISION><<<kReduceBlocks, kReduceThreads, 0, L->stream>>>(a, partials);
     });
     CK3(cudaGetLastError());
-    k3_sum<double><<<1, 32, 0, L->stream>>>(partials, kReduceBlocks, partials + kReduceBlocks);
+    k3_sum<<<1, 32, 0, L->stream>>>(partials, kReduceBlocks, partials + kReduceBlocks);
     CK3(cudaGetLastError());
     CK3(cudaMemcpyAsync(out, partials + kReduceBlocks, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
     CK3(cudaStreamSynchronize(L->stream));
