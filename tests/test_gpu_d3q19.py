@@ -507,3 +507,68 @@ def test_wide_addressing_path_at_136m_nodes():
         ref.run(1)
         got, exp = h2[:, cols][:, 13], ref.h[:, 13]
         assert np.all(np.abs(got - exp) <= 2.0 ** -10 * np.abs(exp) + 1e-7), (x, y, z)
+
+
+# ---------------------------------------------------------------- degenerate inputs
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 7), (5, 1, 1), (2, 3, 2), (1, 4, 3)])
+@pytest.mark.parametrize("algo", ["lptl", "nptl", "aa"])
+def test_tiny_periodic_boxes_match_oracle3(shape, algo):
+    """Boxes where a node is its own neighbour (extent 1) or its neighbour on
+    both sides (extent 2), fully periodic, with a force and random velocities."""
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    r = G.SplitMix64(31, nx * 100 + ny * 10 + nz)
+    u = [r.uniform(N, -0.02, 0.02) for _ in range(3)]
+    rho = 1.0 + r.uniform(N, -0.01, 0.01)
+    case = O.Case3(nx, ny, nz, 0.7, 2e-5, -1e-5, 3e-6, P, P, P)
+    ref = O.Lattice3(case, None, rho, *u).run(12)
+    lat = lbm.Lattice3(nx, ny, nz, 0.7, None, force=(2e-5, -1e-5, 3e-6), algo=algo, storage="f64",
+                       tile=(8, 4, 2))
+    lat.init(rho, *u).step(12, moments=True).sync()
+    assert rel_linf(lat.populations("f64"), ref.h) <= 1e-12
+    lat.close()
+
+
+@pytest.mark.parametrize("algo", ["lptl", "nptl", "aa"])
+def test_all_solid_and_walled_strip3(algo):
+    """An all-solid box stays zero with no fluid nodes; a one-node-wide strip
+    between walls on two axes (every transverse pull bounces) matches the
+    oracle."""
+    m = np.ones((4, 5, 6), np.uint8)
+    lat = lbm.Lattice3(6, 5, 4, 0.8, m, algo=algo, storage="f32", tile=(8, 4, 2))
+    lat.step(6).sync()
+    assert lat.info()["fluid_cells"] == 0
+    assert np.all(lat.populations() == 0.0) and lat.mass() == 0.0
+    lat.close()
+    nx, ny, nz = 9, 1, 1
+    case = O.Case3(nx, ny, nz, 0.8, 1e-5, 0.0, 0.0, P, W, W)
+    ref = O.Lattice3(case, None).run(10)
+    lat = lbm.Lattice3(nx, ny, nz, 0.8, None, force=(1e-5, 0.0, 0.0), bc=(P, W, W), algo=algo,
+                       storage="f64", tile=(8, 4, 2))
+    lat.step(10).sync()
+    assert rel_linf(lat.populations("f64"), ref.h) <= 1e-12
+    lat.close()
+
+
+@pytest.mark.parametrize("tile", [(8, 8, 8), (512, 1, 1), (1, 1, 64), (7, 5, 3)])
+def test_largest_and_odd_tiles3(tile):
+    spec = SPECS["porous"]
+    base = spec.gpu(layout="bundle", algo="lptl", storage="f32")
+    base.step(20, moments=True).sync()
+    ref = base.populations("f32")
+    base.close()
+    for algo in ("nptl", "aa"):
+        lat = spec.gpu(layout="bundle", algo=algo, storage="f32", tile=tile)
+        lat.step(20, moments=True).sync()
+        assert np.array_equal(lat.populations("f32"), ref), (algo, tile)
+        lat.close()
+
+
+def test_bad_shapes_rejected3():
+    for shape in [(0, 4, 4), (4, -1, 4), (4, 4, 0)]:
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm3_workspace_bytes(lbm.make_params3(*shape, 0.8))
+        assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm3_workspace_bytes(lbm.make_params3(8, 8, 8, 0.8, tile=(8, 8, 9)))
