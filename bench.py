@@ -182,11 +182,12 @@ def kernel_name(args, tile=(32, 4)) -> str:
 
 
 def launches_for(k: int, graph_block: int = 64) -> int:
-    """Kernels one lbm_step(k) call enqueues: k updates, one counter bump per
-    graph block and one after the directly launched remainder."""
+    """Kernels one lbm_step(k) call (no moments) enqueues: k updates, one
+    counter bump per graph block and one after the directly launched
+    remainder."""
     n = 0
     left = k
-    while left > graph_block:
+    while left >= graph_block:
         n += graph_block + 1
         left -= graph_block
     if left > 0:
@@ -194,28 +195,44 @@ def launches_for(k: int, graph_block: int = 64) -> int:
     return n
 
 
-def time_steps(lat, k, torch):
-    """k updates bracketed by CUDA events on the lattice's own stream."""
+def chunks_of(k: int, runs: int = 10) -> list[int]:
+    """k updates split into up to `runs` consecutive runs (multiples of 64
+    where possible, so graphs of whole blocks carry most of each run)."""
+    if k < 2 * runs:
+        return [k]
+    base = max(64, (k // runs) // 64 * 64)
+    out = []
+    left = k
+    while left > 0:
+        c = min(base, left)
+        out.append(c)
+        left -= c
+    if len(out) > 1 and out[-1] < base // 2:
+        out[-2] += out.pop()
+    return out
+
+
+def time_steps(lat, k, torch, runs: int = 10):
+    """k updates bracketed by CUDA events on the lattice's own stream, issued
+    as consecutive runs (the paper's protocol: runs, median, min / max) with
+    an event between runs; returns (total seconds, per-update ms of each run,
+    run lengths)."""
     from paper_2607_20650_gb300 import lbm
     s = lat.torch_stream
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    parts = chunks_of(k, runs)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
     torch.cuda.synchronize()
-    e0.record(s)
-    lbm.lbm_step(lat.h, k, False)
-    e1.record(s)
-    e1.synchronize()
+    ev[0].record(s)
+    for j, c in enumerate(parts):
+        lbm.lbm_step(lat.h, c, False)
+        ev[j + 1].record(s)
+    ev[-1].synchronize()
     lbm.lbm_sync(lat.h)
-    return e0.elapsed_time(e1) / 1e3
+    per = [ev[j].elapsed_time(ev[j + 1]) / c for j, c in enumerate(parts)]
+    return ev[0].elapsed_time(ev[-1]) / 1e3, per, parts
 
 
-def cpu_sample(target_s: float = 12.0):
-    """FP64 oracle on the 2048x1024 porous sub-run (same disc statistics,
-    seed 33) for as many updates as fit ~target_s seconds."""
-    import oracle as O
-    from paper_2607_20650_gb300 import geometry as G
-    nx, ny = 2048, 1024
-    mask = G.porous_discs(nx, ny, seed=33)
-    lat = O.Lattice(O.Case(nx, ny, 0.9, fx=1e-6), mask)
+def _oracle_rate(lat, cells: int, target_s: float) -> tuple[float, int, float]:
     t = time.perf_counter()
     lat.run(2)
     per = (time.perf_counter() - t) / 2
@@ -223,10 +240,36 @@ def cpu_sample(target_s: float = 12.0):
     t = time.perf_counter()
     lat.run(k)
     dt = time.perf_counter() - t
-    return {"value": nx * ny * k / dt / 1e6, "unit": "MLUPS", "cores": O.omp_threads(),
-            "kind": "oracle",
+    return cells * k / dt / 1e6, k, dt
+
+
+def cpu_sample(target_s: float = 12.0):
+    """FP64 oracle on the 2048x1024 porous sub-run (same disc statistics,
+    seed 33) for as many updates as fit ~target_s seconds on every host
+    thread; then the same on one thread, and the Poiseuille 256x64 and
+    Karman 2048x512 configurations briefly (all threads)."""
+    import oracle as O
+    from paper_2607_20650_gb300 import geometry as G
+    nx, ny = 2048, 1024
+    mask = G.porous_discs(nx, ny, seed=33)
+    lat = O.Lattice(O.Case(nx, ny, 0.9, fx=1e-6), mask)
+    threads = O.omp_threads()
+    mlups, k, dt = _oracle_rate(lat, nx * ny, target_s)
+    O.set_threads(1)
+    one, k1, dt1 = _oracle_rate(lat, nx * ny, 3.0)
+    O.set_threads(threads)
+    pw = G.poiseuille()
+    pois, _, _ = _oracle_rate(O.Lattice(O.Case(pw.nx, pw.ny, pw.tau, fx=pw.fx, bc_s=pw.bc_s, bc_n=pw.bc_n),
+                                        pw.mask), pw.nx * pw.ny, 1.5)
+    kw = G.karman()
+    karman, _, _ = _oracle_rate(O.Lattice(O.Case(kw.nx, kw.ny, kw.tau, ux_in=kw.ux_in, bc_w=kw.bc_w,
+                                                 bc_e=kw.bc_e, bc_s=kw.bc_s, bc_n=kw.bc_n),
+                                          kw.mask, ux=kw.ux0, uy=kw.uy0), kw.nx * kw.ny, 2.0)
+    return {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
             "sample": f"porous 2048x1024 (seed 33, same statistics), {k} FP64 updates, "
-                      f"{dt:.1f} s, OpenMP threads {O.omp_threads()}"}
+                      f"{dt:.1f} s, OpenMP threads {threads}",
+            "one_core_MLUPS": one, "one_core_sample": f"{k1} updates, {dt1:.1f} s",
+            "poiseuille_256x64_MLUPS": pois, "karman_2048x512_MLUPS": karman}
 
 
 def run_reference(args):
@@ -296,7 +339,7 @@ def run_ours(args):
 
     barrier()
     clk = Clocks(smi_id(torch, local))
-    dt = time_steps(lat, args.steps, torch)
+    dt, per_run, parts = time_steps(lat, args.steps, torch)
     clocks = clk.stop()
     barrier()
     if dist is not None:
@@ -320,7 +363,9 @@ def run_ours(args):
                    "fluid_nodes": info["fluid_cells"], "nodes": cells,
                    "l2": "inputs larger than L2 (two 4.8 GB lattices)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "gpu_launches": launches_for(args.steps),
+        "gpu_launches": sum(launches_for(c) for c in parts),
+        "runs": {"updates": parts, "ms_per_update_median": statistics.median(per_run),
+                 "ms_per_update_min": min(per_run), "ms_per_update_max": max(per_run)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": info["bytes_per_update"],
@@ -365,7 +410,8 @@ def variants(args, mask, torch, world):
                      ("bf16s_rne_bundle_nptl_64x4", dict(storage="bf16s", layout="bundle", tile=(64, 4))),
                      ("f16s_sr_bundle_nptl_64x4", dict(storage="f16s", layout="bundle", tile=(64, 4),
                                                        rounding="sr", seed=7)),
-                     ("f16s_rne_stream_npol_32x8", dict(storage="f16s", algo="npol", tile=(32, 8)))]:
+                     ("f16s_rne_stream_npol_32x8", dict(storage="f16s", algo="npol", tile=(32, 8))),
+                     ("bf16s_rne_stream_npol_32x8", dict(storage="bf16s", algo="npol", tile=(32, 8)))]:
         kw = dict(kw)
         kw.setdefault("layout", "stream")
         geo = kw.pop("geo", "porous")
@@ -374,8 +420,9 @@ def variants(args, mask, torch, world):
                           bc=(lbm.PERIODIC,) * 4, **kw)
         info = lat.info()
         lat.step(args.warmup).sync()
-        dt = time_steps(lat, k, torch)
+        dt, per_run, _ = time_steps(lat, k, torch, runs=4)
         out[name] = {"MLUPS": nx * ny * k / dt / 1e6, "ms_per_step": dt / k * 1e3,
+                     "ms_per_step_min_max": [min(per_run), max(per_run)],
                      "GBps_algorithmic": info["bytes_per_update"] / (dt / k) / 1e9,
                      "frac_of_measured_hbm": info["bytes_per_update"] / (dt / k) / 1e9 / hbm,
                      "bytes_per_update": info["bytes_per_update"],

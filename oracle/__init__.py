@@ -84,6 +84,7 @@ def _load():
         lib.oracle_mass.restype = ctypes.c_double
         lib.oracle_force.argtypes = [P(_Params), u8, u8, d, d]
         lib.oracle_omp_threads.restype = ctypes.c_int
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
         P3 = P(_Params3)
         lib.oracle3_directions.argtypes = [P(ctypes.c_int32), d]
         lib.oracle3_equilibrium.argtypes = [ctypes.c_double] * 4 + [d]
@@ -131,6 +132,11 @@ class Case:
 
 def omp_threads() -> int:
     return int(_load().oracle_omp_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's parallel loops from now on."""
+    _load().oracle_set_threads(int(n))
 
 
 def equilibrium(drho: float, ux: float, uy: float) -> np.ndarray:

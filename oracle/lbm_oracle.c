@@ -81,6 +81,15 @@ int oracle_omp_threads(void) {
 #endif
 }
 
+/* Thread count of the following parallel loops (timing on one core). */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Eq. (2) in deviation form: h_i^eq for density deviation drho = rho - 1. */
 void oracle_equilibrium(double drho, double ux, double uy, double *heq) {
     double usq = ux * ux + uy * uy;

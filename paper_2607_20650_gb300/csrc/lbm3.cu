@@ -855,7 +855,7 @@ extern "C" lbm_status lbm3_step(lbm3_lattice *L, int64_t nsteps, uint32_t want_m
     if (nsteps < 0) return lbm_fail(LBM_EINVAL, "nsteps must be >= 0");
     const int64_t G = 64;
     int64_t left = nsteps;
-    while (!(L->p.flags & LBM_FLAG_NO_GRAPH) && left > G) {
+    while (!(L->p.flags & LBM_FLAG_NO_GRAPH) && (left > G || (left == G && !want_moments))) {
         cudaGraphExec_t &ex = L->graph[L->cur];
         if (!ex) {
             cudaGraph_t gr = nullptr;

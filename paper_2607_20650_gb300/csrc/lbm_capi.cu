@@ -356,7 +356,8 @@ extern "C" lbm_status lbm_step(lbm_lattice *L, int64_t nsteps, uint32_t want_mom
     if (nsteps < 0) return lbm_fail(LBM_EINVAL, "nsteps must be >= 0");
     int64_t left = nsteps;
     const bool graphs = !(L->p.flags & LBM_FLAG_NO_GRAPH);
-    while (graphs && left > L->graph_steps) {
+    // whole graph blocks; the last block runs directly when it must store moments
+    while (graphs && (left > L->graph_steps || (left == L->graph_steps && !want_moments))) {
         cudaGraphExec_t ex;
         lbm_status s = get_graph(L, &ex);
         if (s != LBM_OK) return s;
