@@ -4,8 +4,8 @@
 // as future work), the three layouts generalised (stream, bundle = directions
 // sharing a source row, collision), periodic or half-way wall faces,
 // bounce-back at solid nodes, Guo force, FP64/FP32/FP16/BF16 shifted storage,
-// on-the-fly moments, FP64 mass, CUDA graphs. C ABI: the lbm3_* calls of
-// include/lbm.h.
+// on-the-fly moments, FP64 mass and momentum-exchange force, CUDA graphs.
+// C ABI: the lbm3_* calls of include/lbm.h.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -64,7 +64,8 @@ struct Step3 {
     uint64_t nx_magic, nxy_magic;   // ceil(2^64 / nx), ceil(2^64 / (nx ny)); 0 for 1
     int zero_fill;                  // lanes of a warp hold consecutive nodes
     // 32-bit element offsets from the base of direction i at node n (base =
-    // lattice + mult3(i) n): own slot, interior pull, bounced pull.
+    // lattice + mult3(i) n): own slot i (os), slot i of node n - c_i before
+    // any periodic correction (op), own slot opp(i) for a bounced pull (ob).
     int32_t os[Q], op[Q], ob[Q];
     int32_t oq[Q];   // AA push: slot opp(i) of node n + c_i, from the base of direction i
 };
