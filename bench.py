@@ -66,6 +66,8 @@ def parse():
                     help="d3q19: time only the 3-D extension on an n3^3 sphere packing")
     ap.add_argument("--n3", type=int, default=384)
     ap.add_argument("--geo3", default="porous", choices=["porous", "fluid"])
+    ap.add_argument("--batch-only", action="store_true",
+                    help="time only the 256-channel batched ensemble (profiling)")
     return ap.parse_args()
 
 
@@ -626,6 +628,15 @@ def main():
         run_reference(args)
     elif args.lattice == "d3q19":
         run_d3q19(args)
+    elif args.batch_only:
+        import torch
+        from paper_2607_20650_gb300 import build, lbm
+        build.build()
+        lbm.load()
+        b = batched(args, torch)
+        print(json.dumps({"metric": "batched D2Q9 BGK MLUPS (256 channels)", "value": b["batched_MLUPS"],
+                          "unit": "MLUPS", "n_gpus": 1, "steps": b["steps"], "higher_is_better": True,
+                          "config": {"workload": "256 seeded channels, 37.1M nodes, FP32"}, "batched": b}))
     else:
         run_ours(args)
 
