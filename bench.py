@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--tile", default="")
     ap.add_argument("--layout", default="bundle", choices=["stream", "bundle", "collision"])
     ap.add_argument("--algo", default="nptl", choices=["lptl", "nptl", "npol", "nsol", "aa"],
-                    help="D3Q19 (--lattice d3q19): lptl, nptl or aa")
+                    help="D3Q19 (--lattice d3q19): lptl, nptl, npol or aa")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s", "f64"])
     ap.add_argument("--lattice", default="d2q9", choices=["d2q9", "d3q19"],
                     help="d3q19: time only the 3-D extension on an n3^3 sphere packing")
@@ -499,12 +499,15 @@ def d3q19(args, torch):
                           ("f32_stream_nptl_128x1x1_porous", "porous", dict(storage="f32", layout="stream")),
                           ("f32_collision_nptl_128x1x1_porous", "porous", dict(storage="f32", layout="collision")),
                           ("f16s_rne_bundle_nptl_128x1x1_porous", "porous", dict(storage="f16s", layout="bundle")),
-                          ("f32_bundle_aa_128x1x1_porous", "porous", dict(storage="f32", layout="bundle", algo="aa"))]:
+                          ("f32_bundle_aa_128x1x1_porous", "porous", dict(storage="f32", layout="bundle", algo="aa")),
+                          ("f32_stream_npol_32x8x2_porous", "porous", dict(storage="f32", layout="stream", algo="npol",
+                                                                          tile=(32, 8, 2)))]:
         m = porous if geo == "porous" else np.zeros_like(porous)
         stream = torch.cuda.Stream()
         kw = dict(kw)
         kw.setdefault("algo", "nptl")
-        lat = lbm.Lattice3(n, n, n, 0.8, m, stream=stream, force=(1e-6, 0.0, 0.0), tile=(128, 1, 1), **kw)
+        kw.setdefault("tile", (128, 1, 1))
+        lat = lbm.Lattice3(n, n, n, 0.8, m, stream=stream, force=(1e-6, 0.0, 0.0), **kw)
         info = lat.info()
         lat.step(args.warmup).sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

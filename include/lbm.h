@@ -288,10 +288,13 @@ void lbm_batch_destroy(lbm_batch *B);
  * {0}, {1,2,3}, {4}, {5,6,7}, {8,9,10}, {11,12,13}, {14}, {15,16,17}, {18},
  * a group of size s starting at direction b stored at b N + s n + (i - b).
  * Algorithms: LPTL and NPTL (3-D tiles tile_x * tile_y * tile_z <= 512,
- * 0,0,0 = 128 x 1 x 1; tile_z <= 64), two lattices; AA (the same tiles, one
- * lattice, as in 2-D: populations and mass accessible after an even number
- * of updates only, LBM_EINVAL otherwise; needs 32-bit offset tables, i.e.
- * roughly 19 N < 2^31, LBM_EUNSUPPORTED otherwise). Faces per axis: PERIODIC or WALL
+ * 0,0,0 = 128 x 1 x 1; tile_z <= 64), two lattices; NPOL (one lattice and a
+ * buffer grid: per tile and parity, the five populations leaving each node
+ * of each of the six tile faces, 2 x tiles x 10 (ty tz + tx tz + tx ty)
+ * values); AA (the same tiles, one lattice, as in 2-D: populations and mass
+ * accessible after an even number of updates only, LBM_EINVAL otherwise;
+ * needs 32-bit offset tables, i.e. roughly 19 N < 2^31, LBM_EUNSUPPORTED
+ * otherwise). All produce the same bits at equal storage. Faces per axis: PERIODIC or WALL
  * (half-way bounce-back); solid mask nodes bounce back; a fluid node whose
  * 18 pulls all bounce is treated as solid. Storage, rounding, Guo force,
  * graphs and errors as in 2-D. Workspace: 2 x 19 N elements, 4 N bytes of
@@ -301,7 +304,7 @@ typedef struct lbm3_params {
     double tau;              /* relaxation time, > 1/2 */
     double force[3];         /* Guo body force */
     int32_t bc_x, bc_y, bc_z;   /* LBM_BC_PERIODIC or LBM_BC_WALL, both faces of the axis */
-    int32_t layout, algo, storage, rounding;   /* algo: LBM_LPTL, LBM_NPTL or LBM_AA */
+    int32_t layout, algo, storage, rounding;   /* algo: LBM_LPTL, LBM_NPTL, LBM_NPOL or LBM_AA */
     uint64_t seed;
     int32_t tile_x, tile_y, tile_z;
     uint32_t flags;          /* LBM_FLAG_NO_GRAPH, LBM_FLAG_WIDE_OFFSETS */

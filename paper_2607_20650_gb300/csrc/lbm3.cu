@@ -326,6 +326,215 @@ __global__ void __launch_bounds__(512, PHASE == 0 ? (sizeof(S) == 8 ? 1 : 2) : (
     }
 }
 
+// ------------------------------------------------------------ NPOL (3-D)
+// Buffer grid: per tile and parity, for each of the six tile faces the five
+// populations that leave each face node through it (c_a = +1 for the high
+// face of axis a, -1 for the low face). Face order x+, x-, y+, y-, z+, z-;
+// a face of axis x holds ty tz slots per direction (position ly + ty lz),
+// of axis y tx tz (lx + tx lz), of axis z tx ty (lx + tx ly).
+struct Tile3 {
+    int tx, ty, tz;
+    __host__ __device__ int nodes(int axis) const { return axis == 0 ? ty * tz : (axis == 1 ? tx * tz : tx * ty); }
+    __host__ __device__ int64_t per_tile() const { return 10ll * (nodes(0) + nodes(1) + nodes(2)); }
+    __host__ __device__ int64_t face_off(int axis, int sign) const {
+        int64_t o = 0;
+        for (int a = 0; a < axis; ++a) o += 10ll * nodes(a);
+        return o + (sign > 0 ? 0 : 5ll * nodes(axis));
+    }
+    __host__ __device__ int pos(int axis, int lx, int ly, int lz) const {
+        return axis == 0 ? ly + ty * lz : (axis == 1 ? lx + tx * lz : lx + tx * ly);
+    }
+};
+
+// Rank of direction i among the five directions with the same nonzero c_a.
+__host__ __device__ constexpr int face_rank(int i, int axis) {
+    int r = 0;
+    for (int j = 0; j < i; ++j) {
+        const int cj = axis == 0 ? cx(j) : (axis == 1 ? cy(j) : cz(j));
+        const int ci = axis == 0 ? cx(i) : (axis == 1 ? cy(i) : cz(i));
+        if (cj == ci) ++r;
+    }
+    return r;
+}
+
+// Publish the outgoing populations e (canonical order) of the node at local
+// (lx, ly, lz) of tile t, whose bounds are lo[] .. hi[] (global).
+template <class S>
+__device__ __forceinline__ void publish3(S *hw, const Tile3 &T, int64_t t, const int *p, const int *lo,
+                                         const int *hi, int lx, int ly, int lz, const S *e) {
+    S *base = hw + t * T.per_tile();
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int pos = T.pos(a, lx, ly, lz);
+        const int fn = T.nodes(a);
+        if (p[a] == hi[a]) {
+            S *f = base + T.face_off(a, 1);
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if ((a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i))) > 0) f[face_rank(i, a) * fn + pos] = e[i];
+        }
+        if (p[a] == lo[a]) {
+            S *f = base + T.face_off(a, -1);
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if ((a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i))) < 0) f[face_rank(i, a) * fn + pos] = e[i];
+        }
+    }
+}
+
+// One lattice, pull: every node of the tile reads its 19 incoming values
+// (sources in the tile from the lattice, from other tiles out of the buffer
+// grid the previous update wrote), a block barrier separates all reads from
+// the in-place writes, and face nodes publish their outgoing values.
+template <class S, int L, bool OFF32>
+__global__ void __launch_bounds__(512, sizeof(S) == 8 ? 1 : 2) k3_npol(const Step3<S> a, const S *hr, S *hw) {
+    using C = typename Codec<S>::C;
+    using A = Ar<C>;
+    const Tile3 T{a.tx, a.ty, a.tz};
+    const int ext[3] = {a.g.nx, a.g.ny, a.g.nz};
+    const int b[3] = {(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z};
+    const int tdim[3] = {a.tx, a.ty, a.tz};
+    const int l[3] = {(int)threadIdx.x, (int)threadIdx.y, (int)threadIdx.z};
+    int lo[3], hi[3], p[3];
+    bool valid = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = b[k] * tdim[k];
+        hi[k] = min(lo[k] + tdim[k], ext[k]) - 1;
+        p[k] = lo[k] + l[k];
+        valid = valid && p[k] <= hi[k];
+    }
+    const uint32_t nx = (uint32_t)ext[0], ny = (uint32_t)ext[1];
+    S *lat = a.dst;
+    uint32_t n = 0, lk = SOLID;
+    if (valid) {
+        n = ((uint32_t)p[2] * ny + (uint32_t)p[1]) * nx + (uint32_t)p[0];
+        lk = a.links[n];
+    }
+    const bool fluid = lk != SOLID;
+    const bool inner = p[0] > lo[0] && p[0] < hi[0] && p[1] > lo[1] && p[1] < hi[1] && p[2] > lo[2] && p[2] < hi[2];
+    const int nt[3] = {(int)gridDim.x, (int)gridDim.y, (int)gridDim.z};
+    const int64_t t = ((int64_t)b[2] * nt[1] + b[1]) * nt[0] + b[0];
+    C g[Q];
+    if (fluid && inner) {
+        pull3<S, L, OFF32>(a, (uint32_t)p[0], (uint32_t)p[1], (uint32_t)p[2], n, lk, g);
+    } else if (fluid) {
+        // Per axis: does a pull with c = +1 (-1) leave the tile (the node is on
+        // the tile's low (high) face)? Where the tile spans the whole axis, such
+        // a pull wraps around the box inside the tile (periodic) or bounces.
+        bool lof[3], hif[3];
+        int wrap_lo[3], wrap_hi[3];   // node-index correction of an in-tile wrap
+        int tprev[3], tnext[3], lprev[3];
+        const int stride[3] = {1, (int)nx, (int)(nx * ny)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lof[k] = p[k] == lo[k];
+            hif[k] = p[k] == hi[k];
+            wrap_lo[k] = p[k] == 0 ? ext[k] * stride[k] : 0;
+            wrap_hi[k] = p[k] == ext[k] - 1 ? -ext[k] * stride[k] : 0;
+            tprev[k] = b[k] == 0 ? nt[k] - 1 : b[k] - 1;
+            tnext[k] = b[k] == nt[k] - 1 ? 0 : b[k] + 1;
+            lprev[k] = min(tdim[k], ext[k] - tprev[k] * tdim[k]) - 1;
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (i == REST) {
+                g[i] = Codec<S>::dec(lat[addr<L>(a.N, n, i)]);
+                continue;
+            }
+            if ((lk >> bit(i)) & 1u) {
+                g[i] = Codec<S>::dec(lat[addr<L>(a.N, n, opp(i))]);
+                continue;
+            }
+            const int c[3] = {cx(i), cy(i), cz(i)};
+            bool out = false;   // the source lies in another tile
+            int shift = 0;      // node-index shift of the source (in-tile, wraps included)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (c[k] == 0) continue;
+                const bool cross = c[k] > 0 ? lof[k] : hif[k];
+                shift += -c[k] * stride[k];
+                if (cross) {
+                    if (nt[k] == 1) shift += c[k] > 0 ? wrap_lo[k] : wrap_hi[k];
+                    else out = true;
+                }
+            }
+            if (!out) {
+                g[i] = Codec<S>::dec(lat[addr<L>(a.N, (uint32_t)((int64_t)n + shift), i)]);
+            } else {
+                // the value left the source tile through its face of the first
+                // axis along which the tiles differ
+                int bs[3], ls[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const bool cr = c[k] != 0 && (c[k] > 0 ? lof[k] : hif[k]) && nt[k] > 1;
+                    if (!cr) {
+                        bs[k] = b[k];
+                        int sk = p[k] - c[k];
+                        sk = sk < 0 ? sk + ext[k] : (sk >= ext[k] ? sk - ext[k] : sk);
+                        ls[k] = sk - lo[k];
+                    } else {
+                        bs[k] = c[k] > 0 ? tprev[k] : tnext[k];
+                        ls[k] = c[k] > 0 ? lprev[k] : 0;
+                    }
+                }
+                const int ax = bs[0] != b[0] ? 0 : (bs[1] != b[1] ? 1 : 2);
+                const int64_t ts = ((int64_t)bs[2] * nt[1] + bs[1]) * nt[0] + bs[0];
+                const int64_t slot = ts * T.per_tile() + T.face_off(ax, c[ax]) +
+                                     (int64_t)face_rank(i, ax) * T.nodes(ax) + T.pos(ax, ls[0], ls[1], ls[2]);
+                g[i] = Codec<S>::dec(hr[slot]);
+            }
+        }
+    }
+    __syncthreads();
+    if (!fluid) return;
+    C drho, ux, uy, uz;
+    collide3(a.k, g, drho, ux, uy, uz);
+    if (!isfinite(drho)) atomicOr(a.err, 1u);
+    if (a.mom) {
+        a.mom[n] = A::add(C(1), drho);
+        a.mom[a.N + n] = ux;
+        a.mom[2 * (size_t)a.N + n] = uy;
+        a.mom[3 * (size_t)a.N + n] = uz;
+    }
+    const bool sr = Codec<S>::narrow && a.sr;
+    uint32_t nk = 0;
+    if (sr) nk = node_key(step_key(a.seed, (uint32_t)(*a.tctr + a.toff)), n);
+    S e[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        e[i] = Codec<S>::enc(g[i], sr, sr ? pop_rand(nk, i) : 0u);
+        lat[addr<L>(a.N, n, i)] = e[i];
+    }
+    if (!inner) publish3(hw, T, t, p, lo, hi, l[0], l[1], l[2], e);
+}
+
+// Fill a buffer-grid parity from the stored state (after init or a write).
+template <class S, int L>
+__global__ void k3_publish(const Step3<S> a, S *hw) {
+    const Tile3 T{a.tx, a.ty, a.tz};
+    const int ext[3] = {a.g.nx, a.g.ny, a.g.nz};
+    const int b[3] = {(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z};
+    const int tdim[3] = {a.tx, a.ty, a.tz};
+    const int l[3] = {(int)threadIdx.x, (int)threadIdx.y, (int)threadIdx.z};
+    int lo[3], hi[3], p[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = b[k] * tdim[k];
+        hi[k] = min(lo[k] + tdim[k], ext[k]) - 1;
+        p[k] = lo[k] + l[k];
+        if (p[k] > hi[k]) return;
+    }
+    const uint32_t n = (((uint32_t)p[2] * (uint32_t)ext[1]) + (uint32_t)p[1]) * (uint32_t)ext[0] + (uint32_t)p[0];
+    if (a.links[n] == SOLID) return;
+    const int64_t ntx = (ext[0] + a.tx - 1) / a.tx, nty = (ext[1] + a.ty - 1) / a.ty;
+    const int64_t t = ((int64_t)b[2] * nty + b[1]) * ntx + b[0];
+    S e[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) e[i] = a.dst[addr<L>(a.N, n, i)];
+    publish3(hw, T, t, p, lo, hi, l[0], l[1], l[2], e);
+}
+
 template <class S, int L>
 __global__ void k3_init(const Step3<S> a, const double *rho, const double *ux, const double *uy,
                         const double *uz, uint32_t n0, uint32_t count) {
@@ -486,7 +695,9 @@ struct Plan3 {
     int tx = 0, ty = 1, tz = 1, ntx = 0, nty = 0, ntz = 0;
     size_t elem = 0, comp = 0;
     size_t pop[2] = {0, 0}, links = 0, mom = 0, mom_bytes = 0, partials = 0, misc = 0, total = 0;
-    int one = 0;   // one lattice (AA pattern)
+    int one = 0;   // one lattice (AA pattern, NPOL)
+    size_t halo = 0;          // NPOL buffer grid (two parities)
+    int64_t halo_parity = 0;  // elements per parity
 };
 
 size_t elem_of(int storage) { return storage == LBM_F64 ? 8 : storage == LBM_F32 ? 4 : 2; }
@@ -507,13 +718,13 @@ lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
         if (bc[a] != LBM_BC_PERIODIC && bc[a] != LBM_BC_WALL)
             return lbm_fail(LBM_EINVAL, "D3Q19 faces are PERIODIC or WALL");
     if (p->layout < 0 || p->layout > 2) return lbm_fail(LBM_EINVAL, "bad layout");
-    if (p->algo != LBM_LPTL && p->algo != LBM_NPTL && p->algo != LBM_AA)
-        return lbm_fail(LBM_EUNSUPPORTED, "D3Q19: LPTL, NPTL or AA");
+    if (p->algo != LBM_LPTL && p->algo != LBM_NPTL && p->algo != LBM_AA && p->algo != LBM_NPOL)
+        return lbm_fail(LBM_EUNSUPPORTED, "D3Q19: LPTL, NPTL, NPOL or AA");
     if (p->storage < 0 || p->storage > 3) return lbm_fail(LBM_EINVAL, "bad storage");
     if (p->rounding < 0 || p->rounding > 1) return lbm_fail(LBM_EINVAL, "bad rounding");
     *pl = Plan3();
     pl->N = (int64_t)N;
-    if (p->algo == LBM_NPTL || p->algo == LBM_AA) {
+    if (p->algo == LBM_NPTL || p->algo == LBM_AA || p->algo == LBM_NPOL) {
         int tx = p->tile_x, ty = p->tile_y, tz = p->tile_z;
         if (tx == 0 && ty == 0 && tz == 0) { tx = 128; ty = 1; tz = 1; }
         if (tx < 1 || ty < 1 || tz < 1 || tz > 64 || (int64_t)tx * ty * tz > 512)
@@ -529,10 +740,14 @@ lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off = (off + b + 255) / 256 * 256; return o; };
     pl->pop[0] = take(19 * (size_t)N * pl->elem);
-    pl->one = p->algo == LBM_AA ? 1 : 0;
-    if (pl->one && (!offsets_fit(p, (int64_t)N) || (p->flags & LBM_FLAG_WIDE_OFFSETS)))
+    pl->one = (p->algo == LBM_AA || p->algo == LBM_NPOL) ? 1 : 0;
+    if (p->algo == LBM_AA && (!offsets_fit(p, (int64_t)N) || (p->flags & LBM_FLAG_WIDE_OFFSETS)))
         return lbm_fail(LBM_EUNSUPPORTED, "D3Q19 AA needs 32-bit offset tables (19 N well below 2^31)");
     pl->pop[1] = pl->one ? pl->pop[0] : take(19 * (size_t)N * pl->elem);
+    if (p->algo == LBM_NPOL) {
+        pl->halo_parity = (int64_t)pl->ntx * pl->nty * pl->ntz * Tile3{pl->tx, pl->ty, pl->tz}.per_tile();
+        pl->halo = take(2 * (size_t)pl->halo_parity * pl->elem);
+    }
     pl->links = take(4 * (size_t)N);
     pl->mom_bytes = std::max(4 * (size_t)N * pl->comp, 4 * sizeof(double) * (size_t)std::min<uint64_t>(N, 1 << 16));
     pl->mom = take(pl->mom_bytes);
@@ -671,11 +886,44 @@ static void launch_aa(const lbm3_lattice *L, const Step3<S> &a, cudaStream_t st)
     else k3_aa<S, COLLISION, PHASE><<<g, b, 0, st>>>(a);
 }
 
-// src: the update's parity (two lattices: the source lattice; AA: the phase).
+template <class S>
+static S *halo_parity(const lbm3_lattice *L, int parity) {
+    return (S *)(L->ws + L->pl.halo) + (int64_t)parity * L->pl.halo_parity;
+}
+
+template <class S, bool OFF32>
+static void launch_npol(const lbm3_lattice *L, const Step3<S> &a, int parity, cudaStream_t st) {
+    const dim3 g(L->pl.ntx, L->pl.nty, L->pl.ntz), b(L->pl.tx, L->pl.ty, L->pl.tz);
+    const S *hr = halo_parity<S>(L, parity);
+    S *hw = halo_parity<S>(L, parity ^ 1);
+    const int lay = L->p.layout;
+    if (lay == LBM_LAYOUT_STREAM) k3_npol<S, STREAM, OFF32><<<g, b, 0, st>>>(a, hr, hw);
+    else if (lay == LBM_LAYOUT_BUNDLE) k3_npol<S, BUNDLE, OFF32><<<g, b, 0, st>>>(a, hr, hw);
+    else k3_npol<S, COLLISION, OFF32><<<g, b, 0, st>>>(a, hr, hw);
+}
+
+// NPOL: fill buffer-grid parity `parity` from the stored state.
+template <class S>
+static cudaError_t publish_state(const lbm3_lattice *L, int parity, cudaStream_t st) {
+    const Step3<S> a = make3<S>(L, 0, 0, 0);
+    const dim3 g(L->pl.ntx, L->pl.nty, L->pl.ntz), b(L->pl.tx, L->pl.ty, L->pl.tz);
+    S *hw = halo_parity<S>(L, parity);
+    const int lay = L->p.layout;
+    if (lay == LBM_LAYOUT_STREAM) k3_publish<S, STREAM><<<g, b, 0, st>>>(a, hw);
+    else if (lay == LBM_LAYOUT_BUNDLE) k3_publish<S, BUNDLE><<<g, b, 0, st>>>(a, hw);
+    else k3_publish<S, COLLISION><<<g, b, 0, st>>>(a, hw);
+    return cudaGetLastError();
+}
+
+// src: the update's parity (two lattices: the source lattice; AA: the phase;
+// NPOL: the buffer-grid parity read).
 template <class S>
 static cudaError_t step3(const lbm3_lattice *L, cudaStream_t st, int src, int toff, int mom) {
     const Step3<S> a = make3<S>(L, src, toff, mom);
-    if (L->p.algo == LBM_AA) {
+    if (L->p.algo == LBM_NPOL) {
+        if (L->off32) launch_npol<S, true>(L, a, src, st);
+        else launch_npol<S, false>(L, a, src, st);
+    } else if (L->p.algo == LBM_AA) {
         if (src == 0) launch_aa<S, 0>(L, a, st);
         else launch_aa<S, 1>(L, a, st);
     } else if (L->p.algo == LBM_LPTL) {
@@ -747,6 +995,7 @@ extern "C" lbm_status lbm3_init(lbm3_lattice *L, const double *rho, const double
     CK3(cudaMemsetAsync(L->ws + pl.pop[0], 0, 19 * (size_t)pl.N * pl.elem, st));
     if (!pl.one) CK3(cudaMemsetAsync(L->ws + pl.pop[1], 0, 19 * (size_t)pl.N * pl.elem, st));
     CK3(cudaMemsetAsync(L->ws + pl.misc, 0, 256, st));
+    if (pl.halo_parity) CK3(cudaMemsetAsync(L->ws + pl.halo, 0, 2 * (size_t)pl.halo_parity * pl.elem, st));
     L->cur = 0;
     L->steps = 0;
     if (rho || ux || uy || uz) {
@@ -782,6 +1031,7 @@ extern "C" lbm_status lbm3_init(lbm3_lattice *L, const double *rho, const double
         else k3_state_moments<S, COLLISION><<<g, 256, 0, st>>>(a);
     });
     CK3(cudaGetLastError());
+    if (pl.halo_parity) LBM3_DISPATCH(L, CK3(publish_state<S>(L, 0, st)));
     CK3(cudaStreamSynchronize(st));
     return LBM_OK;
 }
@@ -940,7 +1190,7 @@ static void set_raw(unsigned char *raw, int storage, int64_t k, double v) {
 // AA pattern: the array holds the canonical state only after an even number
 // of updates.
 static lbm_status state_readable(const lbm3_lattice *L) {
-    if (L->pl.one && (L->steps & 1))
+    if (L->p.algo == LBM_AA && (L->steps & 1))
         return lbm_fail(LBM_EINVAL, "AA pattern: the state is accessible after an even number of updates only");
     return LBM_OK;
 }
@@ -976,6 +1226,10 @@ extern "C" lbm_status lbm3_write_populations(lbm3_lattice *L, const void *host, 
         }
     CK3(cudaStreamSynchronize(L->stream));
     CK3(cudaMemcpy(L->ws + L->pl.pop[L->cur], raw.data(), raw.size(), cudaMemcpyHostToDevice));
+    if (L->pl.halo_parity) {   // NPOL: the next update reads parity cur of the buffer grid
+        LBM3_DISPATCH(L, CK3(publish_state<S>(L, L->cur, L->stream)));
+        CK3(cudaStreamSynchronize(L->stream));
+    }
     return LBM_OK;
 }
 
@@ -1024,6 +1278,8 @@ extern "C" lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out) {
     out->tile_x = L->p.algo == LBM_LPTL ? L->block_1d : L->pl.tx;
     out->tile_y = L->p.algo == LBM_LPTL ? 1 : L->pl.ty * L->pl.tz;
     out->bytes_per_update = (double)L->fluid * 38.0 * (double)L->pl.elem + 4.0 * (double)L->pl.N;
+    if (L->pl.halo_parity)   // NPOL buffer grid: one parity read, the other written
+        out->bytes_per_update += 2.0 * (double)L->pl.halo_parity * (double)L->pl.elem;
     out->workspace_bytes = L->pl.total;
     out->reserved = L->off32 ? 0 : 1;   // 1: the 64-bit addressing path
     return LBM_OK;

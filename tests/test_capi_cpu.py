@@ -164,7 +164,7 @@ def test_d3q19_params_checked_without_gpu(lib):
     ok = lbm.lbm3_workspace_bytes(lbm.make_params3(16, 8, 4, 0.8, storage="f32"))
     assert ok >= 2 * 19 * 16 * 8 * 4 * 4
     for bad in (dict(tau=0.5), dict(bc=(lbm.FREESLIP, lbm.PERIODIC, lbm.PERIODIC)),
-                dict(algo="npol"), dict(tile=(32, 8, 4))):
+                dict(algo="nsol"), dict(tile=(32, 8, 4))):
         kw = dict(tau=0.8)
         kw.update(bad)
         tau = kw.pop("tau")
@@ -214,3 +214,14 @@ def test_d3q19_aa_is_one_lattice_and_needs_offset_tables(lib):
         lbm.lbm3_workspace_bytes(lbm.make_params3(32, 16, 8, 0.8, algo="aa",
                                                   flags=lbm.LBM_FLAG_WIDE_OFFSETS))
     assert e.value.status == lbm.LBM_EUNSUPPORTED
+
+
+def test_d3q19_npol_is_one_lattice_plus_buffer_grid(lib):
+    nx, ny, nz = 64, 32, 16
+    two = lbm.lbm3_workspace_bytes(lbm.make_params3(nx, ny, nz, 0.8, algo="nptl", storage="f32"))
+    one = lbm.lbm3_workspace_bytes(lbm.make_params3(nx, ny, nz, 0.8, algo="npol", storage="f32",
+                                                    tile=(16, 4, 4)))
+    # tiles 16x4x4: faces 16 + 64 + 64 nodes, 10 values per face node per parity
+    tiles = (nx // 16) * (ny // 4) * (nz // 4)
+    grid = 2 * tiles * 10 * (4 * 4 + 16 * 4 + 16 * 4) * 4
+    assert two - 19 * nx * ny * nz * 4 + grid - 1024 <= one <= two - 19 * nx * ny * nz * 4 + grid + 1024

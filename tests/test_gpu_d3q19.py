@@ -82,13 +82,14 @@ SPECS = specs()
 
 @pytest.mark.parametrize("case", list(SPECS))
 @pytest.mark.parametrize("layout", LAYOUTS)
-@pytest.mark.parametrize("algo", ALGOS + ("nptl_wide",))
+@pytest.mark.parametrize("algo", ALGOS + ("nptl_wide", "npol", "npol_wide"))
 def test_fp64_matches_oracle3(case, layout, algo):
     spec = SPECS[case]
     T = 40
     ref = spec.oracle().run(T)
-    flags = lbm.LBM_FLAG_WIDE_OFFSETS if algo == "nptl_wide" else 0
-    lat = spec.gpu(layout=layout, algo=algo.split("_")[0], storage="f64", flags=flags)
+    flags = lbm.LBM_FLAG_WIDE_OFFSETS if algo.endswith("_wide") else 0
+    tile = (8, 4, 3) if algo.startswith("npol") else (0, 0, 0)
+    lat = spec.gpu(layout=layout, algo=algo.split("_")[0], storage="f64", flags=flags, tile=tile)
     lat.step(T, moments=True).sync()
     h = lat.populations("f64")
     rho, ux, uy, uz = lat.moments()
@@ -113,7 +114,8 @@ def test_all_layouts_algorithms_and_tiles_bit_identical(storage, rounding):
     for layout in LAYOUTS:
         for algo, tile, flags in (("lptl", (0, 0, 0), 0), ("nptl", (32, 4, 2), 0), ("nptl", (8, 8, 8), 0),
                                   ("nptl", (16, 2, 1), 0), ("lptl", (0, 0, 0), lbm.LBM_FLAG_WIDE_OFFSETS),
-                                  ("nptl", (128, 1, 1), lbm.LBM_FLAG_WIDE_OFFSETS)):
+                                  ("nptl", (128, 1, 1), lbm.LBM_FLAG_WIDE_OFFSETS),
+                                  ("npol", (8, 4, 2), 0), ("npol", (16, 2, 3), 0), ("npol", (64, 1, 1), 0)):
             lat = spec.gpu(layout=layout, algo=algo, tile=tile, storage=storage, rounding=rounding,
                            seed=99, flags=flags)
             lat.step(T, moments=True).sync()
@@ -127,7 +129,7 @@ def test_all_layouts_algorithms_and_tiles_bit_identical(storage, rounding):
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
-@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("algo", ALGOS + ("npol",))
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_pure_streaming_is_bit_exact_shift3(layout, algo, storage):
     nx, ny, nz, T = 23, 9, 7, 5
@@ -398,7 +400,7 @@ def test_aa_pure_streaming_is_bit_exact_shift3(layout):
 
 @pytest.mark.parametrize("case", ["porous", "duct"])
 @pytest.mark.parametrize("layout,algo", [("stream", "nptl"), ("bundle", "lptl"), ("collision", "nptl"),
-                                         ("bundle", "aa")])
+                                         ("bundle", "aa"), ("stream", "npol")])
 def test_force_matches_oracle3(case, layout, algo):
     """FP64 momentum-exchange force on the solid mask (and on a body given as
     a device mask) against the D3Q19 oracle after 40 updates. The force is a
@@ -512,7 +514,7 @@ def test_wide_addressing_path_at_136m_nodes():
 # ---------------------------------------------------------------- degenerate inputs
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 7), (5, 1, 1), (2, 3, 2), (1, 4, 3)])
-@pytest.mark.parametrize("algo", ["lptl", "nptl", "aa"])
+@pytest.mark.parametrize("algo", ["lptl", "nptl", "aa", "npol"])
 def test_tiny_periodic_boxes_match_oracle3(shape, algo):
     """Boxes where a node is its own neighbour (extent 1) or its neighbour on
     both sides (extent 2), fully periodic, with a force and random velocities."""
@@ -530,7 +532,7 @@ def test_tiny_periodic_boxes_match_oracle3(shape, algo):
     lat.close()
 
 
-@pytest.mark.parametrize("algo", ["lptl", "nptl", "aa"])
+@pytest.mark.parametrize("algo", ["lptl", "nptl", "aa", "npol"])
 def test_all_solid_and_walled_strip3(algo):
     """An all-solid box stays zero with no fluid nodes; a one-node-wide strip
     between walls on two axes (every transverse pull bounces) matches the
@@ -558,7 +560,7 @@ def test_largest_and_odd_tiles3(tile):
     base.step(20, moments=True).sync()
     ref = base.populations("f32")
     base.close()
-    for algo in ("nptl", "aa"):
+    for algo in ("nptl", "aa", "npol"):
         lat = spec.gpu(layout="bundle", algo=algo, storage="f32", tile=tile)
         lat.step(20, moments=True).sync()
         assert np.array_equal(lat.populations("f32"), ref), (algo, tile)
