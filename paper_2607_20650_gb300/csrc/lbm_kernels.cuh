@@ -398,7 +398,7 @@ struct AosSpan {
 };
 
 template <class S>
-__global__ void __launch_bounds__(kMaxTileThreads) k_two_lattice_aos(const Step<S> a) {
+__global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : 4) k_two_lattice_aos(const Step<S> a) {
     using C = typename Codec<S>::C;
     using SP = AosSpan<S>;
     extern __shared__ __align__(16) unsigned char smem_aos[];
