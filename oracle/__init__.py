@@ -48,6 +48,8 @@ class _Params3(ctypes.Structure):
         ("tau", ctypes.c_double), ("fx", ctypes.c_double), ("fy", ctypes.c_double),
         ("fz", ctypes.c_double),
         ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32), ("bc_z", ctypes.c_int32),
+        ("bc_xe", ctypes.c_int32),
+        ("ux_in", ctypes.c_double), ("uy_in", ctypes.c_double), ("uz_in", ctypes.c_double),
     ]
 
 
@@ -210,7 +212,9 @@ class Lattice:
 
 @dataclass
 class Case3:
-    """A D3Q19 lattice: size, tau, force, per-axis faces (PERIODIC or WALL)."""
+    """A D3Q19 lattice: size, tau, force, per-axis faces (PERIODIC or WALL);
+    on x the west face may be INLET_EQ (velocity u_in) and the east face
+    (bc_xe, default: as bc_x) OUTFLOW_ZG."""
     nx: int
     ny: int
     nz: int
@@ -221,10 +225,13 @@ class Case3:
     bc_x: int = PERIODIC
     bc_y: int = PERIODIC
     bc_z: int = PERIODIC
+    bc_xe: int = -1
+    u_in: tuple = (0.0, 0.0, 0.0)
 
     def _c(self):
+        east = self.bc_x if self.bc_xe < 0 else self.bc_xe
         return _Params3(self.nx, self.ny, self.nz, self.tau, self.fx, self.fy, self.fz,
-                        self.bc_x, self.bc_y, self.bc_z)
+                        self.bc_x, self.bc_y, self.bc_z, east, *[float(u) for u in self.u_in])
 
 
 def directions3():

@@ -13,23 +13,31 @@
  *   (faces), 1/36 (edges).
  *
  * Two-lattice pull on the canonical layout h[i*N + n], n = (z*ny + y)*nx + x,
- * h = f - w. Faces: periodic or half-way wall per axis; solid nodes bounce
- * back; Guo body force as in the 2-D oracle. A fluid node all of whose 18
- * pulls bounce is treated as solid.
+ * h = f - w. Faces: periodic or half-way wall per axis; on the x axis the
+ * west face may instead be an equilibrium inlet (the x = 0 plane set to
+ * f^eq(rho = 1, u_in) before the collision, the 3-D form of the 2-D
+ * oracle's Dirichlet equilibrium inlet) and the east face a zero-gradient
+ * outflow (the pulled source plane x = nx clamped to nx - 1). Pulls are
+ * mapped in z, then y, then x, as the 2-D oracle maps y before x. Solid
+ * nodes bounce back; Guo body force as in the 2-D oracle. A fluid node all
+ * of whose 18 pulls bounce (or come from outside the inlet face) is treated
+ * as solid.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
-enum { F3_PERIODIC = 0, F3_WALL = 1 };
+enum { F3_PERIODIC = 0, F3_WALL = 1, F3_INLET_EQ = 4, F3_OUTFLOW_ZG = 5 };
 enum { P3_NODE = 0, P3_BOUNCE = 1 };
 
 typedef struct {
     int32_t nx, ny, nz;
     double tau;
     double fx, fy, fz;
-    int32_t bc_x, bc_y, bc_z;   /* per axis: both faces periodic or both walls */
+    int32_t bc_x, bc_y, bc_z;   /* per axis: both faces periodic or both walls; bc_x: the west face */
+    int32_t bc_xe;              /* east face: periodic (with bc_x), wall or zero-gradient outflow */
+    double ux_in, uy_in, uz_in; /* inlet velocity (bc_x = F3_INLET_EQ) */
 } oracle3_params;
 
 static int C3[19][3];
@@ -70,16 +78,24 @@ void oracle3_equilibrium(double drho, double ux, double uy, double uz, double *h
     }
 }
 
-/* Source of the value pulled by (x, y, z) in direction i. */
+/* Source of the value pulled by (x, y, z) in direction i: z and y wrap or
+ * bounce; x wraps, bounces, is clamped (outflow) or unknown (inlet, marked
+ * as a bounce: the inlet plane is overwritten before the collision). */
 static int pull3(const oracle3_params *p, int x, int y, int z, int i, int64_t *src) {
     int s[3] = {x - C3[i][0], y - C3[i][1], z - C3[i][2]};
     const int ext[3] = {p->nx, p->ny, p->nz};
     const int bc[3] = {p->bc_x, p->bc_y, p->bc_z};
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 2; a >= 1; --a) {
         if (s[a] < 0 || s[a] >= ext[a]) {
             if (bc[a] != F3_PERIODIC) return P3_BOUNCE;
             s[a] = (s[a] + ext[a]) % ext[a];
         }
+    }
+    if (s[0] < 0 || s[0] >= p->nx) {
+        const int kind = s[0] < 0 ? p->bc_x : p->bc_xe;
+        if (kind == F3_PERIODIC) s[0] = (s[0] + p->nx) % p->nx;
+        else if (kind == F3_OUTFLOW_ZG) s[0] = s[0] < 0 ? 0 : p->nx - 1;
+        else return P3_BOUNCE;   /* wall, or inlet (unknown) */
     }
     *src = ((int64_t)s[2] * p->ny + s[1]) * p->nx + s[0];
     return P3_NODE;
@@ -137,6 +153,8 @@ void oracle3_step(const oracle3_params *p, const uint8_t *solid, const double *h
                     if (k == P3_NODE && solid[s]) k = P3_BOUNCE;
                     g[i] = k == P3_NODE ? h_in[(int64_t)i * N + s] : h_in[(int64_t)(18 - i) * N + n];
                 }
+                if (x == 0 && p->bc_x == F3_INLET_EQ)   /* Dirichlet equilibrium inlet */
+                    oracle3_equilibrium(0.0, p->ux_in, p->uy_in, p->uz_in, g);
                 double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
                 for (int i = 0; i < 19; ++i) {
                     drho += g[i];
@@ -210,7 +228,8 @@ void oracle3_force(const oracle3_params *p, const uint8_t *solid, const uint8_t 
                     int inside = 1;
                     for (int a = 0; a < 3; ++a) {
                         if (b[a] < 0 || b[a] >= ext[a]) {
-                            if (bc[a] != F3_PERIODIC) inside = 0;
+                            const int kind = a == 0 ? (b[0] < 0 ? p->bc_x : p->bc_xe) : bc[a];
+                            if (kind != F3_PERIODIC) inside = 0;
                             b[a] = (b[a] + ext[a]) % ext[a];
                         }
                     }

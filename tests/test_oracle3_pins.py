@@ -137,3 +137,38 @@ def test_force_balance_steady_duct_3d():
     Fb = lat.force(bottom)
     assert abs(Fb[0] - total / 2) / total < 1e-9
     assert np.all(lat.force(np.zeros_like(mask)) == 0.0)
+
+
+# ---------------------------------------------------------------- inlet / outflow
+
+def test_uniform_inflow_outflow_is_a_fixed_point_3d():
+    """Equilibrium inlet (west) at U and zero-gradient outflow (east) with
+    periodic y and z: the uniform state f^eq(1, U) is stationary."""
+    U = (0.04, 0.01, -0.005)
+    nx, ny, nz = 7, 4, 3
+    N = nx * ny * nz
+    case = O.Case3(nx, ny, nz, 0.8, bc_x=O.INLET_EQ, bc_xe=O.OUTFLOW_ZG, u_in=U)
+    lat = O.Lattice3(case, None, ux=np.full(N, U[0]), uy=np.full(N, U[1]), uz=np.full(N, U[2]))
+    h0 = lat.h.copy()
+    lat.run(50)
+    assert np.max(np.abs(lat.h - h0)) < 1e-16
+    assert np.max(np.abs(lat.ux - U[0])) < 1e-16 and np.max(np.abs(lat.uz - U[2])) < 1e-16
+
+
+def test_inlet_outflow_channel_reduces_to_d2q9():
+    """A z-invariant channel with an obstacle, equilibrium inlet, zero-gradient
+    outflow and walls on y, summed over c_z, is the 2-D oracle's channel with
+    the same edges (the 2-D oracle is pinned by exact-rational brute force)."""
+    nx, ny, nz = 16, 9, 3
+    rng = np.random.default_rng(5)
+    mask2 = np.zeros((ny, nx), np.uint8)
+    mask2[3:6, 5:7] = 1
+    u2 = np.where(mask2 > 0, 0.0, 0.03 + 5e-3 * rng.random((ny, nx)))
+    v2 = np.where(mask2 > 0, 0.0, 5e-3 * rng.random((ny, nx)))
+    tile = lambda a: np.broadcast_to(a, (nz, ny, nx))
+    case3 = O.Case3(nx, ny, nz, 0.7, bc_x=O.INLET_EQ, bc_xe=O.OUTFLOW_ZG, bc_y=O.WALL, u_in=(0.03, 0.0, 0.0))
+    lat3 = O.Lattice3(case3, tile(mask2).ravel(), ux=tile(u2).ravel(), uy=tile(v2).ravel()).run(30)
+    case2 = O.Case(nx, ny, 0.7, ux_in=0.03, bc_w=O.INLET_EQ, bc_e=O.OUTFLOW_ZG, bc_s=O.WALL, bc_n=O.WALL)
+    lat2 = O.Lattice(case2, mask2, ux=u2, uy=v2).run(30)
+    proj = _project(lat3.h, nx, ny, nz, 2).reshape(9, -1)
+    np.testing.assert_allclose(proj, lat2.h, rtol=0, atol=5e-16)
