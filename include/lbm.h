@@ -295,19 +295,29 @@ void lbm_batch_destroy(lbm_batch *B);
  * accessible after an even number of updates only, LBM_EINVAL otherwise;
  * needs 32-bit offset tables, i.e. roughly 19 N < 2^31, LBM_EUNSUPPORTED
  * otherwise). All produce the same bits at equal storage. Faces per axis: PERIODIC or WALL
- * (half-way bounce-back); solid mask nodes bounce back; a fluid node whose
- * 18 pulls all bounce is treated as solid. Storage, rounding, Guo force,
- * graphs and errors as in 2-D. Workspace: 2 x 19 N elements, 4 N bytes of
- * links, 4 N compute-type moments, small scratch.                         */
+ * (half-way bounce-back); on x the west face may instead be an equilibrium
+ * inlet (LBM_BC_INLET_EQ: the x = 0 plane set to f^eq(rho = 1, u_in) before
+ * the collision, Sec. 3.1's Dirichlet equilibrium inlet) with the east face
+ * bc_x_east a wall or a zero-gradient outflow (LBM_BC_OUTFLOW_ZG, the pulled
+ * source plane clamped), or both x faces may be outflows; pulls are mapped
+ * in z, then y, then x; inlet and outflow faces with LPTL and NPTL only
+ * (LBM_EUNSUPPORTED otherwise). Solid mask nodes bounce back; a fluid node
+ * whose 18 pulls all bounce is treated as solid. Storage, rounding, Guo
+ * force, graphs and errors as in 2-D. Workspace: 2 x 19 N elements, 4 N
+ * bytes of links, 4 N compute-type moments, small scratch.               */
 typedef struct lbm3_params {
     int32_t nx, ny, nz;      /* lattice size; nx*ny*nz < 2^32 */
     double tau;              /* relaxation time, > 1/2 */
     double force[3];         /* Guo body force */
-    int32_t bc_x, bc_y, bc_z;   /* LBM_BC_PERIODIC or LBM_BC_WALL, both faces of the axis */
+    int32_t bc_x, bc_y, bc_z;   /* LBM_BC_PERIODIC or LBM_BC_WALL, both faces of the axis;
+                                   bc_x also LBM_BC_INLET_EQ (west) or LBM_BC_OUTFLOW_ZG */
     int32_t layout, algo, storage, rounding;   /* algo: LBM_LPTL, LBM_NPTL, LBM_NPOL or LBM_AA */
     uint64_t seed;
     int32_t tile_x, tile_y, tile_z;
     uint32_t flags;          /* LBM_FLAG_NO_GRAPH, LBM_FLAG_WIDE_OFFSETS */
+    int32_t bc_x_east;       /* east x face when bc_x = LBM_BC_INLET_EQ: LBM_BC_OUTFLOW_ZG or
+                                LBM_BC_WALL (ignored otherwise: both x faces are bc_x) */
+    double u_in[3];          /* inlet velocity for bc_x = LBM_BC_INLET_EQ */
 } lbm3_params;
 
 typedef struct lbm3_lattice lbm3_lattice;

@@ -26,20 +26,29 @@ namespace d3 {
 
 struct Geo3 {
     int nx, ny, nz;
-    int bx, by, bz;   // per axis: PERIODIC or WALL
+    int bx, by, bz;   // y, z: PERIODIC or WALL; x: the west face (also INLET_EQ, OUTFLOW_ZG)
+    int bxe;          // the east face (PERIODIC with bx, WALL or OUTFLOW_ZG)
 };
 
-// Source node of the value pulled by (x, y, z) in direction i, or bounce.
+// Source node of the value pulled by (x, y, z) in direction i, or bounce
+// (walls; the inlet face, whose plane is overwritten before the collision).
+// Mapped in z, then y, then x; the outflow clamps the source plane.
 __host__ __device__ __forceinline__ bool map3(const Geo3 &g, int x, int y, int z, int i, uint32_t &src) {
     int s[3] = {x - cx(i), y - cy(i), z - cz(i)};
     const int ext[3] = {g.nx, g.ny, g.nz};
     const int bc[3] = {g.bx, g.by, g.bz};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 2; a >= 1; --a) {
         if (s[a] < 0 || s[a] >= ext[a]) {
             if (bc[a] != PERIODIC) return false;
             s[a] = s[a] < 0 ? s[a] + ext[a] : s[a] - ext[a];
         }
+    }
+    if (s[0] < 0 || s[0] >= g.nx) {
+        const int kind = s[0] < 0 ? g.bx : g.bxe;
+        if (kind == PERIODIC) s[0] = s[0] < 0 ? s[0] + g.nx : s[0] - g.nx;
+        else if (kind == OUTFLOW_ZG) s[0] = s[0] < 0 ? 0 : g.nx - 1;
+        else return false;
     }
     src = ((uint32_t)s[2] * (uint32_t)g.ny + (uint32_t)s[1]) * (uint32_t)g.nx + (uint32_t)s[0];
     return true;
@@ -68,6 +77,11 @@ struct Step3 {
     // any periodic correction (op), own slot opp(i) for a bounced pull (ob).
     int32_t os[Q], op[Q], ob[Q];
     int32_t oq[Q];   // AA push: slot opp(i) of node n + c_i, from the base of direction i
+    // node-index corrections of a pull across the west (x = 0) / east face:
+    // +nx / -nx periodic, +1 / -1 zero-gradient outflow (clamped source)
+    int xlo_corr, xhi_corr;
+    int inlet;       // the x = 0 plane takes heq_in (equilibrium inlet)
+    C heq_in[Q];
 };
 
 // Node stride of direction i's array in a layout: 1 (stream; one-direction
@@ -138,7 +152,7 @@ __device__ __forceinline__ void pull3(const Step3<S> &a, uint32_t x, uint32_t y,
         // c = +1 pulls from coordinate -1 at the low face, c = -1 from the
         // extent at the high face.
         const int N = (int)a.N, nxy = (int)(nx * ny);
-        const int xlo = x == 0 ? (int)nx : 0, xhi = x == nx - 1 ? -(int)nx : 0;
+        const int xlo = x == 0 ? a.xlo_corr : 0, xhi = x == nx - 1 ? a.xhi_corr : 0;
         const int ylo = y == 0 ? nxy : 0, yhi = y == ny - 1 ? -nxy : 0;
         const int zlo = z == 0 ? N : 0, zhi = z == nz - 1 ? -N : 0;
 #pragma unroll
@@ -262,6 +276,10 @@ __global__ void __launch_bounds__(512, sizeof(S) == 8 ? 2 : 3) k3_step(const Ste
     if (!f) return;
     C g[Q];
     pull3<S, L, OFF32>(a, x, y, z, n, lk, g);
+    if (a.inlet && x == 0) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = a.heq_in[i];
+    }
     finish3<S, L, OFF32>(a, n, g);
 }
 
@@ -705,6 +723,9 @@ size_t comp_of(int storage) { return storage == LBM_F64 ? 8 : 4; }
 
 bool offsets_fit(const lbm3_params *p, int64_t N);
 
+// Kind of the east x face: bc_x_east after an inlet west face, else bc_x.
+int east_kind(const lbm3_params *p) { return p->bc_x == LBM_BC_INLET_EQ ? p->bc_x_east : p->bc_x; }
+
 lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
     if (!p) return lbm_fail(LBM_EINVAL, "params is NULL");
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return lbm_fail(LBM_EINVAL, "nx, ny, nz must be >= 1");
@@ -714,9 +735,19 @@ lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(p->force[a])) return lbm_fail(LBM_EINVAL, "force must be finite");
     const int bc[3] = {p->bc_x, p->bc_y, p->bc_z};
-    for (int a = 0; a < 3; ++a)
+    for (int a = 1; a < 3; ++a)
         if (bc[a] != LBM_BC_PERIODIC && bc[a] != LBM_BC_WALL)
-            return lbm_fail(LBM_EINVAL, "D3Q19 faces are PERIODIC or WALL");
+            return lbm_fail(LBM_EINVAL, "D3Q19 y and z faces are PERIODIC or WALL");
+    if (p->bc_x != LBM_BC_PERIODIC && p->bc_x != LBM_BC_WALL && p->bc_x != LBM_BC_INLET_EQ &&
+        p->bc_x != LBM_BC_OUTFLOW_ZG)
+        return lbm_fail(LBM_EINVAL, "D3Q19 x faces: PERIODIC, WALL, INLET_EQ (west) or OUTFLOW_ZG");
+    if (p->bc_x == LBM_BC_INLET_EQ && p->bc_x_east != LBM_BC_WALL && p->bc_x_east != LBM_BC_OUTFLOW_ZG)
+        return lbm_fail(LBM_EINVAL, "D3Q19 inlet: the east face (bc_x_east) is WALL or OUTFLOW_ZG");
+    const bool open_x = p->bc_x == LBM_BC_INLET_EQ || p->bc_x == LBM_BC_OUTFLOW_ZG;
+    if (open_x && (p->algo == LBM_AA || p->algo == LBM_NPOL))
+        return lbm_fail(LBM_EUNSUPPORTED, "D3Q19 inlet/outflow faces: LPTL or NPTL only");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(p->u_in[a])) return lbm_fail(LBM_EINVAL, "u_in must be finite");
     if (p->layout < 0 || p->layout > 2) return lbm_fail(LBM_EINVAL, "bad layout");
     if (p->algo != LBM_LPTL && p->algo != LBM_NPTL && p->algo != LBM_AA && p->algo != LBM_NPOL)
         return lbm_fail(LBM_EUNSUPPORTED, "D3Q19: LPTL, NPTL, NPOL or AA");
@@ -804,7 +835,18 @@ static Step3<S> make3(const lbm3_lattice *L, int src, int toff, int mom) {
     using C = typename Codec<S>::C;
     Step3<S> a;
     const lbm3_params &p = L->p;
-    a.g = Geo3{p.nx, p.ny, p.nz, p.bc_x, p.bc_y, p.bc_z};
+    a.g = Geo3{p.nx, p.ny, p.nz, p.bc_x, p.bc_y, p.bc_z, east_kind(&p)};
+    a.xlo_corr = p.bc_x == LBM_BC_PERIODIC ? p.nx : (p.bc_x == LBM_BC_OUTFLOW_ZG ? 1 : 0);
+    a.xhi_corr = a.g.bxe == LBM_BC_PERIODIC ? -p.nx : (a.g.bxe == LBM_BC_OUTFLOW_ZG ? -1 : 0);
+    a.inlet = p.bc_x == LBM_BC_INLET_EQ ? 1 : 0;
+    {
+        const double usq = p.u_in[0] * p.u_in[0] + p.u_in[1] * p.u_in[1] + p.u_in[2] * p.u_in[2];
+        for (int i = 0; i < Q; ++i) {
+            const double w = d3::sq(i) == 0 ? 1.0 / 3.0 : (d3::sq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+            const double cu = d3::cx(i) * p.u_in[0] + d3::cy(i) * p.u_in[1] + d3::cz(i) * p.u_in[2];
+            a.heq_in[i] = (C)(w * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
+        }
+    }
     a.N = (uint32_t)L->pl.N;
     const double om = 1.0 / p.tau, kf = 1.0 - 0.5 * om;
     a.k.omega = (C)om;
@@ -1062,7 +1104,7 @@ extern "C" lbm_status lbm3_create(const lbm3_params *p, const uint8_t *mask_host
     uint8_t *dmask = (uint8_t *)(L->ws + pl.mom);   // staged in the moments region (>= N bytes)
     unsigned long long *dcount = (unsigned long long *)(L->ws + pl.partials);
     unsigned long long fluid = 0;
-    const Geo3 g{p->nx, p->ny, p->nz, p->bc_x, p->bc_y, p->bc_z};
+    const Geo3 g{p->nx, p->ny, p->nz, p->bc_x, p->bc_y, p->bc_z, east_kind(p)};
     e = cudaMemcpyAsync(dmask, mask_host, (size_t)pl.N, cudaMemcpyHostToDevice, L->stream);
     if (e == cudaSuccess) {
         k3_links<<<(unsigned)((pl.N + 255) / 256), 256, 0, L->stream>>>(g, dmask, (uint32_t *)(L->ws + pl.links));

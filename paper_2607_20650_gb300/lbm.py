@@ -78,6 +78,8 @@ class lbm3_params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
         ("flags", ctypes.c_uint32),
+        ("bc_x_east", ctypes.c_int32),
+        ("u_in", ctypes.c_double * 3),
     ]
 
 
@@ -387,8 +389,9 @@ def lbm_batch_destroy(h):
 
 def make_params3(nx, ny, nz, tau, *, force=(0.0, 0.0, 0.0), bc=(PERIODIC,) * 3, layout="stream",
                  algo="nptl", storage="f32", rounding="rne", seed=0, tile=(0, 0, 0),
-                 flags=0) -> lbm3_params:
-    """bc = (x, y, z), each PERIODIC or WALL."""
+                 flags=0, bc_x_east=OUTFLOW_ZG, u_in=(0.0, 0.0, 0.0)) -> lbm3_params:
+    """bc = (x, y, z), each PERIODIC or WALL; x may also be INLET_EQ (west;
+    the east face is then bc_x_east) or OUTFLOW_ZG (both x faces)."""
     p = lbm3_params()
     p.nx, p.ny, p.nz, p.tau = int(nx), int(ny), int(nz), float(tau)
     for a in range(3):
@@ -401,6 +404,9 @@ def make_params3(nx, ny, nz, tau, *, force=(0.0, 0.0, 0.0), bc=(PERIODIC,) * 3, 
     p.seed = int(seed)
     p.tile_x, p.tile_y, p.tile_z = tile
     p.flags = int(flags)
+    p.bc_x_east = int(bc_x_east)
+    for a in range(3):
+        p.u_in[a] = float(u_in[a])
     return p
 
 

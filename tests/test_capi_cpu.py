@@ -225,3 +225,20 @@ def test_d3q19_npol_is_one_lattice_plus_buffer_grid(lib):
     tiles = (nx // 16) * (ny // 4) * (nz // 4)
     grid = 2 * tiles * 10 * (4 * 4 + 16 * 4 + 16 * 4) * 4
     assert two - 19 * nx * ny * nz * 4 + grid - 1024 <= one <= two - 19 * nx * ny * nz * 4 + grid + 1024
+
+
+def test_d3q19_inlet_outflow_params(lib):
+    ok = lbm.make_params3(32, 8, 8, 0.8, bc=(lbm.INLET_EQ, lbm.WALL, lbm.WALL), bc_x_east=lbm.OUTFLOW_ZG,
+                          u_in=(0.05, 0.0, 0.0))
+    assert lbm.lbm3_workspace_bytes(ok) > 0
+    for bad in (dict(bc=(lbm.INLET_EQ, lbm.WALL, lbm.WALL), bc_x_east=lbm.PERIODIC),
+                dict(bc=(lbm.WALL, lbm.INLET_EQ, lbm.WALL)),
+                dict(bc=(lbm.FREESLIP, lbm.WALL, lbm.WALL))):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm3_workspace_bytes(lbm.make_params3(32, 8, 8, 0.8, **bad))
+        assert e.value.status == lbm.LBM_EINVAL
+    for algo in ("aa", "npol"):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm3_workspace_bytes(lbm.make_params3(32, 8, 8, 0.8, algo=algo,
+                                                      bc=(lbm.OUTFLOW_ZG, lbm.WALL, lbm.WALL)))
+        assert e.value.status == lbm.LBM_EUNSUPPORTED

@@ -574,3 +574,82 @@ def test_bad_shapes_rejected3():
         assert e.value.status == lbm.LBM_EINVAL
     with pytest.raises(lbm.LbmError):
         lbm.lbm3_workspace_bytes(lbm.make_params3(8, 8, 8, 0.8, tile=(8, 8, 9)))
+
+
+# ---------------------------------------------------------------- inlet / outflow
+
+def _channel3(**kw):
+    """Channel 40 x 14 x 10 with a ball: equilibrium inlet U = 0.04 (west),
+    zero-gradient outflow (east), walls on y and z, initial u = U."""
+    nx, ny, nz = 40, 14, 10
+    mask = G.ball(nx, ny, nz, 12.0, 7.0, 5.0, 3.0).ravel()
+    r = G.SplitMix64(41, 1)
+    ux = np.where(mask > 0, 0.0, 0.04)
+    uy = np.where(mask > 0, 0.0, r.uniform(nx * ny * nz, -1e-3, 1e-3))
+    case = O.Case3(nx, ny, nz, 0.7, bc_x=lbm.INLET_EQ, bc_xe=lbm.OUTFLOW_ZG, bc_y=W, bc_z=W,
+                   u_in=(0.04, 0.0, 0.0))
+    ref = O.Lattice3(case, mask, None, ux, uy, None)
+    lat = lbm.Lattice3(nx, ny, nz, 0.7, mask, bc=(lbm.INLET_EQ, W, W), bc_x_east=lbm.OUTFLOW_ZG,
+                       u_in=(0.04, 0.0, 0.0), **kw)
+    lat.init(None, ux, uy, None)
+    return ref, lat, mask
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("algo", ["lptl", "nptl", "nptl_wide"])
+def test_inlet_outflow_channel_fp64_matches_oracle3(layout, algo):
+    T = 60
+    flags = lbm.LBM_FLAG_WIDE_OFFSETS if algo.endswith("_wide") else 0
+    ref, lat, mask = _channel3(layout=layout, algo=algo.split("_")[0], storage="f64", flags=flags,
+                               tile=(16, 4, 2))
+    ref.run(T)
+    lat.step(T, moments=True).sync()
+    fl = ref.solid == 0
+    assert rel_linf(lat.populations("f64"), ref.h, fl) <= 1e-12
+    rho, ux, uy, uz = lat.moments()
+    assert rel_linf(np.stack([ux, uy, uz]), np.stack([ref.ux, ref.uy, ref.uz]), fl) <= 1e-12
+    body = torch.from_numpy(mask.astype(np.uint8)).cuda()
+    f_gpu, f_ref = lat.force(body), ref.force(mask)
+    assert np.max(np.abs(f_gpu - f_ref)) <= 1e-11 * np.max(np.abs(f_ref))
+    lat.close()
+
+
+@pytest.mark.parametrize("storage,rounding", [("f32", "rne"), ("f16s", "sr")])
+def test_inlet_outflow_channel_bit_identical(storage, rounding):
+    base = None
+    for layout in LAYOUTS:
+        for algo, tile in (("lptl", (0, 0, 0)), ("nptl", (16, 4, 2)), ("nptl", (128, 1, 1))):
+            _, lat, _ = _channel3(layout=layout, algo=algo, tile=tile, storage=storage, rounding=rounding,
+                                  seed=3)
+            lat.step(70, moments=True).sync()
+            got = (lat.populations("f64"), *lat.moments())
+            lat.close()
+            if base is None:
+                base = got
+            else:
+                assert all(np.array_equal(a, b) for a, b in zip(got, base)), (layout, algo, tile)
+
+
+def test_inlet_outflow_channel_fp32_close_to_oracle3():
+    ref, lat, _ = _channel3(layout="bundle", algo="nptl", storage="f32")
+    ref.run(200)
+    lat.step(200, moments=True).sync()
+    fl = ref.solid == 0
+    rho, ux, uy, uz = lat.moments()
+    assert rel_linf(rho, ref.rho, fl) <= 1e-5
+    assert rel_linf(np.stack([ux, uy, uz]), np.stack([ref.ux, ref.uy, ref.uz]), fl) <= 1e-5
+    lat.close()
+
+
+def test_outflow_on_both_x_faces_matches_oracle3():
+    nx, ny, nz, T = 20, 6, 5, 30
+    N = nx * ny * nz
+    r = G.SplitMix64(43, 2)
+    ux = r.uniform(N, 0.0, 0.03)
+    case = O.Case3(nx, ny, nz, 0.8, fx=1e-5, bc_x=lbm.OUTFLOW_ZG, bc_y=P, bc_z=W)
+    ref = O.Lattice3(case, None, None, ux, None, None).run(T)
+    lat = lbm.Lattice3(nx, ny, nz, 0.8, None, force=(1e-5, 0.0, 0.0), bc=(lbm.OUTFLOW_ZG, P, W),
+                       storage="f64", tile=(8, 4, 2))
+    lat.init(None, ux, None, None).step(T).sync()
+    assert rel_linf(lat.populations("f64"), ref.h) <= 1e-12
+    lat.close()
