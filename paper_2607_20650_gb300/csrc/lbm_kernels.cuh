@@ -214,25 +214,20 @@ template <int L> __device__ __forceinline__ uint32_t lay_base(uint32_t N, int i)
                        : (L == BUNDLE ? (uint32_t)(i / 3) * 3u * N + (uint32_t)(i % 3) : (uint32_t)i);
 }
 
-// Whether a solid node's record shares a 32-byte DRAM sector with a fluid
-// node's record, from the warp's fluid ballot F (lanes = consecutive nodes).
-// Stream layout: aligned groups of 32/sizeof(S) lanes; bundle / collision:
-// lanes within ceil(32 / record bytes) on either side.
+// Whether a solid node rewrites its (zero) record because it shares a
+// 32-byte DRAM sector with a fluid node's record, from the warp's fluid
+// ballot F (lanes = consecutive nodes). Only the stream layout does it
+// (aligned groups of 32/sizeof(S) lanes): measured +9 % for the stream
+// two-lattice kernels on the porous medium, but -6 % (FP32) / -10 % (FP16)
+// for the bundle layout, -27 % for the AA pattern on it and -2 % for the
+// collision layout, where the partial-sector writes cost less than the
+// extra zeros.
 template <class S, int L>
 __device__ __forceinline__ bool shares_sector(unsigned F, int lane) {
-    if (L == STREAM) {
-        constexpr int G = (int)(32 / sizeof(S)) < 32 ? (int)(32 / sizeof(S)) : 32;
-        const unsigned m = G >= 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(G - 1));
-        return (F & m) != 0u;
-    } else {
-        constexpr int b = (int)(lay_mul<L>() * sizeof(S));
-        constexpr int k = (32 + b - 1) / b;
-        const int lo = lane - k < 0 ? 0 : lane - k;
-        const int hi = lane + k > 31 ? 31 : lane + k;
-        const int w = hi - lo + 1;
-        const unsigned m = w >= 32 ? 0xffffffffu : ((1u << w) - 1u) << lo;
-        return (F & m) != 0u;
-    }
+    if (L != STREAM) return false;
+    constexpr int G = (int)(32 / sizeof(S)) < 32 ? (int)(32 / sizeof(S)) : 32;
+    const unsigned m = G >= 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(G - 1));
+    return (F & m) != 0u;
 }
 
 template <class S, int L>
@@ -557,7 +552,8 @@ __device__ __forceinline__ void npol_tile(const Step<S> &a, int bx, int by, int 
     }
     const bool fluid = lk != SOLID_LINKS;
     const unsigned F = __ballot_sync(__activemask(), fluid);
-    const bool zero_fill = valid && !fluid && shares_sector<S, L>(F, lane);
+    (void)F;
+    const bool zero_fill = false;   // measured: NPOL is 5 % faster without the sector zero fill
     const bool inner = x > x0 && x < x1 && y > y0 && y < y1;
     C g[9];
     if (fluid && inner && a.off32) {
@@ -648,7 +644,8 @@ __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int 
     }
     const bool fluid = lk != SOLID_LINKS;
     const unsigned F = __ballot_sync(__activemask(), fluid);
-    const bool zero_fill = valid && !fluid && shares_sector<S, L>(F, lane);
+    (void)F;
+    const bool zero_fill = false;   // measured: NSOL is 2 % faster without the sector zero fill
     if (member) fl[tid] = fluid ? 1 : 0;
     if (fluid) {
 #pragma unroll
