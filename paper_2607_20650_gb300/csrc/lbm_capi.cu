@@ -265,6 +265,8 @@ fail:
     return s;
 }
 
+static void stage_free(lbm_lattice *L);
+
 static void drop_graphs(lbm_lattice *L) {
     for (auto &g : L->graph)
         if (g) {
@@ -277,6 +279,7 @@ extern "C" void lbm_destroy(lbm_lattice *L) {
     if (!L) return;
     cudaStreamSynchronize(L->stream);
     drop_graphs(L);
+    stage_free(L);
     cudaStreamDestroy(L->cap);
     free(L);
 }
@@ -437,26 +440,94 @@ static void parallel_for(int64_t count, Fn fn) {
 }
 
 // ------------------------------------------------------------ read-out
+// Device address of a page-locked, mapped host buffer (cudaHostAlloc,
+// cudaHostRegister, torch pin_memory), or NULL for pageable memory.
+static void *mapped_host(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// FP32 -> FP64 widening straight into mapped host memory (over the
+// CPU-GPU link, no staging copy).
+constexpr int kWidenBlocks = 1216;  // grid-stride; 8 blocks per SM on 152 SMs
+__global__ void k_widen(const float *__restrict__ s, double *__restrict__ d, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) d[k] = (double)s[k];
+}
+
+// Page-locked staging for pageable destinations: two chunks, copied and
+// widened alternately so the copy of one overlaps the widening of the other.
+static constexpr size_t kStageBytes = (size_t)64 << 20;
+
+static lbm_status stage_alloc(lbm_lattice *L) {
+    if (L->stage) return LBM_OK;
+    CK(cudaHostAlloc(&L->stage, 2 * kStageBytes, cudaHostAllocDefault));
+    for (auto &e : L->stage_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return LBM_OK;
+}
+
+static void stage_free(lbm_lattice *L) {
+    for (auto &e : L->stage_ev)
+        if (e) cudaEventDestroy(e);
+    if (L->stage) cudaFreeHost(L->stage);
+    L->stage = nullptr;
+}
+
+static lbm_status widen_staged(lbm_lattice *L, const float *src, double *dst, int64_t n) {
+    lbm_status s = stage_alloc(L);
+    if (s != LBM_OK) return s;
+    const int64_t chunk = (int64_t)(kStageBytes / sizeof(float));
+    const int64_t nch = (n + chunk - 1) / chunk;
+    auto issue = [&](int64_t c) -> cudaError_t {
+        const int64_t b = c * chunk, m = std::min(chunk, n - b);
+        float *slot = (float *)(L->stage + (size_t)(c & 1) * kStageBytes);
+        cudaError_t e = cudaMemcpyAsync(slot, src + b, (size_t)m * sizeof(float), cudaMemcpyDeviceToHost,
+                                        L->stream);
+        return e != cudaSuccess ? e : cudaEventRecord(L->stage_ev[c & 1], L->stream);
+    };
+    for (int64_t c = 0; c < std::min<int64_t>(2, nch); ++c) CK(issue(c));
+    for (int64_t c = 0; c < nch; ++c) {
+        CK(cudaEventSynchronize(L->stage_ev[c & 1]));
+        const int64_t b = c * chunk, m = std::min(chunk, n - b);
+        const float *f = (const float *)(L->stage + (size_t)(c & 1) * kStageBytes);
+        double *d = dst + b;
+        parallel_for(m, [f, d](int64_t lo, int64_t hi) {
+            for (int64_t k = lo; k < hi; ++k) d[k] = f[k];
+        });
+        if (c + 2 < nch) CK(issue(c + 2));   // this slot is free again
+    }
+    return LBM_OK;
+}
+
+// Copy one moments field of N values (device, FP32 or FP64) to host doubles.
+static lbm_status moments_to_host(lbm_lattice *L, const void *dev, double *dst, int64_t N) {
+    if (L->ops->compute == 8) {
+        CK(cudaMemcpyAsync(dst, dev, (size_t)N * 8, cudaMemcpyDeviceToHost, L->stream));
+        return LBM_OK;
+    }
+    if (double *d = (double *)mapped_host(dst)) {
+        k_widen<<<kWidenBlocks, 256, 0, L->stream>>>((const float *)dev, d, N);
+        CK(cudaGetLastError());
+        return LBM_OK;
+    }
+    return widen_staged(L, (const float *)dev, dst, N);
+}
+
 extern "C" lbm_status lbm_read_moments(lbm_lattice *L, double *rho, double *ux, double *uy) {
     if (!L) return lbm_fail(LBM_EINVAL, "lattice is NULL");
     const int64_t N = L->pl.N;
     const size_t comp = L->ops->compute;
-    std::vector<unsigned char> buf(3 * (size_t)N * comp);
-    CK(cudaStreamSynchronize(L->stream));
-    CK(cudaMemcpy(buf.data(), L->h.mom, buf.size(), cudaMemcpyDeviceToHost));
     double *dst[3] = {rho, ux, uy};
     for (int k = 0; k < 3; ++k) {
         if (!dst[k]) continue;
-        if (comp == 8) {
-            memcpy(dst[k], buf.data() + (size_t)k * N * 8, (size_t)N * 8);
-        } else {
-            const float *f = (const float *)(buf.data() + (size_t)k * N * 4);
-            double *d = dst[k];
-            parallel_for(N, [f, d](int64_t b, int64_t e) {
-                for (int64_t n = b; n < e; ++n) d[n] = f[n];
-            });
-        }
+        const lbm_status s = moments_to_host(L, (const char *)L->h.mom + (size_t)k * N * comp, dst[k], N);
+        if (s != LBM_OK) return s;
     }
+    CK(cudaStreamSynchronize(L->stream));
     return check_err(L);
 }
 

@@ -40,6 +40,8 @@ struct lbm_lattice {
     unsigned long long *count;
     cudaGraphExec_t graph[4];
     int graph_steps;
+    char *stage;                // page-locked read-back staging (lazy), two chunks
+    cudaEvent_t stage_ev[2];
 };
 
 lbm_status lbm_fail(lbm_status s, const char *fmt, ...);

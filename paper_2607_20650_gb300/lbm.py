@@ -234,8 +234,14 @@ def lbm_wait(h, timeout_s: float) -> int:
     return s
 
 
-def lbm_read_moments(h, N: int):
-    out = [np.empty(N) for _ in range(3)]
+def lbm_read_moments(h, N: int, out=None):
+    """(rho, ux, uy) as FP64 host arrays; ``out`` gives the three arrays
+    (N contiguous doubles each, e.g. views of page-locked torch tensors)."""
+    if out is None:
+        out = [np.empty(N) for _ in range(3)]
+    for a in out:
+        if a.dtype != np.float64 or a.size != N or not a.flags.c_contiguous:
+            raise ValueError("moments output arrays must be N contiguous float64 values each")
     _check(load().lbm_read_moments(h, *[a.ctypes.data for a in out]), "lbm_read_moments")
     return out
 
@@ -523,8 +529,8 @@ class Lattice:
         lbm_sync(self.h)
         return self
 
-    def moments(self):
-        return lbm_read_moments(self.h, self.N)
+    def moments(self, out=None):
+        return lbm_read_moments(self.h, self.N, out)
 
     def populations(self, as_: str = "f64") -> np.ndarray:
         return lbm_read_populations(self.h, self.N, as_)
