@@ -113,6 +113,10 @@ typedef enum {
                                      row spans (default when tile_x % 32 == 0) */
 #define LBM_FLAG_WIDE_OFFSETS 0x8u  /* D3Q19: 64-bit addressing for every pull, the path
                                        lattices too large for 32-bit offset tables take */
+#define LBM_FLAG_NO_PREFETCH 0x10u  /* LPTL/NPTL/AA: no L2 prefetch of the records pulled
+                                       by the blocks launched next (default: on for 32-bit
+                                       storage in the stream and bundle layouts when a
+                                       lattice exceeds the L2 cache) */
 
 typedef struct lbm_params {
     int32_t nx, ny;          /* lattice size; nx*ny < 2^32 */

@@ -20,6 +20,7 @@ struct HostArgs {
     int block_1d;              // LPTL block size
     uint32_t flags;            // lbm_params.flags
     uint64_t nx_magic;         // ceil(2^64 / nx) for n -> (x, y); 0 when nx == 1
+    uint32_t pf;               // L2 prefetch distance: nodes (LPTL) or rows (NPTL); 0 = off
     const uint8_t *links;
     void *pop[2];              // pop[1] == nullptr for one-lattice algorithms
     void *halo;                // one-lattice buffer grid (2 parities)

@@ -37,6 +37,7 @@ struct Step {
     uint64_t nx_magic;
     int off32;  // 9N < 2^32: element offsets fit 32 bits
     int aos16;  // nx % 16 == 0: warp segments of 32 records start on 16-byte boundaries
+    uint32_t pf;  // L2 prefetch distance of the two-lattice kernel: nodes (LPTL), rows (NPTL); 0 = off
 };
 
 // Host: FP64 constants rounded once to the compute type.
@@ -93,6 +94,7 @@ Step<S> make_step(const HostArgs &h, const StepCall &c) {
     a.nx_magic = h.nx_magic;
     a.off32 = (9 * h.N) < (int64_t(1) << 32) ? 1 : 0;
     a.aos16 = (h.nx % 16 == 0) ? 1 : 0;
+    a.pf = h.pf;
     return a;
 }
 
@@ -468,23 +470,55 @@ __global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : 4) k_two
     for (int k = lane; k < OUT_CHUNKS; k += 32) d4[k] = o4[k];
 }
 
+// L2 prefetch of one node's source record (stream and bundle layouts): one
+// address per DRAM sector the record occupies, every value of the stream
+// layout and the first value of each bundle (a bundle straddling two sectors
+// has its second one fetched by the neighbour's prefetch).
+template <class S, int L>
+__device__ __forceinline__ void prefetch_record(const S *src, uint32_t N, uint32_t n) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        if (L == STREAM || i % 3 == 0)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(src + addr<L>(N, n, i)));
+}
+
 // LPTL (LINEAR: one node per thread over n, block size from the runtime) and
 // NPTL (2-D tiles of tx x ty nodes over a padded grid).
+//
+// Blocks start in index order, so the node a.pf nodes (LPTL) or a.pf rows
+// (NPTL) ahead belongs to a block that starts a few microseconds later. Each
+// thread loads that node's link byte first and, once its own node is stored,
+// prefetches the node's source record into L2 when it is fluid: the pulls of
+// the later block then hit L2 instead of waiting on DRAM, and the prefetches
+// keep more DRAM requests in flight than the pulls alone at full occupancy.
+// Solid records are not fetched, so DRAM traffic does not grow. Only 32-bit
+// storage in the stream and bundle layouts has it: the 16-bit update is bound
+// by instruction issue (the prefetch cost 3 %), and the collision layout's
+// LPTL form spills at 32 registers with it (its NPTL form is the staged
+// kernel above).
 template <class S, int L, bool LINEAR>
 __global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : 4) k_two_lattice(const Step<S> a) {
     const uint32_t nx = (uint32_t)a.geo.nx, ny = (uint32_t)a.geo.ny;
-    uint32_t x, y;
+    constexpr bool PF = sizeof(S) == 4 && L != COLLISION;
+    uint32_t x, y, np = 0;
+    bool ahead;
     if (LINEAR) {
         const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
         if (n >= a.N) return;
         y = a.nx_magic ? (uint32_t)__umul64hi((unsigned long long)n, a.nx_magic) : n;
         x = n - y * nx;
+        ahead = PF && a.pf != 0u && a.N - n > a.pf;
+        np = n + a.pf;
     } else {
         x = blockIdx.x * a.tx + threadIdx.x;
         y = blockIdx.y * a.ty + threadIdx.y;
         if (x >= nx || y >= ny) return;
+        ahead = PF && a.pf != 0u && ny - y > a.pf;
+        np = (y + a.pf) * nx + x;
     }
+    const uint32_t lkp = ahead ? (uint32_t)a.links[np] : SOLID_LINKS;
     two_lattice_node<S, L>(a, x, y, (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u));
+    if (PF && lkp != SOLID_LINKS) prefetch_record<S, L>(a.src, a.N, np);
 }
 
 // ------------------------------------------------------------ buffer grid
@@ -885,7 +919,13 @@ __global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : (PHASE =
     const uint32_t x = blockIdx.x * a.tx + threadIdx.x;
     const uint32_t y = blockIdx.y * a.ty + threadIdx.y;
     if (x >= (uint32_t)a.geo.nx || y >= (uint32_t)a.geo.ny) return;
+    // L2 prefetch of the record a.pf rows ahead, as in the two-lattice kernel
+    constexpr bool PF = sizeof(S) == 4 && L != COLLISION;
+    const bool ahead = PF && a.pf != 0u && (uint32_t)a.geo.ny - y > a.pf;
+    const uint32_t np = (y + a.pf) * (uint32_t)a.geo.nx + x;
+    const uint32_t lkp = ahead ? (uint32_t)a.links[np] : SOLID_LINKS;
     aa_node<S, L, PHASE>(a, x, y, (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u));
+    if (PF && lkp != SOLID_LINKS) prefetch_record<S, L>(a.dst, a.N, np);
 }
 
 // ------------------------------------------------------------ batches

@@ -25,6 +25,7 @@ LBM_FLAG_NO_GRAPH = 1
 LBM_FLAG_TWO_NODES_PER_THREAD = 2
 LBM_FLAG_NO_STAGING = 4
 LBM_FLAG_WIDE_OFFSETS = 8
+LBM_FLAG_NO_PREFETCH = 16
 LBM_AUTO = -1
 
 

@@ -242,3 +242,13 @@ def test_d3q19_inlet_outflow_params(lib):
             lbm.lbm3_workspace_bytes(lbm.make_params3(32, 8, 8, 0.8, algo=algo,
                                                       bc=(lbm.OUTFLOW_ZG, lbm.WALL, lbm.WALL)))
         assert e.value.status == lbm.LBM_EUNSUPPORTED
+
+
+def test_flag_constants_match_header():
+    """Every LBM_FLAG_* of include/lbm.h has the same value in the binding."""
+    import re
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    flags = dict(re.findall(r"#define (LBM_FLAG_\w+) (0x[0-9a-fA-F]+)u", text))
+    assert {"LBM_FLAG_NO_GRAPH", "LBM_FLAG_NO_PREFETCH", "LBM_FLAG_WIDE_OFFSETS"} <= set(flags)
+    for name, value in flags.items():
+        assert getattr(lbm, name) == int(value, 16), name
