@@ -193,7 +193,8 @@ typedef struct lbm_info {
     int64_t cells, fluid_cells;
     int64_t steps;                 /* updates done since lbm_init */
     int32_t tile_x, tile_y;        /* tile used (LPTL: block size, 1) */
-    int32_t reserved;
+    int32_t aux;                   /* lbm_get_info: L2 prefetch distance (LPTL: nodes, NPTL
+                                      and AA: rows; 0 = off); lbm3_get_info: see there */
     double bytes_per_update;       /* algorithmic DRAM bytes of one update */
     size_t workspace_bytes;
 } lbm_info;
@@ -353,7 +354,7 @@ lbm_status lbm3_mass(lbm3_lattice *L, double *out);
  * Synchronous; AA: after an even number of updates only. */
 lbm_status lbm3_force(lbm3_lattice *L, const uint8_t *d_body, double out[3]);
 /* cells, fluid_cells, steps, tile (tile_y = tile_y * tile_z), bytes per
- * update; reserved = 1 when pulls use 64-bit addressing (large lattices or
+ * update; aux = 1 when pulls use 64-bit addressing (large lattices or
  * LBM_FLAG_WIDE_OFFSETS), 0 with the 32-bit offset tables. */
 lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out);
 void lbm3_destroy(lbm3_lattice *L);

@@ -1323,6 +1323,6 @@ extern "C" lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out) {
     if (L->pl.halo_parity)   // NPOL buffer grid: one parity read, the other written
         out->bytes_per_update += 2.0 * (double)L->pl.halo_parity * (double)L->pl.elem;
     out->workspace_bytes = L->pl.total;
-    out->reserved = L->off32 ? 0 : 1;   // 1: the 64-bit addressing path
+    out->aux = L->off32 ? 0 : 1;   // 1: the 64-bit addressing path
     return LBM_OK;
 }

@@ -704,6 +704,7 @@ extern "C" lbm_status lbm_get_info(lbm_lattice *L, lbm_info *out) {
     if (L->pl.halo_grid) bytes += 2.0 * (double)L->pl.halo_parity_elems * elem;  // buffer grid read + write
     out->bytes_per_update = bytes;
     out->workspace_bytes = L->pl.total;
+    out->aux = (int32_t)L->h.pf;
     return LBM_OK;
 }
 

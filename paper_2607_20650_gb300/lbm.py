@@ -55,7 +55,7 @@ class lbm_params(ctypes.Structure):
 class lbm_info(ctypes.Structure):
     _fields_ = [
         ("cells", ctypes.c_int64), ("fluid_cells", ctypes.c_int64), ("steps", ctypes.c_int64),
-        ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("aux", ctypes.c_int32),
         ("bytes_per_update", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
     ]
 
@@ -279,7 +279,9 @@ def lbm_write_populations(h, pops: np.ndarray):
 def lbm_get_info(h) -> dict:
     i = lbm_info()
     _check(load().lbm_get_info(h, ctypes.byref(i)), "lbm_get_info")
-    return {f: getattr(i, f) for f, _ in lbm_info._fields_ if f != "reserved"}
+    out = {f: getattr(i, f) for f, _ in lbm_info._fields_ if f != "aux"}
+    out["prefetch_distance"] = int(i.aux)
+    return out
 
 
 def lbm_destroy(h):
@@ -478,8 +480,8 @@ def lbm3_force(h, body=None) -> np.ndarray:
 def lbm3_get_info(h) -> dict:
     i = lbm_info()
     _check(load().lbm3_get_info(h, ctypes.byref(i)), "lbm3_get_info")
-    out = {f: getattr(i, f) for f, _ in lbm_info._fields_ if f != "reserved"}
-    out["wide_addressing"] = bool(i.reserved)
+    out = {f: getattr(i, f) for f, _ in lbm_info._fields_ if f != "aux"}
+    out["wide_addressing"] = bool(i.aux)
     return out
 
 
