@@ -12,6 +12,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
+#include <new>
 #include <string>
 #include <thread>
 #include <vector>
@@ -492,12 +494,26 @@ __global__ void k_widen(const float *__restrict__ s, double *__restrict__ d, int
 
 // Page-locked staging for pageable destinations: two chunks, copied and
 // widened alternately so the copy of one overlaps the widening of the other.
+// A field of up to kStageBytes goes through an unpinned host buffer instead
+// (one copy; pinning costs more than it saves there).
 static constexpr size_t kStageBytes = (size_t)64 << 20;
 
 static lbm_status stage_alloc(lbm_lattice *L) {
     if (L->stage) return LBM_OK;
     CK(cudaHostAlloc(&L->stage, 2 * kStageBytes, cudaHostAllocDefault));
     for (auto &e : L->stage_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return LBM_OK;
+}
+
+static lbm_status widen_small(lbm_lattice *L, const float *src, double *dst, int64_t n) {
+    std::unique_ptr<float[]> buf(new (std::nothrow) float[(size_t)n]);
+    if (!buf) return lbm_fail(LBM_ENOMEM, "host allocation failed");
+    CK(cudaMemcpyAsync(buf.get(), src, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, L->stream));
+    CK(cudaStreamSynchronize(L->stream));
+    const float *f = buf.get();
+    parallel_for(n, [f, dst](int64_t lo, int64_t hi) {
+        for (int64_t k = lo; k < hi; ++k) dst[k] = f[k];
+    });
     return LBM_OK;
 }
 
@@ -545,6 +561,7 @@ static lbm_status moments_to_host(lbm_lattice *L, const void *dev, double *dst, 
         CK(cudaGetLastError());
         return LBM_OK;
     }
+    if ((size_t)N * sizeof(float) <= kStageBytes) return widen_small(L, (const float *)dev, dst, N);
     return widen_staged(L, (const float *)dev, dst, N);
 }
 

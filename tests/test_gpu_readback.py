@@ -1,12 +1,13 @@
 """Host read-back of the moments through the C ABI.
 
-lbm_read_moments takes one of three routes: FP64 moments are copied as they
+lbm_read_moments takes one of four routes: FP64 moments are copied as they
 are; FP32 moments are widened to FP64 either by the device straight into a
-page-locked destination, or on the host through two page-locked staging
-chunks of 64 MB for a pageable one. Every route must give the device's
-moments exactly (widening FP32 to FP64 is exact), including a lattice whose
-fields span several staging chunks with a ragged tail, and a call that asks
-for one field only."""
+page-locked destination, or on the host for a pageable one: through an
+unpinned buffer for a field of up to 64 MB, through two page-locked staging
+chunks of 64 MB beyond that. Every route must give the device's moments
+exactly (widening FP32 to FP64 is exact), including a lattice whose fields
+span several staging chunks with a ragged tail, and a call that asks for one
+field only."""
 import numpy as np
 import pytest
 
