@@ -167,7 +167,11 @@ lbm_status lbm_sync(lbm_lattice *L);
 lbm_status lbm_wait(lbm_lattice *L, double timeout_s);
 
 /* Moments of the last update that stored them (or of lbm_init), as host
- * doubles, N each (solid nodes: rho = 1, v = 0). Synchronous. */
+ * doubles, N each (solid nodes: rho = 1, v = 0); a NULL array is skipped.
+ * Synchronous. Page-locked destinations (cudaHostAlloc, cudaHostRegister)
+ * are written by the device directly; pageable ones of more than 64 MB per
+ * field go through page-locked staging the lattice allocates on first use
+ * (128 MB of host memory, freed by lbm_destroy). */
 lbm_status lbm_read_moments(lbm_lattice *L, double *rho, double *ux, double *uy);
 
 /* Same moments as FP32 device arrays (N each), enqueued on the stream. */
