@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--geo3", default="porous", choices=["porous", "fluid"])
     ap.add_argument("--batch-only", action="store_true",
                     help="time only the 256-channel batched ensemble (profiling)")
+    ap.add_argument("--ref-seconds", type=float, default=120.0,
+                    help="--impl reference: CPU seconds for the warm-up and timed steps together")
     return ap.parse_args()
 
 
@@ -289,8 +291,7 @@ def run_reference(args):
     t = time.perf_counter()
     lat.run(1)
     per = time.perf_counter() - t
-    budget = 120.0
-    k_per_step = max(1, int(budget / max(steps + warm, 1) / per))
+    k_per_step = max(1, int(args.ref_seconds / max(steps + warm, 1) / per))
     for _ in range(warm):
         lat.run(k_per_step)
     t = time.perf_counter()
