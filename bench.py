@@ -384,7 +384,7 @@ def run_ours(args):
         result["variants"] = variants(args, mask, torch, world)
         result["batched"] = batched(args, torch)
         result["d3q19"] = d3q19(args, torch)
-    result["e2e"] = e2e(args, mask, torch)
+    result["e2e"] = e2e(args, mask, torch, world)
     if rank == 0 and not args.no_cpu and world == 1:
         result["cpu_baseline"] = cpu_sample()
     if rank == 0:
@@ -596,10 +596,11 @@ def batched(args, torch):
             "tuned_ns_per_node": [[round(tuning.ns_per_cell[l][a], 5) for a in range(4)] for l in range(3)]}
 
 
-def e2e(args, mask, torch):
+def e2e(args, mask, torch, world=1):
     """Through the C ABI with page-locked host buffers: create (mask H2D),
     init, K updates, moments D2H (three FP64 arrays), all inside the timed
-    region."""
+    region. With several ranks (replicas) the ranks start together and the
+    job's time is the slowest rank's."""
     from paper_2607_20650_gb300 import lbm
     nx, ny = args.nx, args.ny
     N = nx * ny
@@ -615,6 +616,9 @@ def e2e(args, mask, torch):
     rho, ux, uy = (torch.empty(N, dtype=torch.float64, pin_memory=True).numpy() for _ in range(3))
     stream = torch.cuda.Stream().cuda_stream
     torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     t = time.perf_counter()
     h = lbm.lbm_create(p, host_mask, ws, nbytes, stream)
     lbm.lbm_step(h, k, True)
@@ -625,8 +629,10 @@ def e2e(args, mask, torch):
     assert st == 0
     del ws
     torch.cuda.empty_cache()
-    return {"value": N * k / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": N / k,
-            "d2h_bytes_per_step": 3 * 8 * N / k, "steps": k,
+    if world > 1:
+        dt = max_over_ranks(dt, "cuda")
+    return {"value": N * k * world / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": N * world / k,
+            "d2h_bytes_per_step": 3 * 8 * N * world / k, "steps": k, "replicas": world,
             "host_buffers": "page-locked",
             "region": "lbm_create(host mask) + init + K updates + lbm_read_moments(host f64)"}
 
