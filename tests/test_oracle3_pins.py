@@ -65,6 +65,35 @@ def test_mass_conserved_3d():
     assert abs(lat.mass() - m0) / m0 < 1e-14
 
 
+def test_mass_value_is_sum_of_rho_3d():
+    """sum_i f_i^eq = rho (Eq. 2 in 3-D), so after initialisation from a given
+    density field the mass is that field summed over the fluid nodes, and
+    the rest state gives the fluid-node count. The fluid set is known by
+    construction: a solid 3x3x3 cube with a one-node hole at its centre
+    (the hole has no open pull, so it counts as solid) and a solid slab.
+    Dropping the rest weight or counting solid nodes fails."""
+    nx, ny, nz = 9, 8, 7
+    m = np.zeros((nz, ny, nx), np.uint8)
+    m[1:4, 1:4, 1:4] = 1
+    m[2, 2, 2] = 0
+    m[5, :, 6:8] = 1
+    fluid = m == 0
+    fluid[2, 2, 2] = False
+    case = O.Case3(nx, ny, nz, 0.7, bc_z=O.WALL)
+    assert O.Lattice3(case, m).mass() == float(fluid.sum())
+    rng = np.random.default_rng(5)
+    N = nx * ny * nz
+    rho = 1.0 + 0.05 * (rng.random(N) - 0.5)
+    u = [0.06 * (rng.random(N) - 0.5) for _ in range(3)]
+    lat = O.Lattice3(case, m, rho=rho, ux=u[0], uy=u[1], uz=u[2])
+    exp = math.fsum(rho[fluid.ravel()])
+    assert abs(lat.mass() - exp) <= 4e-16 * exp
+    h = lat.h.copy()
+    h[:, ~fluid.ravel()] = rng.normal(0, 0.3, size=(19, int((~fluid).sum())))
+    lat.set_h(h)
+    assert abs(lat.mass() - exp) <= 4e-16 * exp
+
+
 def _project(h3, nx, ny, nz, axis):
     """Sum D3Q19 populations over the velocity component along `axis` of a
     lattice invariant along that axis; returns D2Q9 h on the other two axes."""

@@ -94,6 +94,47 @@ def test_mass_conserved_porous_periodic():
     assert abs(lat.mass() - m0) / m0 < 1e-14
 
 
+def _pocket_mask(nx, ny):
+    """Mask with two solid blocks and one enclosed single-node fluid pocket.
+    Returns the mask and the fluid set known by construction: every mask-0
+    node except the pocket node (all eight neighbours solid: no open pull)."""
+    m = np.zeros((ny, nx), np.uint8)
+    m[2:5, 3:6] = 1          # 3x3 block with a hole in the middle ...
+    m[3, 4] = 0              # ... the enclosed pocket
+    m[6:8, 9:12] = 1         # a plain 2x3 block
+    fluid = (m == 0)
+    fluid[3, 4] = False
+    return m, fluid
+
+
+@pytest.mark.parametrize("edges", ["periodic", "walls"])
+def test_mass_value_is_sum_of_rho(edges):
+    """Eq. (2) gives sum_i f_i^eq = rho, so right after initialisation from a
+    given density field (any velocity) the total mass is sum of that field
+    over the fluid nodes; the rest state gives the fluid-node count. The
+    expected values use the inputs and the hand-known fluid set only.
+    Dropping the rest weight (rho = sum h) gives ~0.1 instead of ~100;
+    counting solid or pocket nodes adds >= 1 per node."""
+    nx, ny = 14, 10
+    mask, fluid = _pocket_mask(nx, ny)
+    kw = dict(bc_s=O.WALL, bc_n=O.WALL) if edges == "walls" else {}
+    case = O.Case(nx, ny, 0.8, **kw)
+    rest = O.Lattice(case, mask)
+    assert rest.mass() == float(fluid.sum())
+    rng = np.random.default_rng(21)
+    rho = 1.0 + 0.05 * (rng.random(nx * ny) - 0.5)
+    ux = 0.08 * (rng.random(nx * ny) - 0.5)
+    uy = 0.08 * (rng.random(nx * ny) - 0.5)
+    lat = O.Lattice(case, mask, rho=rho, ux=ux, uy=uy)
+    exp = math.fsum(rho[fluid.ravel()])
+    assert abs(lat.mass() - exp) <= 4e-16 * exp
+    # Values written into solid and pocket nodes are not mass.
+    h = lat.h.copy()
+    h[:, ~fluid.ravel()] = rng.normal(0, 0.3, size=(9, int((~fluid).sum())))
+    lat.set_h(h)
+    assert abs(lat.mass() - exp) <= 4e-16 * exp
+
+
 def test_isolated_fluid_node_is_solid():
     nx, ny = 7, 7
     mask = np.ones((ny, nx), np.uint8)
