@@ -50,6 +50,7 @@ class _Params3(ctypes.Structure):
         ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32), ("bc_z", ctypes.c_int32),
         ("bc_xe", ctypes.c_int32),
         ("ux_in", ctypes.c_double), ("uy_in", ctypes.c_double), ("uz_in", ctypes.c_double),
+        ("rho_out", ctypes.c_double),
     ]
 
 
@@ -213,8 +214,9 @@ class Lattice:
 @dataclass
 class Case3:
     """A D3Q19 lattice: size, tau, force, per-axis faces (PERIODIC or WALL);
-    on x the west face may be INLET_EQ (velocity u_in) and the east face
-    (bc_xe, default: as bc_x) OUTFLOW_ZG."""
+    on x the west face may be INLET_EQ or INLET_ZOUHE (velocity u_in) and the
+    east face (bc_xe, default: as bc_x) OUTFLOW_ZG or OUTLET_PRESSURE
+    (density rho_out)."""
     nx: int
     ny: int
     nz: int
@@ -227,11 +229,13 @@ class Case3:
     bc_z: int = PERIODIC
     bc_xe: int = -1
     u_in: tuple = (0.0, 0.0, 0.0)
+    rho_out: float = 1.0
 
     def _c(self):
         east = self.bc_x if self.bc_xe < 0 else self.bc_xe
         return _Params3(self.nx, self.ny, self.nz, self.tau, self.fx, self.fy, self.fz,
-                        self.bc_x, self.bc_y, self.bc_z, east, *[float(u) for u in self.u_in])
+                        self.bc_x, self.bc_y, self.bc_z, east, *[float(u) for u in self.u_in],
+                        float(self.rho_out))
 
 
 def directions3():

@@ -16,19 +16,38 @@
  * h = f - w. Faces: periodic or half-way wall per axis; on the x axis the
  * west face may instead be an equilibrium inlet (the x = 0 plane set to
  * f^eq(rho = 1, u_in) before the collision, the 3-D form of the 2-D
- * oracle's Dirichlet equilibrium inlet) and the east face a zero-gradient
- * outflow (the pulled source plane x = nx clamped to nx - 1). Pulls are
- * mapped in z, then y, then x, as the 2-D oracle maps y before x. Solid
- * nodes bounce back; Guo body force as in the 2-D oracle. A fluid node all
- * of whose 18 pulls bounce (or come from outside the inlet face) is treated
- * as solid.
+ * oracle's Dirichlet equilibrium inlet) or an incompressible Zou-He velocity
+ * inlet, and the east face a zero-gradient outflow (the pulled source plane
+ * x = nx clamped to nx - 1) or a Zou-He pressure outlet. Pulls are mapped in
+ * z, then y, then x, as the 2-D oracle maps y before x. Solid nodes bounce
+ * back; Guo body force as in the 2-D oracle. A fluid node all of whose 18
+ * pulls bounce (or come from outside an inlet or outlet face) is treated as
+ * solid.
+ *
+ * Zou-He faces in 3-D (the 2-D oracle's Sec. 3.1 inlet and "adapted Zou and
+ * He" outlet, written for the 19 velocities). At the west face the five
+ * populations with c_x = +1 are unknown; with T_y, T_z the y and z momentum
+ * of the nine c_x = 0 populations, sum_i g_i c_i = U and bounce-back of the
+ * normal non-equilibrium part give
+ *   g(1,0,0)   = g(-1,0,0)  + U_x / 3
+ *   g(1,+-1,0) = g(-1,-+1,0) + (U_x +- U_y) / 6 -+ (T_y / 2 - U_y / 3)
+ *   g(1,0,+-1) = g(-1,0,-+1) + (U_x +- U_z) / 6 -+ (T_z / 2 - U_z / 3).
+ * At the east face rho = rho_out and v_y = v_z = 0 fix the five c_x = -1
+ * populations: with H+, H0 the sums of the known c_x = +1 and c_x = 0
+ * deviations, u_x = 2 H+ + H0 - (rho_out - 1), and
+ *   g(-1,0,0)   = g(1,0,0)   - u_x / 3
+ *   g(-1,+-1,0) = g(1,-+1,0) - u_x / 6 -+ T_y / 2
+ *   g(-1,0,+-1) = g(1,0,-+1) - u_x / 6 -+ T_z / 2.
+ * Both hold unchanged for the deviations h (opposite weights are equal), and
+ * summed over c_z they are the 2-D oracle's formulas.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
-enum { F3_PERIODIC = 0, F3_WALL = 1, F3_INLET_EQ = 4, F3_OUTFLOW_ZG = 5 };
+enum { F3_PERIODIC = 0, F3_WALL = 1, F3_INLET_ZOUHE = 3, F3_INLET_EQ = 4, F3_OUTFLOW_ZG = 5,
+       F3_OUTLET_PRESSURE = 7 };
 enum { P3_NODE = 0, P3_BOUNCE = 1 };
 
 typedef struct {
@@ -36,8 +55,10 @@ typedef struct {
     double tau;
     double fx, fy, fz;
     int32_t bc_x, bc_y, bc_z;   /* per axis: both faces periodic or both walls; bc_x: the west face */
-    int32_t bc_xe;              /* east face: periodic (with bc_x), wall or zero-gradient outflow */
-    double ux_in, uy_in, uz_in; /* inlet velocity (bc_x = F3_INLET_EQ) */
+    int32_t bc_xe;              /* east face: periodic (with bc_x), wall, zero-gradient outflow or
+                                   pressure outlet */
+    double ux_in, uy_in, uz_in; /* inlet velocity (bc_x = F3_INLET_EQ or F3_INLET_ZOUHE) */
+    double rho_out;             /* outlet density (bc_xe = F3_OUTLET_PRESSURE) */
 } oracle3_params;
 
 static int C3[19][3];
@@ -79,8 +100,9 @@ void oracle3_equilibrium(double drho, double ux, double uy, double uz, double *h
 }
 
 /* Source of the value pulled by (x, y, z) in direction i: z and y wrap or
- * bounce; x wraps, bounces, is clamped (outflow) or unknown (inlet, marked
- * as a bounce: the inlet plane is overwritten before the collision). */
+ * bounce; x wraps, bounces, is clamped (outflow) or unknown (inlet or
+ * pressure outlet, marked as a bounce: those values are replaced before the
+ * collision). */
 static int pull3(const oracle3_params *p, int x, int y, int z, int i, int64_t *src) {
     int s[3] = {x - C3[i][0], y - C3[i][1], z - C3[i][2]};
     const int ext[3] = {p->nx, p->ny, p->nz};
@@ -131,6 +153,54 @@ void oracle3_init(const oracle3_params *p, const uint8_t *solid, const double *r
     }
 }
 
+/* Index of the direction (cx, cy, cz). */
+static int dir3(int cx, int cy, int cz) {
+    for (int i = 0; i < 19; ++i)
+        if (C3[i][0] == cx && C3[i][1] == cy && C3[i][2] == cz) return i;
+    return -1;
+}
+
+/* y and z momentum of the nine populations with c_x = 0. */
+static void transverse3(const double *g, double *ty, double *tz) {
+    *ty = 0.0;
+    *tz = 0.0;
+    for (int i = 0; i < 19; ++i) {
+        if (C3[i][0] != 0) continue;
+        *ty += C3[i][1] * g[i];
+        *tz += C3[i][2] * g[i];
+    }
+}
+
+/* Zou-He velocity inlet on the west face (formulas in the header). */
+static void zou_he_inlet3(const oracle3_params *p, double *g) {
+    const double Ux = p->ux_in, Uy = p->uy_in, Uz = p->uz_in;
+    double ty, tz;
+    transverse3(g, &ty, &tz);
+    const double ny_ = 0.5 * ty - Uy / 3.0, nz_ = 0.5 * tz - Uz / 3.0;
+    g[dir3(1, 0, 0)] = g[dir3(-1, 0, 0)] + Ux / 3.0;
+    g[dir3(1, 1, 0)] = g[dir3(-1, -1, 0)] + (Ux + Uy) / 6.0 - ny_;
+    g[dir3(1, -1, 0)] = g[dir3(-1, 1, 0)] + (Ux - Uy) / 6.0 + ny_;
+    g[dir3(1, 0, 1)] = g[dir3(-1, 0, -1)] + (Ux + Uz) / 6.0 - nz_;
+    g[dir3(1, 0, -1)] = g[dir3(-1, 0, 1)] + (Ux - Uz) / 6.0 + nz_;
+}
+
+/* Zou-He pressure outlet on the east face (formulas in the header). */
+static void zou_he_outlet3(const oracle3_params *p, double *g) {
+    double hp = 0.0, h0 = 0.0;
+    for (int i = 0; i < 19; ++i) {
+        if (C3[i][0] > 0) hp += g[i];
+        if (C3[i][0] == 0) h0 += g[i];
+    }
+    const double ux = 2.0 * hp + h0 - (p->rho_out - 1.0);
+    double ty, tz;
+    transverse3(g, &ty, &tz);
+    g[dir3(-1, 0, 0)] = g[dir3(1, 0, 0)] - ux / 3.0;
+    g[dir3(-1, 1, 0)] = g[dir3(1, -1, 0)] - ux / 6.0 - 0.5 * ty;
+    g[dir3(-1, -1, 0)] = g[dir3(1, 1, 0)] - ux / 6.0 + 0.5 * ty;
+    g[dir3(-1, 0, 1)] = g[dir3(1, 0, -1)] - ux / 6.0 - 0.5 * tz;
+    g[dir3(-1, 0, -1)] = g[dir3(1, 0, 1)] - ux / 6.0 + 0.5 * tz;
+}
+
 void oracle3_step(const oracle3_params *p, const uint8_t *solid, const double *h_in, double *h_out,
                   double *rho, double *ux, double *uy, double *uz) {
     tables();
@@ -155,6 +225,8 @@ void oracle3_step(const oracle3_params *p, const uint8_t *solid, const double *h
                 }
                 if (x == 0 && p->bc_x == F3_INLET_EQ)   /* Dirichlet equilibrium inlet */
                     oracle3_equilibrium(0.0, p->ux_in, p->uy_in, p->uz_in, g);
+                if (x == 0 && p->bc_x == F3_INLET_ZOUHE) zou_he_inlet3(p, g);
+                if (x == p->nx - 1 && p->bc_xe == F3_OUTLET_PRESSURE) zou_he_outlet3(p, g);
                 double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
                 for (int i = 0; i < 19; ++i) {
                     drho += g[i];

@@ -201,3 +201,62 @@ def test_inlet_outflow_channel_reduces_to_d2q9():
     lat2 = O.Lattice(case2, mask2, ux=u2, uy=v2).run(30)
     proj = _project(lat3.h, nx, ny, nz, 2).reshape(9, -1)
     np.testing.assert_allclose(proj, lat2.h, rtol=0, atol=5e-16)
+
+
+# ---------------------------------------------------------------- Zou-He faces
+
+@pytest.mark.parametrize("axis", [1, 2])
+def test_zou_he_channel_reduces_to_d2q9(axis):
+    """Zou-He velocity inlet (west) and pressure outlet (east) with walls on
+    the kept transverse axis and an obstacle: a lattice invariant along y
+    (axis 1, inlet velocity with a z component) or z (axis 2, with a y
+    component), summed over that velocity component, is the 2-D oracle's
+    channel with the same edges, whose inlet and outlet are pinned by their
+    defining conditions and by exact-rational brute force."""
+    n1, n2, m = 18, 9, 3
+    rng = np.random.default_rng(7 + axis)
+    mask2 = np.zeros((n2, n1), np.uint8)
+    mask2[3:6, 6:8] = 1
+    u2 = np.where(mask2 > 0, 0.0, 0.03 + 5e-3 * rng.random((n2, n1)))
+    v2 = np.where(mask2 > 0, 0.0, 5e-3 * (rng.random((n2, n1)) - 0.5))
+    rho2 = 1.0 + 1e-3 * rng.random((n2, n1))
+    U, Ut, rho_out = 0.035, 0.004, 0.9985
+    if axis == 2:
+        nx, ny, nz = n1, n2, m
+        tile = lambda a: np.broadcast_to(a, (nz, ny, nx))
+        case3 = O.Case3(nx, ny, nz, 0.7, bc_x=O.INLET_ZOUHE, bc_xe=O.OUTLET_PRESSURE, bc_y=O.WALL,
+                        u_in=(U, Ut, 0.0), rho_out=rho_out)
+        uu = dict(ux=tile(u2).ravel(), uy=tile(v2).ravel())
+    else:
+        nx, ny, nz = n1, m, n2
+        tile = lambda a: np.broadcast_to(a[:, None, :], (nz, ny, nx))
+        case3 = O.Case3(nx, ny, nz, 0.7, bc_x=O.INLET_ZOUHE, bc_xe=O.OUTLET_PRESSURE, bc_z=O.WALL,
+                        u_in=(U, 0.0, Ut), rho_out=rho_out)
+        uu = dict(ux=tile(u2).ravel(), uz=tile(v2).ravel())
+    lat3 = O.Lattice3(case3, tile(mask2).ravel(), rho=tile(rho2).ravel(), **uu).run(30)
+    case2 = O.Case(n1, n2, 0.7, ux_in=U, uy_in=Ut, bc_w=O.INLET_ZOUHE, bc_e=O.OUTLET_PRESSURE, bc_s=O.WALL,
+                   bc_n=O.WALL, rho_out=rho_out)
+    lat2 = O.Lattice(case2, mask2, rho=rho2, ux=u2, uy=v2).run(30)
+    proj = _project(lat3.h, nx, ny, nz, axis).reshape(9, -1)
+    np.testing.assert_allclose(proj, lat2.h, rtol=0, atol=5e-16)
+
+
+def test_zou_he_faces_fix_their_moments_3d():
+    """The defining conditions, on a fully 3-D state (no invariant axis):
+    every inlet node's velocity after the update is U (sum_i g_i c_i = U, no
+    force), every outlet node's density is rho_out and its transverse
+    velocity is zero."""
+    nx, ny, nz = 9, 6, 5
+    N = nx * ny * nz
+    rng = np.random.default_rng(11)
+    U, rho_out = (0.03, -0.006, 0.004), 1.002
+    case = O.Case3(nx, ny, nz, 0.65, bc_x=O.INLET_ZOUHE, bc_xe=O.OUTLET_PRESSURE, bc_y=O.WALL,
+                   u_in=U, rho_out=rho_out)
+    lat = O.Lattice3(case, None, rho=1 + 2e-3 * rng.random(N), ux=0.03 + 1e-2 * rng.random(N),
+                     uy=1e-2 * (rng.random(N) - 0.5), uz=1e-2 * (rng.random(N) - 0.5)).run(3)
+    x = np.arange(N) % nx
+    inl, out = x == 0, x == nx - 1
+    for comp, u in zip((lat.ux, lat.uy, lat.uz), U):
+        assert np.max(np.abs(comp[inl] - u)) < 1e-16
+    assert np.max(np.abs(lat.rho[out] - rho_out)) < 4e-16
+    assert np.max(np.abs(lat.uy[out])) < 1e-16 and np.max(np.abs(lat.uz[out])) < 1e-16
