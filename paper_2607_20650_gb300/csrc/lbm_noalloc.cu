@@ -17,9 +17,13 @@
 //    different streams, or from different host threads) race on it;
 //  - every block overwrites its own partial and the final kernel overwrites
 //    the sum, so nothing has to be cleared between calls;
-//  - the first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture.
+//  - the first call on a device does the set-up: it looks up the array's
+//    device address (cudaGetSymbolAddress) with that device current and keeps
+//    it for the process; make that first call before any stream capture;
+//  - the kept address is not refreshed after cudaDeviceReset, so the entry
+//    point must not be called after a reset of the device in this process;
+//  - every call copies the result into host memory and synchronises its
+//    stream before returning.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -41,8 +45,11 @@ __device__ __align__(256) double g_mass_scratch[kMaxBlocks + 32];
 std::mutex g_mu;
 double *g_scratch_addr[kMaxDevices] = {};
 
-// Same sum as the workspace reduction: over fluid nodes, rho = 1 + sum_i h_i
-// with h in canonical order h[i*N + n], accumulated in FP64 per block.
+// The same quantity as the workspace reduction (over fluid nodes,
+// rho = 1 + sum_i h_i with h in canonical order h[i*N + n], in FP64) in a
+// different fixed order: blocks of kNodesPerBlock nodes, then the block sums
+// in index order. It agrees with lbm_mass to round-off, and repeated calls
+// on the same data give identical bits.
 __global__ void __launch_bounds__(kThreads) k_mass_blocks(const float *h, const uint8_t *solid,
                                                           uint32_t N, double *partials) {
     __shared__ double red[kThreads];
