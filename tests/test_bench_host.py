@@ -68,4 +68,6 @@ def test_reference_arm_json_line():
     assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 3 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["config"]["workload"].startswith("porous 2048x1024") and "seed 33" in d["config"]["workload"]
+    assert d["config"]["stands_in_for"] == bench.WORKLOAD
     assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

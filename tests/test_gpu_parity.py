@@ -192,10 +192,14 @@ def test_divergence_is_reported_not_trapped():
 
 
 def test_bounded_wait_times_out_then_completes():
-    lat = lbm.Lattice(2048, 1024, 0.8, None, storage="f32", flags=lbm.LBM_FLAG_NO_GRAPH)
-    lat.step(400)
+    """2,000 ungraphed updates of an 8.4M-node lattice queue about 100 ms of
+    GPU work; a zero timeout right after enqueueing must report LBM_ETIMEOUT
+    (the queue holds at most ~1,000 launches, so at least half of it is
+    still pending), and a long one must then complete."""
+    lat = lbm.Lattice(4096, 2048, 0.8, None, storage="f32", flags=lbm.LBM_FLAG_NO_GRAPH)
+    lat.step(2000)
     s = lbm.lbm_wait(lat.h, 0.0)
-    assert s in (lbm.LBM_ETIMEOUT, lbm.LBM_OK)
+    assert s == lbm.LBM_ETIMEOUT
     assert lbm.lbm_wait(lat.h, 120.0) == lbm.LBM_OK
     lat.close()
 
