@@ -176,8 +176,19 @@ extern "C" lbm_status lbm_workspace_bytes(const lbm_params *p, size_t *bytes) {
 // resident thread sets ahead gain 5 to 9 %, 3.4 sets nothing, 6.7 sets lose
 // 18 %; on the 134M-node lattice without solids 0.8 sets gain 5 %, 1.3 sets
 // 3 %, 2.1 sets lose 6 %.
-static uint32_t prefetch_distance(const lbm_params *p, int64_t N, size_t elem) {
-    if ((p->flags & LBM_FLAG_NO_PREFETCH) || elem != 4) return 0;
+#ifndef LBM_PF_PAIRS
+#define LBM_PF_PAIRS 1
+#endif
+static uint32_t prefetch_distance(const lbm_params *p, int64_t N, size_t elem, int tile_x) {
+    if (p->flags & LBM_FLAG_NO_PREFETCH) return 0;
+    // 16-bit storage: only the node-pair kernel (LPTL/NPTL, bundle layout,
+    // nx even) prefetches; its distance counts pairs of nodes. Measured on
+    // the 134M-node porous lattice (FP16, NPTL 32 x 8): +6 %.
+    const bool pairs = elem == 2 && LBM_PF_PAIRS && (p->algo == LBM_LPTL || p->algo == LBM_NPTL) &&
+                       p->layout == LBM_LAYOUT_BUNDLE && p->nx % 2 == 0 &&
+                       !(p->flags & LBM_FLAG_NO_PAIRS) && 9 * N < (int64_t(1) << 32) &&
+                       (p->algo == LBM_LPTL || tile_x % 2 == 0);
+    if (elem != 4 && !pairs) return 0;
     if ((p->algo != LBM_LPTL && p->algo != LBM_NPTL && p->algo != LBM_AA) || p->layout == LBM_LAYOUT_COLLISION)
         return 0;
     int dev = 0, sms = 0, threads = 0, l2 = 0;
@@ -189,7 +200,11 @@ static uint32_t prefetch_distance(const lbm_params *p, int64_t N, size_t elem) {
         return 0;
     }
     if ((double)N * 9.0 * (double)elem <= (double)l2) return 0;
-    const int64_t nodes = (int64_t)sms * threads * 5 / 4;
+#ifndef LBM_PF_NUM
+#define LBM_PF_NUM 5
+#endif
+    // pairs: LPTL distances count pairs (the kernel doubles them), NPTL rows
+    const int64_t nodes = (int64_t)sms * threads * LBM_PF_NUM / 4 * (pairs && p->algo == LBM_NPTL ? 2 : 1);
     if (p->algo == LBM_LPTL) return nodes < N ? (uint32_t)nodes : 0;
     const int64_t rows = std::max<int64_t>(1, (nodes + p->nx / 2) / p->nx);
     return rows < p->ny ? (uint32_t)rows : 0;
@@ -224,7 +239,7 @@ void lbm_fill_args(const lbm_params *p, const Plan &pl, char *ws, const Ops *ops
     h->block_1d = p->algo == LBM_LPTL ? ops->lptl_block(p->layout) : 0;
     h->flags = p->flags;
     h->nx_magic = p->nx == 1 ? 0ull : (~0ull / (uint64_t)p->nx) + 1ull;
-    h->pf = prefetch_distance(p, pl.N, ops->elem);
+    h->pf = prefetch_distance(p, pl.N, ops->elem, pl.tx);
     h->links = (const uint8_t *)(ws + pl.links);
     h->pop[0] = ws + pl.pop[0];
     h->pop[1] = pl.two ? ws + pl.pop[1] : nullptr;

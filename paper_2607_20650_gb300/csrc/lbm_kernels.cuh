@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
@@ -38,6 +39,7 @@ struct Step {
     int off32;  // 9N < 2^32: element offsets fit 32 bits
     int aos16;  // nx % 16 == 0: warp segments of 32 records start on 16-byte boundaries
     uint32_t pf;  // L2 prefetch distance of the two-lattice kernel: nodes (LPTL), rows (NPTL); 0 = off
+    Consts2 k2;   // FP32 arithmetic: k with every constant duplicated for the packed node pairs
 };
 
 // Host: FP64 constants rounded once to the compute type.
@@ -95,6 +97,8 @@ Step<S> make_step(const HostArgs &h, const StepCall &c) {
     a.off32 = (9 * h.N) < (int64_t(1) << 32) ? 1 : 0;
     a.aos16 = (h.nx % 16 == 0) ? 1 : 0;
     a.pf = h.pf;
+    if constexpr (sizeof(C) == 4) a.k2 = make_consts2(a.k);
+    else memset(&a.k2, 0, sizeof(a.k2));
     return a;
 }
 
@@ -191,7 +195,7 @@ __device__ __forceinline__ void collide_encode(const Step<S> &a, uint32_t x, uin
     using A = Ar<C>;
     if (EDGE) edge_substitute(a, x, g, drho_nb);
     C drho, ux, uy;
-    collide(a.k, g, drho, ux, uy);
+    collide<Codec<S>::narrow>(a.k, g, drho, ux, uy);
     if (!isfinite(drho)) atomicOr(a.err, 1u);
     if (a.mom) {
         a.mom[n] = A::add(C(1), drho);
@@ -521,6 +525,215 @@ __global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : 4) k_two
     if (PF && lkp != SOLID_LINKS) prefetch_record<S, L>(a.src, a.N, np);
 }
 
+// ------------------------------------------------------------ node pairs
+// Two-lattice update (LPTL, NPTL) for 16-bit storage with two horizontally
+// adjacent nodes per thread, x even (nx even, so a pair never wraps a row).
+// The 16-bit update is bound by instruction issue, not by DRAM, so the pair
+// shares what one node per thread repeats: one 16-bit load brings both link
+// bytes, the collision runs on packed FP32 pairs (collide2: each lane is the
+// scalar collide() bit for bit), two results are rounded to 16 bits by one
+// packed conversion, and the stores are 32-bit words. A pair's values of
+// one direction are adjacent in the stream layout (i N + n, n even); in the
+// bundle layout a pair's bundle is six adjacent values (3n even), stored as
+// three words. A solid node of a pair holding a fluid one stores its zeros in
+// the same words, so the pair's sector is written whole. Pairs touching the
+// domain edge take the per-node path.
+template <class S>
+__device__ __forceinline__ uint32_t pack_rne(float lo, float hi) {
+    uint32_t r;
+    if constexpr (sizeof(S) == 2 && std::is_same<S, __half>::value)
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    else
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+template <class S>
+__device__ __forceinline__ uint32_t bits16(S v) {
+    unsigned short u;
+    memcpy(&u, &v, 2);
+    return u;
+}
+
+// Encoded 16-bit pair words for the nine directions: word i holds direction i
+// of node a (low half) and node b (high half). A node with keep = false
+// contributes +0.
+template <class S>
+__device__ __forceinline__ void encode_pair(const Step<S> &a, uint32_t n, const f2 *g, bool ka, bool kb,
+                                            uint32_t *w) {
+    const bool sr = a.sr != 0;
+    if (!sr) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            float lo, hi;
+            up2(g[i], lo, hi);
+            w[i] = pack_rne<S>(ka ? lo : 0.0f, kb ? hi : 0.0f);
+        }
+    } else {
+        const uint32_t sk = step_key(a.seed, (uint32_t)(*a.tctr + a.toff));
+        const uint32_t nka = node_key(sk, n), nkb = node_key(sk, n + 1);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            float lo, hi;
+            up2(g[i], lo, hi);
+            const uint32_t ea = ka ? bits16(Codec<S>::enc(lo, true, pop_rand(nka, i))) : 0u;
+            const uint32_t eb = kb ? bits16(Codec<S>::enc(hi, true, pop_rand(nkb, i))) : 0u;
+            w[i] = ea | (eb << 16);
+        }
+    }
+}
+
+// Store the pair words of nodes n, n + 1 (n even) in layout L (STREAM or BUNDLE).
+template <class S, int L>
+__device__ __forceinline__ void store_pair(S *dst, uint32_t N, uint32_t n, const uint32_t *w) {
+    if (L == STREAM) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) *reinterpret_cast<uint32_t *>(dst + (uint32_t)i * N + n) = w[i];
+    } else {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            uint32_t *p = reinterpret_cast<uint32_t *>(dst + (uint32_t)b * 3u * N + 3u * n);
+            const uint32_t w0 = w[3 * b], w1 = w[3 * b + 1], w2 = w[3 * b + 2];
+            p[0] = (w0 & 0xFFFFu) | (w1 << 16);            // (a, 3b), (a, 3b+1)
+            p[1] = (w2 & 0xFFFFu) | (w0 & 0xFFFF0000u);    // (a, 3b+2), (b, 3b)
+            p[2] = (w1 >> 16) | (w2 & 0xFFFF0000u);        // (b, 3b+1), (b, 3b+2)
+        }
+    }
+}
+
+// L2 prefetch of a pair's source records (both nodes): one address per
+// bundle, or per direction in the stream layout.
+template <class S, int L>
+__device__ __forceinline__ void prefetch_pair(const S *src, uint32_t N, uint32_t n) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        if (L == STREAM || i % 3 == 0)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(src + addr<L>(N, n, i)));
+}
+
+// One pair: both link bytes in lk2 (node n in the low byte).
+template <class S, int L>
+__device__ __forceinline__ void pair_update(const Step<S> &a, uint32_t x, uint32_t y, uint32_t n, uint32_t lk2,
+                                            int lane) {
+    const uint32_t nx = (uint32_t)a.geo.nx, ny = (uint32_t)a.geo.ny;
+    const uint32_t lka = lk2 & 0xFFu, lkb = lk2 >> 8;
+    const bool fa = lka != SOLID_LINKS, fb = lkb != SOLID_LINKS;
+    const unsigned F = __ballot_sync(__activemask(), fa || fb);
+    if (!fa && !fb) {
+        // Stream layout: rewrite the zeros of a solid pair whose 32-byte
+        // sector (16 nodes = 8 pairs) also holds fluid nodes.
+        if (L == STREAM) {
+            const unsigned m = 0xFFu << (lane & ~7);
+            if (F & m) {
+                const uint32_t z[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+                store_pair<S, L>(a.dst, a.N, n, z);
+            }
+        }
+        return;
+    }
+    const bool interior = (x - 1u < nx - 3u) && (y - 1u < ny - 2u);
+    if (!interior || !a.off32) {
+        if (fa) two_lattice_fluid<S, L>(a, x, y, n, lka);
+        else if (L == STREAM) store_zero<S, L>(a.dst, a.N, n, a.off32);
+        if (fb) two_lattice_fluid<S, L>(a, x + 1u, y, n + 1u, lkb);
+        else if (L == STREAM) store_zero<S, L>(a.dst, a.N, n + 1u, a.off32);
+        return;
+    }
+    float ga[9], gb[9];
+    if (fa) {
+        pull_interior<S, L>(a.src, n, nx, a.N, lka, ga);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ga[i] = 0.0f;
+    }
+    if (fb) {
+        pull_interior<S, L>(a.src, n + 1u, nx, a.N, lkb, gb);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) gb[i] = 0.0f;
+    }
+    f2 g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = pk2(ga[i], gb[i]);
+    f2 drho2, ux2, uy2;
+    collide2(a.k2, a.k.force, g, drho2, ux2, uy2);
+    float da, db;
+    up2(drho2, da, db);
+    if ((fa && !isfinite(da)) || (fb && !isfinite(db))) atomicOr(a.err, 1u);
+    if (a.mom) {
+        const f2 r2 = add2(dup2(1.0f), drho2);
+        if (fa && fb) {
+            *reinterpret_cast<f2 *>(a.mom + n) = r2;
+            *reinterpret_cast<f2 *>(a.mom + a.N + n) = ux2;
+            *reinterpret_cast<f2 *>(a.mom + 2 * a.N + n) = uy2;
+        } else {
+            float r0, r1, u0, u1, v0, v1;
+            up2(r2, r0, r1);
+            up2(ux2, u0, u1);
+            up2(uy2, v0, v1);
+            const uint32_t m = fa ? n : n + 1u;
+            a.mom[m] = fa ? r0 : r1;
+            a.mom[a.N + m] = fa ? u0 : u1;
+            a.mom[2 * a.N + m] = fa ? v0 : v1;
+        }
+    }
+    if (L == BUNDLE && fa && fb && !a.sr) {
+        // both fluid, nearest rounding: each 32-bit word of a bundle pair is
+        // one packed conversion of the two values it holds
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            float a0, b0, a1, b1, a2, b2;
+            up2(g[3 * b], a0, b0);
+            up2(g[3 * b + 1], a1, b1);
+            up2(g[3 * b + 2], a2, b2);
+            uint32_t *p = reinterpret_cast<uint32_t *>(a.dst + (uint32_t)b * 3u * a.N + 3u * n);
+            p[0] = pack_rne<S>(a0, a1);
+            p[1] = pack_rne<S>(a2, b0);
+            p[2] = pack_rne<S>(b1, b2);
+        }
+        return;
+    }
+    uint32_t w[9];
+    encode_pair<S>(a, n, g, fa, fb, w);
+    store_pair<S, L>(a.dst, a.N, n, w);
+}
+
+// a.pf: L2 prefetch distance as for the 32-bit kernel (pairs of nodes for
+// LPTL, rows for NPTL; 0 = off): the link bytes of the pair that far ahead
+// are loaded first, and after the pair is stored its source records are
+// prefetched into L2 when either node is fluid.
+// Measured on the 134M-node porous lattice (FP16, bundle, NPTL 32 x 8): 72
+// registers unbounded gives 119 GLUPS, 48 (five blocks of 256) 144, 40 with
+// spills 143; one node per thread 126.
+#ifndef LBM_PAIR_MINB
+#define LBM_PAIR_MINB 5
+#endif
+template <class S, int L, bool LINEAR>
+__global__ void __launch_bounds__(kMaxTileThreads / 2, LBM_PAIR_MINB) k_two_lattice_pair(const Step<S> a) {
+    const uint32_t nx = (uint32_t)a.geo.nx, ny = (uint32_t)a.geo.ny;
+    uint32_t x, y, n, np;
+    bool ahead;
+    if (LINEAR) {
+        n = 2u * (blockIdx.x * blockDim.x + threadIdx.x);
+        if (n >= a.N) return;
+        y = a.nx_magic ? (uint32_t)__umul64hi((unsigned long long)n, a.nx_magic) : n;
+        x = n - y * nx;
+        ahead = a.pf != 0u && a.N - n > 2u * a.pf;
+        np = n + 2u * a.pf;
+    } else {
+        x = blockIdx.x * (uint32_t)a.tx + 2u * threadIdx.x;
+        y = blockIdx.y * (uint32_t)a.ty + threadIdx.y;
+        if (x >= nx || y >= ny) return;
+        n = y * nx + x;
+        ahead = a.pf != 0u && ny - y > a.pf;
+        np = n + a.pf * nx;
+    }
+    const uint32_t lkp = ahead ? (uint32_t)*reinterpret_cast<const unsigned short *>(a.links + np) : 0xFFFFu;
+    const uint32_t lk2 = *reinterpret_cast<const unsigned short *>(a.links + n);
+    pair_update<S, L>(a, x, y, n, lk2, (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u));
+    if (lkp != 0xFFFFu) prefetch_pair<S, L>(a.src, a.N, np);
+}
+
 // ------------------------------------------------------------ buffer grid
 // Per tile and parity: east edge 3 x ty values (directions 2,5,8), west
 // 3 x ty (0,3,6), north 3 x tx (6,7,8), south 3 x tx (0,1,2).
@@ -570,6 +783,50 @@ __device__ __forceinline__ void halo_publish(S *hw, int tx, int ty, int ntx, int
 // sources from the lattice, cross-tile sources from the buffer grid of the
 // previous update), the block barrier separates all reads from the in-place
 // writes, and edge nodes publish their outgoing values for the next update.
+
+// Pulls of a node off the domain edge (32-bit offsets): every lane runs the
+// interior pull (neighbour value, or the own opposite value of a bounced
+// link) and, where the source lies across a tile edge, reads instead the
+// source tile's publication of the previous update: its east/west edge when
+// the tiles differ in x (the diagonal tile at a corner), else its north/south
+// edge. Tile-edge nodes thus take no separate per-direction path, so a warp
+// holding them does not run two.
+template <class S, int L>
+__device__ __forceinline__ void npol_pull(const Step<S> &a, int bx, int by, int lx, int ly, int x, int y,
+                                          int x0, int x1, int y0, int y1, uint32_t n, uint32_t lk,
+                                          typename Codec<S>::C *g) {
+    const uint32_t nx = (uint32_t)a.geo.nx;
+    const S *own = a.dst + lay_mul<L>() * n;
+    const S *rs = own + (ptrdiff_t)lay_mul<L>() * nx;  // row y+1: source of c_y = -1
+    const S *rn = own - (ptrdiff_t)lay_mul<L>() * nx;  // row y-1: source of c_y = +1
+    const bool ex0 = x == x0, ex1 = x == x1, ey0 = y == y0, ey1 = y == y1;
+    const int per = 6 * (a.tx + a.ty);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (i == 4) {
+            g[i] = Codec<S>::dec(own[(ptrdiff_t)lay_base<L>(a.N, 4)]);
+            continue;
+        }
+        const bool bounce = (lk >> link_bit(i)) & 1u;
+        const S *row = cy(i) < 0 ? rs : (cy(i) > 0 ? rn : own);
+        const S *p = bounce ? own + (ptrdiff_t)lay_base<L>(a.N, opp(i))
+                            : row + ((ptrdiff_t)lay_base<L>(a.N, i) - (ptrdiff_t)lay_mul<L>() * cx(i));
+        const bool crx = (cx(i) > 0 && ex0) || (cx(i) < 0 && ex1);
+        const bool cry = (cy(i) > 0 && ey0) || (cy(i) < 0 && ey1);
+        if (!bounce && (crx || cry)) {
+            const int bxs = bx - (crx ? cx(i) : 0), bys = by - (cry ? cy(i) : 0);
+            const S *t = a.halo_rd + (int64_t)(bys * a.ntx + bxs) * per;
+            if (crx) {
+                const int r = cry ? (cy(i) > 0 ? a.ty - 1 : 0) : ly - cy(i);
+                p = t + (cx(i) > 0 ? 0 : 3 * a.ty) + (i / 3) * a.ty + r;
+            } else {
+                p = t + 6 * a.ty + (cy(i) > 0 ? 0 : 3 * a.tx) + (i % 3) * a.tx + (lx - cx(i));
+            }
+        }
+        g[i] = Codec<S>::dec(*p);
+    }
+}
+
 template <class S, int L>
 __device__ __forceinline__ void npol_tile(const Step<S> &a, int bx, int by, int lx, int ly, int lane) {
     using C = typename Codec<S>::C;
@@ -589,11 +846,11 @@ __device__ __forceinline__ void npol_tile(const Step<S> &a, int bx, int by, int 
     (void)F;
     const bool zero_fill = false;   // measured: NPOL is 5 % faster without the sector zero fill
     const bool inner = x > x0 && x < x1 && y > y0 && y < y1;
+    const bool dom_inner = x > 0 && x < nx - 1 && y > 0 && y < ny - 1;
     C g[9];
-    if (fluid && inner && a.off32) {
-        pull_interior<S, L>(lat, n, (uint32_t)nx, a.N, lk, g);
+    if (fluid && dom_inner && a.off32) {
+        npol_pull<S, L>(a, bx, by, lx, ly, x, y, x0, x1, y0, y1, n, lk, g);
     } else if (fluid) {
-        const bool dom_inner = x > 0 && x < nx - 1 && y > 0 && y < ny - 1;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if (i == 4) {
@@ -811,33 +1068,36 @@ __device__ __forceinline__ void aa_node(const Step<S> &a, uint32_t x, uint32_t y
     }
     const bool interior = (x - 1u < nx - 2u) && (y - 1u < ny - 2u);
     if (interior && a.off32) {
-        // Row pointers with constant offsets: pull slot 8-i of x - c_i (or
-        // own slot i when bounced), push to slot i of x + c_i (or own slot 8-i).
-        S *own = lat + lay_mul<L>() * n;
-        S *ra = own + (ptrdiff_t)lay_mul<L>() * nx;  // row y+1
-        S *rb = own - (ptrdiff_t)lay_mul<L>() * nx;  // row y-1
+        // 32-bit element indices with constant offsets: pull slot 8-i of
+        // x - c_i (or own slot i when bounced), push to slot i of x + c_i (or
+        // own slot 8-i). Each access is one select between two indices and one
+        // widening address computation (measured 2 % faster than selecting
+        // between 64-bit row pointers, at the same 40 registers).
+        const uint32_t own = lay_mul<L>() * n;
+        const uint32_t ra = own + lay_mul<L>() * nx;  // row y+1
+        const uint32_t rb = own - lay_mul<L>() * nx;  // row y-1
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if (i == 4) {
-                g[i] = Codec<S>::dec(own[(ptrdiff_t)lay_base<L>(a.N, 4)]);
+                g[i] = Codec<S>::dec(lat[own + lay_base<L>(a.N, 4)]);
                 continue;
             }
-            S *src_row = cy(i) < 0 ? ra : (cy(i) > 0 ? rb : own);
-            const S *pp = src_row + ((ptrdiff_t)lay_base<L>(a.N, opp(i)) - (ptrdiff_t)lay_mul<L>() * cx(i));
-            const S *pb = own + (ptrdiff_t)lay_base<L>(a.N, i);
-            g[i] = Codec<S>::dec(*(((lk >> link_bit(i)) & 1u) ? pb : pp));
+            const uint32_t row = cy(i) < 0 ? ra : (cy(i) > 0 ? rb : own);
+            const uint32_t ip = row + lay_base<L>(a.N, opp(i)) - (uint32_t)((int)lay_mul<L>() * cx(i));
+            const uint32_t ib = own + lay_base<L>(a.N, i);
+            g[i] = Codec<S>::dec(lat[((lk >> link_bit(i)) & 1u) ? ib : ip]);
         }
         collide_encode(a, x, n, g, e);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if (i == 4) {
-                own[(ptrdiff_t)lay_base<L>(a.N, 4)] = e[4];
+                lat[own + lay_base<L>(a.N, 4)] = e[4];
                 continue;
             }
-            S *dst_row = cy(i) > 0 ? ra : (cy(i) < 0 ? rb : own);
-            S *pp = dst_row + ((ptrdiff_t)lay_base<L>(a.N, i) + (ptrdiff_t)lay_mul<L>() * cx(i));
-            S *pb = own + (ptrdiff_t)lay_base<L>(a.N, opp(i));
-            *(((lk >> link_bit(opp(i))) & 1u) ? pb : pp) = e[i];
+            const uint32_t row = cy(i) > 0 ? ra : (cy(i) < 0 ? rb : own);
+            const uint32_t ip = row + lay_base<L>(a.N, i) + (uint32_t)((int)lay_mul<L>() * cx(i));
+            const uint32_t ib = own + lay_base<L>(a.N, opp(i));
+            lat[((lk >> link_bit(opp(i))) & 1u) ? ib : ip] = e[i];
         }
         return;
     }
@@ -1272,12 +1532,30 @@ int lptl_block() {
     return block;
 }
 
+// Node pairs: 16-bit storage in the bundle layout, nx even, 32-bit offsets,
+// unless LBM_FLAG_NO_PAIRS asks for one node per thread. (The stream layout
+// measured 7 % slower with pairs than with one node per thread: nine
+// separate arrays give each pair nine 32-bit stores and nine prefetches.)
+template <class S, int L>
+bool pairs_ok(const HostArgs &h) {
+    return sizeof(S) == 2 && L == BUNDLE && (h.nx % 2) == 0 && (9 * h.N) < (int64_t(1) << 32) &&
+           !(h.flags & 0x20u);
+}
+
 template <class S, int L>
 cudaError_t step_layout(const HostArgs &h, const Step<S> &a, int phase, cudaStream_t st) {
     using C = typename Codec<S>::C;
     const dim3 tile(h.tile_x, h.tile_y), grid(h.ntx, h.nty);
     switch (h.algo) {
         case LPTL: {
+            if constexpr (sizeof(S) == 2 && L == BUNDLE) {
+                if (pairs_ok<S, L>(h)) {
+                    const int b = 128;
+                    const unsigned g = (unsigned)((h.N / 2 + b - 1) / b);
+                    k_two_lattice_pair<S, L, true><<<g, b, 0, st>>>(a);
+                    break;
+                }
+            }
             const int b = h.block_1d;
             const unsigned g = (unsigned)((h.N + b - 1) / b);
             k_two_lattice<S, L, true><<<g, b, 0, st>>>(a);
@@ -1288,6 +1566,12 @@ cudaError_t step_layout(const HostArgs &h, const Step<S> &a, int phase, cudaStre
                 const size_t sm = (size_t)AosSpan<S>::WARP_BYTES * ((h.tile_x * h.tile_y + 31) / 32);
                 k_two_lattice_aos<S><<<grid, tile, sm, st>>>(a);
                 break;
+            }
+            if constexpr (sizeof(S) == 2 && L == BUNDLE) {
+                if (pairs_ok<S, L>(h) && !(h.tile_x & 1)) {
+                    k_two_lattice_pair<S, L, false><<<grid, dim3(h.tile_x / 2, h.tile_y), 0, st>>>(a);
+                    break;
+                }
             }
             // Two nodes per thread on request (4- and 8-byte storage): one node
             // per thread at 32 registers keeps full occupancy and measured faster.
