@@ -117,6 +117,11 @@ typedef enum {
                                        by the blocks launched next (default: on for 32-bit
                                        storage in the stream and bundle layouts when a
                                        lattice exceeds the L2 cache) */
+#define LBM_FLAG_NO_PAIRS 0x20u  /* LPTL/NPTL, F16S/BF16S storage: one node per thread
+                                    with scalar FP32 arithmetic (default when nx is even,
+                                    the layout is bundle and tile_x is even: two
+                                    adjacent nodes per thread with packed FP32
+                                    arithmetic; the results are bit-identical) */
 
 typedef struct lbm_params {
     int32_t nx, ny;          /* lattice size; nx*ny < 2^32 */
@@ -223,14 +228,25 @@ lbm_status lbm_quantize(int32_t storage, int32_t rounding, uint64_t seed, int64_
  * code hosted by a framework that owns every device allocation and forbids
  * direct cudaMalloc, or loops that must not incur an allocation's implicit
  * synchronisation. The paper has no counterpart; this is a library utility.
- * d_h: canonical FP32 deviations h[i*N + n] (9N floats, device); d_solid: N
- * bytes, nonzero = solid (device); out: host double, written before return
- * (the call synchronises cuda_stream). Allocates nothing: its scratch is a
- * fixed device array inside the library (one per GPU, kept until exit), so
- * N is limited to 134,217,728 nodes (LBM_EINVAL beyond). All calls share
- * that array: calls whose GPU work overlaps race. The first call on a device
- * looks the array up with that device current; make it before any stream
- * capture. */
+ * d_h: canonical FP32 deviations h[i*N + n] (9N floats, device).
+ * d_solid: N bytes (device), nonzero = a node that is not counted. It must be
+ * the effective solid set that lbm_mass skips: the given solid nodes plus
+ * every fluid node whose eight pulls all bounce (no open neighbour; such a
+ * node is treated as solid). A raw geometry mask counts each such enclosed
+ * node as rho = 1 + sum(h) = 1, i.e. one more per node.
+ * out: host double, written before return.
+ * Allocates nothing: its scratch is a fixed device array inside the library
+ * (one per GPU, kept until exit), so N is limited to 134,217,728 nodes
+ * (LBM_EINVAL beyond). All calls share that array: calls whose GPU work
+ * overlaps race. The first call on a device does the set-up: it looks the
+ * array's device address up with that device current and keeps it for the
+ * rest of the process; make that first call before any stream capture. The
+ * kept address is not refreshed after cudaDeviceReset: do not call this
+ * entry point after resetting the device in the same process. Every call
+ * copies the result to host memory and synchronises cuda_stream before it
+ * returns. The sum is the same quantity as lbm_mass in a different fixed
+ * order: it agrees with lbm_mass to round-off, and repeated calls on the
+ * same data return identical bits. */
 lbm_status lbm_mass_f32_noalloc(const float *d_h, const uint8_t *d_solid, int64_t N, double *out,
                                 void *cuda_stream);
 
@@ -319,14 +335,18 @@ typedef struct lbm3_params {
     double tau;              /* relaxation time, > 1/2 */
     double force[3];         /* Guo body force */
     int32_t bc_x, bc_y, bc_z;   /* LBM_BC_PERIODIC or LBM_BC_WALL, both faces of the axis;
-                                   bc_x also LBM_BC_INLET_EQ (west) or LBM_BC_OUTFLOW_ZG */
-    int32_t layout, algo, storage, rounding;   /* algo: LBM_LPTL, LBM_NPTL, LBM_NPOL or LBM_AA */
+                                   bc_x also LBM_BC_INLET_EQ or LBM_BC_INLET_ZOUHE (west face,
+                                   see bc_x_east) or LBM_BC_OUTFLOW_ZG (both x faces) */
+    int32_t layout, algo, storage, rounding;   /* algo: LBM_LPTL, LBM_NPTL, LBM_NPOL, LBM_NSOL
+                                                  or LBM_AA */
     uint64_t seed;
     int32_t tile_x, tile_y, tile_z;
     uint32_t flags;          /* LBM_FLAG_NO_GRAPH, LBM_FLAG_WIDE_OFFSETS */
-    int32_t bc_x_east;       /* east x face when bc_x = LBM_BC_INLET_EQ: LBM_BC_OUTFLOW_ZG or
-                                LBM_BC_WALL (ignored otherwise: both x faces are bc_x) */
-    double u_in[3];          /* inlet velocity for bc_x = LBM_BC_INLET_EQ */
+    int32_t bc_x_east;       /* east x face after an inlet west face: LBM_BC_OUTFLOW_ZG,
+                                LBM_BC_WALL or LBM_BC_OUTLET_PRESSURE (ignored otherwise:
+                                both x faces are bc_x) */
+    double u_in[3];          /* inlet velocity for bc_x = LBM_BC_INLET_EQ or LBM_BC_INLET_ZOUHE */
+    double rho_out;          /* outlet density for bc_x_east = LBM_BC_OUTLET_PRESSURE (> 0) */
 } lbm3_params;
 
 typedef struct lbm3_lattice lbm3_lattice;

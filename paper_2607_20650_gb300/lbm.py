@@ -26,6 +26,7 @@ LBM_FLAG_TWO_NODES_PER_THREAD = 2
 LBM_FLAG_NO_STAGING = 4
 LBM_FLAG_WIDE_OFFSETS = 8
 LBM_FLAG_NO_PREFETCH = 16
+LBM_FLAG_NO_PAIRS = 32
 LBM_AUTO = -1
 
 
@@ -81,6 +82,7 @@ class lbm3_params(ctypes.Structure):
         ("flags", ctypes.c_uint32),
         ("bc_x_east", ctypes.c_int32),
         ("u_in", ctypes.c_double * 3),
+        ("rho_out", ctypes.c_double),
     ]
 
 
@@ -398,9 +400,10 @@ def lbm_batch_destroy(h):
 
 def make_params3(nx, ny, nz, tau, *, force=(0.0, 0.0, 0.0), bc=(PERIODIC,) * 3, layout="stream",
                  algo="nptl", storage="f32", rounding="rne", seed=0, tile=(0, 0, 0),
-                 flags=0, bc_x_east=OUTFLOW_ZG, u_in=(0.0, 0.0, 0.0)) -> lbm3_params:
-    """bc = (x, y, z), each PERIODIC or WALL; x may also be INLET_EQ (west;
-    the east face is then bc_x_east) or OUTFLOW_ZG (both x faces)."""
+                 flags=0, bc_x_east=OUTFLOW_ZG, u_in=(0.0, 0.0, 0.0), rho_out=1.0) -> lbm3_params:
+    """bc = (x, y, z), each PERIODIC or WALL; x may also be INLET_EQ or
+    INLET_ZOUHE (west; the east face is then bc_x_east: OUTFLOW_ZG, WALL or
+    OUTLET_PRESSURE at density rho_out) or OUTFLOW_ZG (both x faces)."""
     p = lbm3_params()
     p.nx, p.ny, p.nz, p.tau = int(nx), int(ny), int(nz), float(tau)
     for a in range(3):
@@ -416,6 +419,7 @@ def make_params3(nx, ny, nz, tau, *, force=(0.0, 0.0, 0.0), bc=(PERIODIC,) * 3, 
     p.bc_x_east = int(bc_x_east)
     for a in range(3):
         p.u_in[a] = float(u_in[a])
+    p.rho_out = float(rho_out)
     return p
 
 
