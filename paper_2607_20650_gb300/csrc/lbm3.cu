@@ -1,11 +1,14 @@
 // D3Q19 lattices (the paper's 3-D future work, Sec. 6) with the method of
 // Sec. 3.1: two-lattice pull (LPTL: one node per thread over n; NPTL: 3-D
-// tiles) and the one-lattice AA pattern (Sec. 3.3 names it, Sec. 6 lists it
-// as future work), the three layouts generalised (stream, bundle = directions
-// sharing a source row, collision), periodic or half-way wall faces,
-// bounce-back at solid nodes, Guo force, FP64/FP32/FP16/BF16 shifted storage,
-// on-the-fly moments, FP64 mass and momentum-exchange force, CUDA graphs.
-// C ABI: the lbm3_* calls of include/lbm.h.
+// tiles), the one-lattice NPOL pull and NSOL swap of Sec. 3.3 (tiles and a
+// buffer grid), and the one-lattice AA pattern (Sec. 3.3 names it, Sec. 6
+// lists it as future work), the three layouts generalised (stream, bundle =
+// directions sharing a source row, collision), periodic or half-way wall
+// faces, equilibrium or Zou-He inlet, zero-gradient outflow or Zou-He
+// pressure outlet on x, bounce-back at solid nodes, Guo force,
+// FP64/FP32/FP16/BF16 shifted storage, on-the-fly moments, FP64 mass and
+// momentum-exchange force, CUDA graphs. C ABI: the lbm3_* calls of
+// include/lbm.h.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -26,8 +29,8 @@ namespace d3 {
 
 struct Geo3 {
     int nx, ny, nz;
-    int bx, by, bz;   // y, z: PERIODIC or WALL; x: the west face (also INLET_EQ, OUTFLOW_ZG)
-    int bxe;          // the east face (PERIODIC with bx, WALL or OUTFLOW_ZG)
+    int bx, by, bz;   // y, z: PERIODIC or WALL; x: the west face (also INLET_EQ, INLET_ZOUHE, OUTFLOW_ZG)
+    int bxe;          // the east face (PERIODIC with bx, WALL, OUTFLOW_ZG or OUTLET_PRESSURE)
 };
 
 // Source node of the value pulled by (x, y, z) in direction i, or bounce
@@ -80,9 +83,86 @@ struct Step3 {
     // node-index corrections of a pull across the west (x = 0) / east face:
     // +nx / -nx periodic, +1 / -1 zero-gradient outflow (clamped source)
     int xlo_corr, xhi_corr;
-    int inlet;       // the x = 0 plane takes heq_in (equilibrium inlet)
+    int inlet;       // x = 0 plane: 1 takes heq_in (equilibrium inlet), 2 Zou-He velocity inlet
+    int outlet;      // x = nx - 1 plane: Zou-He pressure outlet
+    int rev;         // NSOL: population i of a node is stored in its slot opp(i)
     C heq_in[Q];
+    // Zou-He: U_x/3, (U_x + U_y)/6, (U_x - U_y)/6, (U_x + U_z)/6, (U_x - U_z)/6,
+    // -U_y/3, -U_z/3, rho_out - 1
+    C zh[8];
 };
+
+// Storage slot of population i in the stored state.
+template <class S>
+__host__ __device__ __forceinline__ int slot3(const Step3<S> &a, int i) {
+    return a.rev ? opp(i) : i;
+}
+
+// Zou-He velocity inlet on the west face: the five populations with
+// c_x = +1 (unknown, pulled from outside) follow from sum_i g_i c_i = U and
+// bounce-back of the normal non-equilibrium part, with the transverse
+// momenta T_y, T_z of the nine c_x = 0 populations:
+//   g10 = g8 + U_x/3,  g13 = g5 + (U_x + U_y)/6 - N_y,  g7 = g11 + (U_x - U_y)/6 + N_y,
+//   g17 = g1 + (U_x + U_z)/6 - N_z,  g3 = g15 + (U_x - U_z)/6 + N_z,
+//   N_y = T_y/2 - U_y/3,  N_z = T_z/2 - U_z/3.
+template <class S>
+__device__ __forceinline__ void zou_he3(const Step3<S> &a, typename Codec<S>::C *g) {
+    using C = typename Codec<S>::C;
+    using A = Ar<C>;
+    const C ty = A::sub(A::add(A::add(g[4], g[12]), g[18]), A::add(A::add(g[0], g[6]), g[14]));
+    const C tz = A::sub(A::add(A::add(g[14], g[16]), g[18]), A::add(A::add(g[0], g[2]), g[4]));
+    const C ny = A::fma(C(0.5), ty, a.zh[5]);
+    const C nz = A::fma(C(0.5), tz, a.zh[6]);
+    g[10] = A::add(g[8], a.zh[0]);
+    g[13] = A::sub(A::add(g[5], a.zh[1]), ny);
+    g[7] = A::add(A::add(g[11], a.zh[2]), ny);
+    g[17] = A::sub(A::add(g[1], a.zh[3]), nz);
+    g[3] = A::add(A::add(g[15], a.zh[4]), nz);
+}
+
+// Zou-He pressure outlet on the east face: rho = rho_out and v_y = v_z = 0
+// fix the five c_x = -1 populations; u_x = 2 H+ + H0 - (rho_out - 1) from
+// the known c_x = +1 (H+) and c_x = 0 (H0) deviations, then
+//   g8 = g10 - u_x/3,  g11 = g7 - u_x/6 - T_y/2,  g5 = g13 - u_x/6 + T_y/2,
+//   g15 = g3 - u_x/6 - T_z/2,  g1 = g17 - u_x/6 + T_z/2.
+template <class S>
+__device__ __forceinline__ void zou_he_pressure3(const Step3<S> &a, typename Codec<S>::C *g) {
+    using C = typename Codec<S>::C;
+    using A = Ar<C>;
+    const C hp = A::add(A::add(A::add(A::add(g[3], g[7]), g[10]), g[13]), g[17]);
+    C h0 = g[0];
+    h0 = A::add(h0, g[2]);
+    h0 = A::add(h0, g[4]);
+    h0 = A::add(h0, g[6]);
+    h0 = A::add(h0, g[9]);
+    h0 = A::add(h0, g[12]);
+    h0 = A::add(h0, g[14]);
+    h0 = A::add(h0, g[16]);
+    h0 = A::add(h0, g[18]);
+    const C ux = A::sub(A::fma(C(2), hp, h0), a.zh[7]);
+    const C ty = A::sub(A::add(A::add(g[4], g[12]), g[18]), A::add(A::add(g[0], g[6]), g[14]));
+    const C tz = A::sub(A::add(A::add(g[14], g[16]), g[18]), A::add(A::add(g[0], g[2]), g[4]));
+    const C u6 = A::mul(ux, C(1.0 / 6.0));
+    g[8] = A::fma(C(-1.0 / 3.0), ux, g[10]);
+    g[11] = A::fma(C(-0.5), ty, A::sub(g[7], u6));
+    g[5] = A::fma(C(0.5), ty, A::sub(g[13], u6));
+    g[15] = A::fma(C(-0.5), tz, A::sub(g[3], u6));
+    g[1] = A::fma(C(0.5), tz, A::sub(g[17], u6));
+}
+
+// Inlet (x = 0) and outlet (x = nx - 1) substitutions of the pulled values.
+template <class S>
+__device__ __forceinline__ void faces3(const Step3<S> &a, uint32_t x, typename Codec<S>::C *g) {
+    if (a.inlet && x == 0) {
+        if (a.inlet == 1) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[i] = a.heq_in[i];
+        } else {
+            zou_he3(a, g);
+        }
+    }
+    if (a.outlet && x == (uint32_t)a.g.nx - 1) zou_he_pressure3(a, g);
+}
 
 // Node stride of direction i's array in a layout: 1 (stream; one-direction
 // bundles), 3 (three-direction bundles), 19 (collision).
@@ -276,10 +356,7 @@ __global__ void __launch_bounds__(512, sizeof(S) == 8 ? 2 : 3) k3_step(const Ste
     if (!f) return;
     C g[Q];
     pull3<S, L, OFF32>(a, x, y, z, n, lk, g);
-    if (a.inlet && x == 0) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = a.heq_in[i];
-    }
+    faces3(a, x, g);
     finish3<S, L, OFF32>(a, n, g);
 }
 
@@ -400,6 +477,47 @@ __device__ __forceinline__ void publish3(S *hw, const Tile3 &T, int64_t t, const
     }
 }
 
+// Pulls of a fluid node off the box faces with the 32-bit offset tables:
+// every lane runs the interior pull (neighbour value, or the node's own
+// opposite value for a bounced link) and, for a direction whose source lies
+// in another tile, reads the source tile's publication of the previous
+// update instead (the face of the first axis along which the tiles differ).
+// Face nodes therefore run the same code as inner nodes plus a short
+// address computation per crossing direction.
+template <class S, int L>
+__device__ __forceinline__ void npol3_pull(const Step3<S> &a, const S *hr, const Tile3 &T, const int *b,
+                                           const int *nt, const int *tdim, const int *l, const int *p,
+                                           const int *lo, const int *hi, uint32_t n, uint32_t lk,
+                                           typename Codec<S>::C *g) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const S *base = a.src + mult3<L>(i) * n;
+        if (i == REST) {
+            g[i] = Codec<S>::dec(base[a.os[i]]);
+            continue;
+        }
+        const bool bounce = (lk >> bit(i)) & 1u;
+        const S *q = base + (bounce ? a.ob[i] : a.op[i]);
+        const int c[3] = {cx(i), cy(i), cz(i)};
+        bool cr[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cr[k] = (c[k] > 0 && p[k] == lo[k]) || (c[k] < 0 && p[k] == hi[k]);
+        if (!bounce && (cr[0] || cr[1] || cr[2])) {
+            int bs[3], ls[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                bs[k] = cr[k] ? b[k] - c[k] : b[k];
+                ls[k] = cr[k] ? (c[k] > 0 ? tdim[k] - 1 : 0) : l[k] - c[k];
+            }
+            const int ax = cr[0] ? 0 : (cr[1] ? 1 : 2);
+            const int64_t ts = ((int64_t)bs[2] * nt[1] + bs[1]) * nt[0] + bs[0];
+            q = hr + ts * T.per_tile() + T.face_off(ax, c[ax]) + (int64_t)face_rank(i, ax) * T.nodes(ax) +
+                T.pos(ax, ls[0], ls[1], ls[2]);
+        }
+        g[i] = Codec<S>::dec(*q);
+    }
+}
+
 // One lattice, pull: every node of the tile reads its 19 incoming values
 // (sources in the tile from the lattice, from other tiles out of the buffer
 // grid the previous update wrote), a block barrier separates all reads from
@@ -434,8 +552,12 @@ __global__ void __launch_bounds__(512, sizeof(S) == 8 ? 1 : 2) k3_npol(const Ste
     const int nt[3] = {(int)gridDim.x, (int)gridDim.y, (int)gridDim.z};
     const int64_t t = ((int64_t)b[2] * nt[1] + b[1]) * nt[0] + b[0];
     C g[Q];
+    const bool box_inner = p[0] > 0 && p[0] < ext[0] - 1 && p[1] > 0 && p[1] < ext[1] - 1 && p[2] > 0 &&
+                           p[2] < ext[2] - 1;
     if (fluid && inner) {
         pull3<S, L, OFF32>(a, (uint32_t)p[0], (uint32_t)p[1], (uint32_t)p[2], n, lk, g);
+    } else if (OFF32 && fluid && box_inner) {
+        npol3_pull<S, L>(a, hr, T, b, nt, tdim, l, p, lo, hi, n, lk, g);
     } else if (fluid) {
         // Per axis: does a pull with c = +1 (-1) leave the tile (the node is on
         // the tile's low (high) face)? Where the tile spans the whole axis, such
@@ -527,6 +649,168 @@ __global__ void __launch_bounds__(512, sizeof(S) == 8 ? 1 : 2) k3_npol(const Ste
     if (!inner) publish3(hw, T, t, p, lo, hi, l[0], l[1], l[2], e);
 }
 
+// ------------------------------------------------------------ NSOL (3-D)
+// One lattice, swap streaming (Sec. 3.3): the stored state holds population
+// i of every node in its slot opp(i). The tile's slots are staged in shared
+// memory; for each of the nine positive directions i (i > 9: c lexically
+// positive), slot opp(i) of node x is exchanged with slot i of x + c_i when
+// x + c_i is in the tile and no bounce separates them. After the exchanges
+// slot j of x holds the value x pulls in direction j (a bounced link keeps
+// the node's own value, i.e. bounce-back). Pulls from other tiles come from
+// the buffer grid, in the same format as NPOL's; pulls that wrap around a
+// periodic face inside one tile are read from the staged slots before the
+// exchange. Results are stored back into the opposite slots and face nodes
+// publish their outgoing values. Shared memory: 19 planes of the tile's
+// nodes (compute type).
+template <class S>
+size_t nsol3_smem_bytes(int tx, int ty, int tz) {
+    return sizeof(typename Codec<S>::C) * (size_t)Q * (size_t)tx * ty * tz;
+}
+
+template <class S, int L>
+__global__ void __launch_bounds__(512, sizeof(S) == 8 ? 1 : 2) k3_nsol(const Step3<S> a, const S *hr, S *hw) {
+    using C = typename Codec<S>::C;
+    using A = Ar<C>;
+    extern __shared__ __align__(16) unsigned char smem_nsol3[];
+    C *sm = reinterpret_cast<C *>(smem_nsol3);
+    const Tile3 T{a.tx, a.ty, a.tz};
+    const int TN = a.tx * a.ty * a.tz;
+    const int ext[3] = {a.g.nx, a.g.ny, a.g.nz};
+    const int b[3] = {(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z};
+    const int tdim[3] = {a.tx, a.ty, a.tz};
+    const int l[3] = {(int)threadIdx.x, (int)threadIdx.y, (int)threadIdx.z};
+    const int tid = (l[2] * a.ty + l[1]) * a.tx + l[0];
+    int lo[3], hi[3], p[3];
+    bool valid = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = b[k] * tdim[k];
+        hi[k] = min(lo[k] + tdim[k], ext[k]) - 1;
+        p[k] = lo[k] + l[k];
+        valid = valid && p[k] <= hi[k];
+    }
+    const uint32_t nx = (uint32_t)ext[0], ny = (uint32_t)ext[1];
+    S *lat = a.dst;
+    uint32_t n = 0, lk = SOLID;
+    if (valid) {
+        n = ((uint32_t)p[2] * ny + (uint32_t)p[1]) * nx + (uint32_t)p[0];
+        lk = a.links[n];
+    }
+    const bool fluid = lk != SOLID;
+    const bool inner = p[0] > lo[0] && p[0] < hi[0] && p[1] > lo[1] && p[1] < hi[1] && p[2] > lo[2] && p[2] < hi[2];
+    const int nt[3] = {(int)gridDim.x, (int)gridDim.y, (int)gridDim.z};
+    const int64_t t = ((int64_t)b[2] * nt[1] + b[1]) * nt[0] + b[0];
+    if (fluid) {
+#pragma unroll
+        for (int s = 0; s < Q; ++s) sm[s * TN + tid] = Codec<S>::dec(lat[addr<L>(a.N, n, s)]);
+    }
+    __syncthreads();
+    // Pulls the in-tile exchange does not cover: sources in another tile
+    // (buffer grid) or reached through a periodic face inside this tile.
+    C fix[Q];
+    uint32_t fixmask = 0;
+    if (fluid && !inner) {
+        bool lof[3], hif[3];
+        int tprev[3], tnext[3], lprev[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lof[k] = p[k] == lo[k];
+            hif[k] = p[k] == hi[k];
+            tprev[k] = b[k] == 0 ? nt[k] - 1 : b[k] - 1;
+            tnext[k] = b[k] == nt[k] - 1 ? 0 : b[k] + 1;
+            lprev[k] = min(tdim[k], ext[k] - tprev[k] * tdim[k]) - 1;
+        }
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            fix[j] = C(0);
+            if (j == REST || ((lk >> bit(j)) & 1u)) continue;
+            const int c[3] = {cx(j), cy(j), cz(j)};
+            bool cross = false, out = false;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (c[k] == 0) continue;
+                if (c[k] > 0 ? lof[k] : hif[k]) {
+                    cross = true;
+                    if (nt[k] > 1) out = true;
+                }
+            }
+            if (!cross) continue;   // adjacent in the tile: the exchange delivers it
+            fixmask |= 1u << j;
+            if (!out) {
+                // wraps around a periodic face of an axis the tile spans whole
+                int q[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    int sk = p[k] - c[k];
+                    sk = sk < 0 ? sk + ext[k] : (sk >= ext[k] ? sk - ext[k] : sk);
+                    q[k] = sk - lo[k];
+                }
+                fix[j] = sm[opp(j) * TN + (q[2] * a.ty + q[1]) * a.tx + q[0]];
+            } else {
+                int bs[3], ls[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const bool cr = c[k] != 0 && (c[k] > 0 ? lof[k] : hif[k]) && nt[k] > 1;
+                    if (!cr) {
+                        bs[k] = b[k];
+                        int sk = p[k] - c[k];
+                        sk = sk < 0 ? sk + ext[k] : (sk >= ext[k] ? sk - ext[k] : sk);
+                        ls[k] = sk - lo[k];
+                    } else {
+                        bs[k] = c[k] > 0 ? tprev[k] : tnext[k];
+                        ls[k] = c[k] > 0 ? lprev[k] : 0;
+                    }
+                }
+                const int ax = bs[0] != b[0] ? 0 : (bs[1] != b[1] ? 1 : 2);
+                const int64_t ts = ((int64_t)bs[2] * nt[1] + bs[1]) * nt[0] + bs[0];
+                const int64_t slot = ts * T.per_tile() + T.face_off(ax, c[ax]) +
+                                     (int64_t)face_rank(j, ax) * T.nodes(ax) + T.pos(ax, ls[0], ls[1], ls[2]);
+                fix[j] = Codec<S>::dec(hr[slot]);
+            }
+        }
+    }
+    __syncthreads();
+    if (fluid) {
+#pragma unroll
+        for (int i = REST + 1; i < Q; ++i) {
+            if ((lk >> bit(opp(i))) & 1u) continue;   // bounced: no exchange
+            const int c[3] = {cx(i), cy(i), cz(i)};
+            bool in = true;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) in = in && p[k] + c[k] >= lo[k] && p[k] + c[k] <= hi[k];
+            if (!in) continue;
+            const int pt = tid + (c[2] * a.ty + c[1]) * a.tx + c[0];
+            const C v = sm[opp(i) * TN + tid];
+            sm[opp(i) * TN + tid] = sm[i * TN + pt];
+            sm[i * TN + pt] = v;
+        }
+    }
+    __syncthreads();
+    if (!fluid) return;
+    C g[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) g[j] = ((fixmask >> j) & 1u) ? fix[j] : sm[j * TN + tid];
+    C drho, ux, uy, uz;
+    collide3(a.k, g, drho, ux, uy, uz);
+    if (!isfinite(drho)) atomicOr(a.err, 1u);
+    if (a.mom) {
+        a.mom[n] = A::add(C(1), drho);
+        a.mom[a.N + n] = ux;
+        a.mom[2 * (size_t)a.N + n] = uy;
+        a.mom[3 * (size_t)a.N + n] = uz;
+    }
+    const bool sr = Codec<S>::narrow && a.sr;
+    uint32_t nk = 0;
+    if (sr) nk = node_key(step_key(a.seed, (uint32_t)(*a.tctr + a.toff)), n);
+    S e[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        e[i] = Codec<S>::enc(g[i], sr, sr ? pop_rand(nk, i) : 0u);
+        lat[addr<L>(a.N, n, opp(i))] = e[i];
+    }
+    if (!inner) publish3(hw, T, t, p, lo, hi, l[0], l[1], l[2], e);
+}
+
 // Fill a buffer-grid parity from the stored state (after init or a write).
 template <class S, int L>
 __global__ void k3_publish(const Step3<S> a, S *hw) {
@@ -549,7 +833,7 @@ __global__ void k3_publish(const Step3<S> a, S *hw) {
     const int64_t t = ((int64_t)b[2] * nty + b[1]) * ntx + b[0];
     S e[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) e[i] = a.dst[addr<L>(a.N, n, i)];
+    for (int i = 0; i < Q; ++i) e[i] = a.dst[addr<L>(a.N, n, slot3(a, i))];
     publish3(hw, T, t, p, lo, hi, l[0], l[1], l[2], e);
 }
 
@@ -568,7 +852,7 @@ __global__ void k3_init(const Step3<S> a, const double *rho, const double *ux, c
         const double w = sq(i) == 0 ? 1.0 / 3.0 : (sq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
         const double cu = cx(i) * v[0] + cy(i) * v[1] + cz(i) * v[2];
         const double h = w * (dr + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-        a.dst[addr<L>(a.N, n, i)] = Codec<S>::enc((typename Codec<S>::C)h, false, 0u);
+        a.dst[addr<L>(a.N, n, slot3(a, i))] = Codec<S>::enc((typename Codec<S>::C)h, false, 0u);
     }
 }
 
@@ -590,7 +874,7 @@ __global__ void k3_state_moments(const Step3<S> a) {
     C r = C(0), j[3] = {C(0), C(0), C(0)};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const C h = Codec<S>::dec(a.src[addr<L>(a.N, n, i)]);
+        const C h = Codec<S>::dec(a.src[addr<L>(a.N, n, slot3(a, i))]);
         r = A::add(r, h);
         if (cx(i)) j[0] = cx(i) > 0 ? A::add(j[0], h) : A::sub(j[0], h);
         if (cy(i)) j[1] = cy(i) > 0 ? A::add(j[1], h) : A::sub(j[1], h);
@@ -612,7 +896,7 @@ __global__ void __launch_bounds__(kReduceThreads) k3_mass(const Step3<S> a, doub
         if (a.links[n] == SOLID) continue;
         double r = 1.0;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) r += (double)Codec<S>::dec(a.src[addr<L>(a.N, n, i)]);
+        for (int i = 0; i < Q; ++i) r += (double)Codec<S>::dec(a.src[addr<L>(a.N, n, slot3(a, i))]);
         acc += r;
     }
     red[threadIdx.x] = acc;
@@ -664,7 +948,7 @@ __global__ void __launch_bounds__(kReduceThreads) k3_force(const Step3<S> a, con
             const bool hit = body ? body[m] != 0 : a.links[m] == SOLID;
             if (!hit) continue;
             const double w = sq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0;
-            const double f = w + (double)Codec<S>::dec(a.src[addr<L>(a.N, n, i)]);
+            const double f = w + (double)Codec<S>::dec(a.src[addr<L>(a.N, n, slot3(a, i))]);
 #pragma unroll
             for (int k = 0; k < 3; ++k) acc[k] += 2.0 * c[k] * f;
         }
@@ -723,8 +1007,10 @@ size_t comp_of(int storage) { return storage == LBM_F64 ? 8 : 4; }
 
 bool offsets_fit(const lbm3_params *p, int64_t N);
 
+bool inlet_kind(int bc) { return bc == LBM_BC_INLET_EQ || bc == LBM_BC_INLET_ZOUHE; }
+
 // Kind of the east x face: bc_x_east after an inlet west face, else bc_x.
-int east_kind(const lbm3_params *p) { return p->bc_x == LBM_BC_INLET_EQ ? p->bc_x_east : p->bc_x; }
+int east_kind(const lbm3_params *p) { return inlet_kind(p->bc_x) ? p->bc_x_east : p->bc_x; }
 
 lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
     if (!p) return lbm_fail(LBM_EINVAL, "params is NULL");
@@ -738,24 +1024,28 @@ lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
     for (int a = 1; a < 3; ++a)
         if (bc[a] != LBM_BC_PERIODIC && bc[a] != LBM_BC_WALL)
             return lbm_fail(LBM_EINVAL, "D3Q19 y and z faces are PERIODIC or WALL");
-    if (p->bc_x != LBM_BC_PERIODIC && p->bc_x != LBM_BC_WALL && p->bc_x != LBM_BC_INLET_EQ &&
+    if (p->bc_x != LBM_BC_PERIODIC && p->bc_x != LBM_BC_WALL && !inlet_kind(p->bc_x) &&
         p->bc_x != LBM_BC_OUTFLOW_ZG)
-        return lbm_fail(LBM_EINVAL, "D3Q19 x faces: PERIODIC, WALL, INLET_EQ (west) or OUTFLOW_ZG");
-    if (p->bc_x == LBM_BC_INLET_EQ && p->bc_x_east != LBM_BC_WALL && p->bc_x_east != LBM_BC_OUTFLOW_ZG)
-        return lbm_fail(LBM_EINVAL, "D3Q19 inlet: the east face (bc_x_east) is WALL or OUTFLOW_ZG");
-    const bool open_x = p->bc_x == LBM_BC_INLET_EQ || p->bc_x == LBM_BC_OUTFLOW_ZG;
-    if (open_x && (p->algo == LBM_AA || p->algo == LBM_NPOL))
-        return lbm_fail(LBM_EUNSUPPORTED, "D3Q19 inlet/outflow faces: LPTL or NPTL only");
+        return lbm_fail(LBM_EINVAL, "D3Q19 x faces: PERIODIC, WALL, INLET_EQ or INLET_ZOUHE (west) or OUTFLOW_ZG");
+    if (inlet_kind(p->bc_x) && p->bc_x_east != LBM_BC_WALL && p->bc_x_east != LBM_BC_OUTFLOW_ZG &&
+        p->bc_x_east != LBM_BC_OUTLET_PRESSURE)
+        return lbm_fail(LBM_EINVAL, "D3Q19 inlet: the east face (bc_x_east) is WALL, OUTFLOW_ZG or OUTLET_PRESSURE");
+    if (inlet_kind(p->bc_x) && p->bc_x_east == LBM_BC_OUTLET_PRESSURE && !(p->rho_out > 0.0 && std::isfinite(p->rho_out)))
+        return lbm_fail(LBM_EINVAL, "D3Q19 pressure outlet: rho_out must be finite and > 0");
+    const bool open_x = inlet_kind(p->bc_x) || p->bc_x == LBM_BC_OUTFLOW_ZG;
+    if (open_x && (p->algo == LBM_AA || p->algo == LBM_NPOL || p->algo == LBM_NSOL))
+        return lbm_fail(LBM_EUNSUPPORTED, "D3Q19 inlet/outlet faces: LPTL or NPTL only");
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(p->u_in[a])) return lbm_fail(LBM_EINVAL, "u_in must be finite");
     if (p->layout < 0 || p->layout > 2) return lbm_fail(LBM_EINVAL, "bad layout");
-    if (p->algo != LBM_LPTL && p->algo != LBM_NPTL && p->algo != LBM_AA && p->algo != LBM_NPOL)
-        return lbm_fail(LBM_EUNSUPPORTED, "D3Q19: LPTL, NPTL, NPOL or AA");
+    if (p->algo != LBM_LPTL && p->algo != LBM_NPTL && p->algo != LBM_AA && p->algo != LBM_NPOL &&
+        p->algo != LBM_NSOL)
+        return lbm_fail(LBM_EUNSUPPORTED, "D3Q19: LPTL, NPTL, NPOL, NSOL or AA");
     if (p->storage < 0 || p->storage > 3) return lbm_fail(LBM_EINVAL, "bad storage");
     if (p->rounding < 0 || p->rounding > 1) return lbm_fail(LBM_EINVAL, "bad rounding");
     *pl = Plan3();
     pl->N = (int64_t)N;
-    if (p->algo == LBM_NPTL || p->algo == LBM_AA || p->algo == LBM_NPOL) {
+    if (p->algo == LBM_NPTL || p->algo == LBM_AA || p->algo == LBM_NPOL || p->algo == LBM_NSOL) {
         int tx = p->tile_x, ty = p->tile_y, tz = p->tile_z;
         if (tx == 0 && ty == 0 && tz == 0) { tx = 128; ty = 1; tz = 1; }
         if (tx < 1 || ty < 1 || tz < 1 || tz > 64 || (int64_t)tx * ty * tz > 512)
@@ -771,11 +1061,11 @@ lbm_status plan3(const lbm3_params *p, Plan3 *pl) {
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off = (off + b + 255) / 256 * 256; return o; };
     pl->pop[0] = take(19 * (size_t)N * pl->elem);
-    pl->one = (p->algo == LBM_AA || p->algo == LBM_NPOL) ? 1 : 0;
+    pl->one = (p->algo == LBM_AA || p->algo == LBM_NPOL || p->algo == LBM_NSOL) ? 1 : 0;
     if (p->algo == LBM_AA && (!offsets_fit(p, (int64_t)N) || (p->flags & LBM_FLAG_WIDE_OFFSETS)))
         return lbm_fail(LBM_EUNSUPPORTED, "D3Q19 AA needs 32-bit offset tables (19 N well below 2^31)");
     pl->pop[1] = pl->one ? pl->pop[0] : take(19 * (size_t)N * pl->elem);
-    if (p->algo == LBM_NPOL) {
+    if (p->algo == LBM_NPOL || p->algo == LBM_NSOL) {
         pl->halo_parity = (int64_t)pl->ntx * pl->nty * pl->ntz * Tile3{pl->tx, pl->ty, pl->tz}.per_tile();
         pl->halo = take(2 * (size_t)pl->halo_parity * pl->elem);
     }
@@ -838,7 +1128,20 @@ static Step3<S> make3(const lbm3_lattice *L, int src, int toff, int mom) {
     a.g = Geo3{p.nx, p.ny, p.nz, p.bc_x, p.bc_y, p.bc_z, east_kind(&p)};
     a.xlo_corr = p.bc_x == LBM_BC_PERIODIC ? p.nx : (p.bc_x == LBM_BC_OUTFLOW_ZG ? 1 : 0);
     a.xhi_corr = a.g.bxe == LBM_BC_PERIODIC ? -p.nx : (a.g.bxe == LBM_BC_OUTFLOW_ZG ? -1 : 0);
-    a.inlet = p.bc_x == LBM_BC_INLET_EQ ? 1 : 0;
+    a.inlet = p.bc_x == LBM_BC_INLET_EQ ? 1 : (p.bc_x == LBM_BC_INLET_ZOUHE ? 2 : 0);
+    a.outlet = (inlet_kind(p.bc_x) && p.bc_x_east == LBM_BC_OUTLET_PRESSURE) ? 1 : 0;
+    a.rev = p.algo == LBM_NSOL ? 1 : 0;
+    {
+        const double U[3] = {p.u_in[0], p.u_in[1], p.u_in[2]};
+        a.zh[0] = (C)(U[0] / 3.0);
+        a.zh[1] = (C)((U[0] + U[1]) / 6.0);
+        a.zh[2] = (C)((U[0] - U[1]) / 6.0);
+        a.zh[3] = (C)((U[0] + U[2]) / 6.0);
+        a.zh[4] = (C)((U[0] - U[2]) / 6.0);
+        a.zh[5] = (C)(-U[1] / 3.0);
+        a.zh[6] = (C)(-U[2] / 3.0);
+        a.zh[7] = (C)(p.rho_out - 1.0);
+    }
     {
         const double usq = p.u_in[0] * p.u_in[0] + p.u_in[1] * p.u_in[1] + p.u_in[2] * p.u_in[2];
         for (int i = 0; i < Q; ++i) {
@@ -944,6 +1247,33 @@ static void launch_npol(const lbm3_lattice *L, const Step3<S> &a, int parity, cu
     else k3_npol<S, COLLISION, OFF32><<<g, b, 0, st>>>(a, hr, hw);
 }
 
+template <class S>
+static void launch_nsol(const lbm3_lattice *L, const Step3<S> &a, int parity, cudaStream_t st) {
+    const dim3 g(L->pl.ntx, L->pl.nty, L->pl.ntz), b(L->pl.tx, L->pl.ty, L->pl.tz);
+    const size_t sm = nsol3_smem_bytes<S>(L->pl.tx, L->pl.ty, L->pl.tz);
+    const S *hr = halo_parity<S>(L, parity);
+    S *hw = halo_parity<S>(L, parity ^ 1);
+    const int lay = L->p.layout;
+    if (lay == LBM_LAYOUT_STREAM) k3_nsol<S, STREAM><<<g, b, sm, st>>>(a, hr, hw);
+    else if (lay == LBM_LAYOUT_BUNDLE) k3_nsol<S, BUNDLE><<<g, b, sm, st>>>(a, hr, hw);
+    else k3_nsol<S, COLLISION><<<g, b, sm, st>>>(a, hr, hw);
+}
+
+// Largest staged tile of the 3-D NSOL kernel (512 nodes) beyond the default
+// 48 KB of dynamic shared memory (FP64: 76 KB).
+template <class S>
+static void nsol3_prepare() {
+    static const bool done = [] {
+        const int bytes = (int)nsol3_smem_bytes<S>(512, 1, 1);
+        cudaFuncSetAttribute(k3_nsol<S, STREAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(k3_nsol<S, BUNDLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(k3_nsol<S, COLLISION>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaGetLastError();
+        return true;
+    }();
+    (void)done;
+}
+
 // NPOL: fill buffer-grid parity `parity` from the stored state.
 template <class S>
 static cudaError_t publish_state(const lbm3_lattice *L, int parity, cudaStream_t st) {
@@ -965,6 +1295,8 @@ static cudaError_t step3(const lbm3_lattice *L, cudaStream_t st, int src, int to
     if (L->p.algo == LBM_NPOL) {
         if (L->off32) launch_npol<S, true>(L, a, src, st);
         else launch_npol<S, false>(L, a, src, st);
+    } else if (L->p.algo == LBM_NSOL) {
+        launch_nsol<S>(L, a, src, st);
     } else if (L->p.algo == LBM_AA) {
         if (src == 0) launch_aa<S, 0>(L, a, st);
         else launch_aa<S, 1>(L, a, st);
@@ -1095,6 +1427,7 @@ extern "C" lbm_status lbm3_create(const lbm3_params *p, const uint8_t *mask_host
     L->ws = (char *)d_workspace;
     L->stream = (cudaStream_t)cuda_stream;
     LBM3_DISPATCH(L, L->block_1d = block_of<S>(p->layout));
+    if (p->algo == LBM_NSOL) LBM3_DISPATCH(L, nsol3_prepare<S>());
     L->off32 = (offsets_fit(p, pl.N) && !(p->flags & LBM_FLAG_WIDE_OFFSETS)) ? 1 : 0;
     cudaError_t e = cudaStreamCreateWithFlags(&L->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -1247,7 +1580,8 @@ extern "C" lbm_status lbm3_read_populations(lbm3_lattice *L, void *host, int32_t
     CK3(cudaMemcpy(raw.data(), L->ws + L->pl.pop[L->cur], raw.size(), cudaMemcpyDeviceToHost));
     for (int i = 0; i < 19; ++i)
         for (int64_t n = 0; n < N; ++n) {
-            const double v = get_raw(raw.data(), L->p.storage, lbm3_layout_index(L->p.layout, N, n, i));
+            const double v = get_raw(raw.data(), L->p.storage,
+                                     lbm3_layout_index(L->p.layout, N, n, L->p.algo == LBM_NSOL ? 18 - i : i));
             if (as == LBM_F64) ((double *)host)[(int64_t)i * N + n] = v;
             else ((float *)host)[(int64_t)i * N + n] = (float)v;
         }
@@ -1264,7 +1598,8 @@ extern "C" lbm_status lbm3_write_populations(lbm3_lattice *L, const void *host, 
         for (int64_t n = 0; n < N; ++n) {
             const double v = as == LBM_F64 ? ((const double *)host)[(int64_t)i * N + n]
                                            : (double)((const float *)host)[(int64_t)i * N + n];
-            set_raw(raw.data(), L->p.storage, lbm3_layout_index(L->p.layout, N, n, i), v);
+            set_raw(raw.data(), L->p.storage, lbm3_layout_index(L->p.layout, N, n, L->p.algo == LBM_NSOL ? 18 - i : i),
+                    v);
         }
     CK3(cudaStreamSynchronize(L->stream));
     CK3(cudaMemcpy(L->ws + L->pl.pop[L->cur], raw.data(), raw.size(), cudaMemcpyHostToDevice));
@@ -1320,7 +1655,7 @@ extern "C" lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out) {
     out->tile_x = L->p.algo == LBM_LPTL ? L->block_1d : L->pl.tx;
     out->tile_y = L->p.algo == LBM_LPTL ? 1 : L->pl.ty * L->pl.tz;
     out->bytes_per_update = (double)L->fluid * 38.0 * (double)L->pl.elem + 4.0 * (double)L->pl.N;
-    if (L->pl.halo_parity)   // NPOL buffer grid: one parity read, the other written
+    if (L->pl.halo_parity)   // NPOL/NSOL buffer grid: one parity read, the other written
         out->bytes_per_update += 2.0 * (double)L->pl.halo_parity * (double)L->pl.elem;
     out->workspace_bytes = L->pl.total;
     out->aux = L->off32 ? 0 : 1;   // 1: the 64-bit addressing path

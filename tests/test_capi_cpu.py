@@ -163,8 +163,13 @@ def test_d3q19_layout_maps_are_bijections_grouped_by_source_row(lib):
 def test_d3q19_params_checked_without_gpu(lib):
     ok = lbm.lbm3_workspace_bytes(lbm.make_params3(16, 8, 4, 0.8, storage="f32"))
     assert ok >= 2 * 19 * 16 * 8 * 4 * 4
+    assert lbm.lbm3_workspace_bytes(lbm.make_params3(16, 8, 4, 0.8, algo="nsol", tile=(8, 4, 2))) >= \
+        19 * 16 * 8 * 4 * 4
+    zh = (lbm.INLET_ZOUHE, lbm.WALL, lbm.PERIODIC)
     for bad in (dict(tau=0.5), dict(bc=(lbm.FREESLIP, lbm.PERIODIC, lbm.PERIODIC)),
-                dict(algo="nsol"), dict(tile=(32, 8, 4))):
+                dict(algo="nsol", bc=zh, bc_x_east=lbm.OUTLET_PRESSURE), dict(tile=(32, 8, 4)),
+                dict(bc=zh, bc_x_east=lbm.OUTLET_PRESSURE, rho_out=-1.0),
+                dict(bc=zh, bc_x_east=lbm.INLET_ZOUHE)):
         kw = dict(tau=0.8)
         kw.update(bad)
         tau = kw.pop("tau")

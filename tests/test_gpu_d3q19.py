@@ -82,13 +82,15 @@ SPECS = specs()
 
 @pytest.mark.parametrize("case", list(SPECS))
 @pytest.mark.parametrize("layout", LAYOUTS)
-@pytest.mark.parametrize("algo", ALGOS + ("nptl_wide", "npol", "npol_wide"))
+@pytest.mark.parametrize("algo", ALGOS + ("nptl_wide", "npol", "npol_wide", "nsol", "nsol_spanx"))
 def test_fp64_matches_oracle3(case, layout, algo):
     spec = SPECS[case]
     T = 40
     ref = spec.oracle().run(T)
     flags = lbm.LBM_FLAG_WIDE_OFFSETS if algo.endswith("_wide") else 0
-    tile = (8, 4, 3) if algo.startswith("npol") else (0, 0, 0)
+    # nsol_spanx: one tile spans the whole x axis (64 >= nx), so periodic x
+    # pulls wrap inside the tile
+    tile = (64, 2, 3) if algo == "nsol_spanx" else ((8, 4, 3) if algo.startswith(("npol", "nsol")) else (0, 0, 0))
     lat = spec.gpu(layout=layout, algo=algo.split("_")[0], storage="f64", flags=flags, tile=tile)
     lat.step(T, moments=True).sync()
     h = lat.populations("f64")
@@ -115,7 +117,9 @@ def test_all_layouts_algorithms_and_tiles_bit_identical(storage, rounding):
         for algo, tile, flags in (("lptl", (0, 0, 0), 0), ("nptl", (32, 4, 2), 0), ("nptl", (8, 8, 8), 0),
                                   ("nptl", (16, 2, 1), 0), ("lptl", (0, 0, 0), lbm.LBM_FLAG_WIDE_OFFSETS),
                                   ("nptl", (128, 1, 1), lbm.LBM_FLAG_WIDE_OFFSETS),
-                                  ("npol", (8, 4, 2), 0), ("npol", (16, 2, 3), 0), ("npol", (64, 1, 1), 0)):
+                                  ("npol", (8, 4, 2), 0), ("npol", (16, 2, 3), 0), ("npol", (64, 1, 1), 0),
+                                  ("nsol", (8, 4, 2), 0), ("nsol", (16, 2, 3), 0), ("nsol", (64, 1, 1), 0),
+                                  ("nsol", (4, 21, 2), 0)):
             lat = spec.gpu(layout=layout, algo=algo, tile=tile, storage=storage, rounding=rounding,
                            seed=99, flags=flags)
             lat.step(T, moments=True).sync()
@@ -129,7 +133,7 @@ def test_all_layouts_algorithms_and_tiles_bit_identical(storage, rounding):
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
-@pytest.mark.parametrize("algo", ALGOS + ("npol",))
+@pytest.mark.parametrize("algo", ALGOS + ("npol", "nsol"))
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_pure_streaming_is_bit_exact_shift3(layout, algo, storage):
     nx, ny, nz, T = 23, 9, 7, 5
@@ -652,4 +656,104 @@ def test_outflow_on_both_x_faces_matches_oracle3():
                        storage="f64", tile=(8, 4, 2))
     lat.init(None, ux, None, None).step(T).sync()
     assert rel_linf(lat.populations("f64"), ref.h) <= 1e-12
+    lat.close()
+
+
+# ---------------------------------------------------------------- Zou-He faces
+
+def _zou_he3(**kw):
+    """Channel 42 x 14 x 10 with a ball: Zou-He velocity inlet
+    U = (0.04, 0.003, -0.002) (west), Zou-He pressure outlet rho = 0.999
+    (east), walls on y and z, perturbed initial velocity."""
+    nx, ny, nz = 42, 14, 10
+    N = nx * ny * nz
+    mask = G.ball(nx, ny, nz, 13.0, 7.0, 5.0, 3.0).ravel()
+    r = G.SplitMix64(47, 1)
+    ux = np.where(mask > 0, 0.0, 0.04)
+    uy = np.where(mask > 0, 0.0, r.uniform(N, -1e-3, 1e-3))
+    uz = np.where(mask > 0, 0.0, r.uniform(N, -1e-3, 1e-3))
+    U, rho_out = (0.04, 0.003, -0.002), 0.999
+    case = O.Case3(nx, ny, nz, 0.7, bc_x=lbm.INLET_ZOUHE, bc_xe=lbm.OUTLET_PRESSURE, bc_y=W, bc_z=W,
+                   u_in=U, rho_out=rho_out)
+    ref = O.Lattice3(case, mask, None, ux, uy, uz)
+    lat = lbm.Lattice3(nx, ny, nz, 0.7, mask, bc=(lbm.INLET_ZOUHE, W, W), bc_x_east=lbm.OUTLET_PRESSURE,
+                       u_in=U, rho_out=rho_out, **kw)
+    lat.init(None, ux, uy, uz)
+    return ref, lat, mask
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("algo", ["lptl", "nptl", "nptl_wide"])
+def test_zou_he_channel_fp64_matches_oracle3(layout, algo):
+    T = 60
+    flags = lbm.LBM_FLAG_WIDE_OFFSETS if algo.endswith("_wide") else 0
+    ref, lat, mask = _zou_he3(layout=layout, algo=algo.split("_")[0], storage="f64", flags=flags,
+                              tile=(16, 4, 2))
+    ref.run(T)
+    lat.step(T, moments=True).sync()
+    fl = ref.solid == 0
+    assert rel_linf(lat.populations("f64"), ref.h, fl) <= 1e-12
+    rho, ux, uy, uz = lat.moments()
+    assert rel_linf(rho, ref.rho, fl) <= 1e-14
+    assert rel_linf(np.stack([ux, uy, uz]), np.stack([ref.ux, ref.uy, ref.uz]), fl) <= 1e-12
+    x = np.arange(lat.N) % 42
+    # the faces' defining conditions hold on the GPU too
+    assert np.max(np.abs(ux[(x == 0) & fl] - 0.04)) < 1e-15
+    assert np.max(np.abs(rho[(x == 41) & fl] - 0.999)) < 1e-15
+    body = torch.from_numpy(mask.astype(np.uint8)).cuda()
+    f_gpu, f_ref = lat.force(body), ref.force(mask)
+    assert np.max(np.abs(f_gpu - f_ref)) <= 1e-11 * np.max(np.abs(f_ref))
+    lat.close()
+
+
+@pytest.mark.parametrize("storage,rounding", [("f32", "rne"), ("f16s", "sr"), ("bf16s", "rne")])
+def test_zou_he_channel_bit_identical3(storage, rounding):
+    base = None
+    for layout in LAYOUTS:
+        for algo, tile in (("lptl", (0, 0, 0)), ("nptl", (16, 4, 2)), ("nptl", (128, 1, 1))):
+            _, lat, _ = _zou_he3(layout=layout, algo=algo, tile=tile, storage=storage, rounding=rounding,
+                                 seed=5)
+            lat.step(70, moments=True).sync()
+            got = (lat.populations("f64"), *lat.moments())
+            lat.close()
+            if base is None:
+                base = got
+            else:
+                assert all(np.array_equal(a, b) for a, b in zip(got, base)), (layout, algo, tile)
+
+
+def test_zou_he_channel_fp32_close_to_oracle3():
+    ref, lat, _ = _zou_he3(layout="bundle", algo="nptl", storage="f32")
+    ref.run(200)
+    lat.step(200, moments=True).sync()
+    fl = ref.solid == 0
+    rho, ux, uy, uz = lat.moments()
+    assert rel_linf(rho, ref.rho, fl) <= 1e-5
+    assert rel_linf(np.stack([ux, uy, uz]), np.stack([ref.ux, ref.uy, ref.uz]), fl) <= 1e-5
+    lat.close()
+
+
+def test_open_faces_rejected_for_one_lattice_algorithms3():
+    for algo in ("npol", "nsol", "aa"):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm3_workspace_bytes(lbm.make_params3(16, 8, 8, 0.8, bc=(lbm.INLET_ZOUHE, W, W), algo=algo,
+                                                      bc_x_east=lbm.OUTLET_PRESSURE))
+        assert e.value.status == lbm.LBM_EUNSUPPORTED
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm3_workspace_bytes(lbm.make_params3(16, 8, 8, 0.8, bc=(lbm.INLET_ZOUHE, W, W),
+                                                  bc_x_east=lbm.OUTLET_PRESSURE, rho_out=0.0))
+    assert e.value.status == lbm.LBM_EINVAL
+
+
+def test_nsol_mass_and_force_match_oracle3():
+    spec = SPECS["duct"]
+    T = 30
+    ref = spec.oracle().run(T)
+    lat = spec.gpu(layout="bundle", algo="nsol", storage="f64", tile=(8, 4, 3))
+    lat.step(T).sync()
+    fl = ref.solid == 0
+    assert abs(lat.mass() - ref.mass()) <= 1e-13 * ref.mass()
+    body = torch.from_numpy(spec.mask.astype(np.uint8)).cuda()
+    f_gpu, f_ref = lat.force(body), ref.force(spec.mask)
+    assert np.max(np.abs(f_gpu - f_ref)) <= 1e-11 * np.max(np.abs(f_ref))
     lat.close()
