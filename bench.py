@@ -60,8 +60,10 @@ def parse():
     ap.add_argument("--tile", default="")
     ap.add_argument("--layout", default="bundle", choices=["stream", "bundle", "collision"])
     ap.add_argument("--algo", default="nptl", choices=["lptl", "nptl", "npol", "nsol", "aa"],
-                    help="D3Q19 (--lattice d3q19): lptl, nptl, npol or aa")
+                    help="D3Q19 (--lattice d3q19): lptl, nptl, npol, nsol or aa")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s", "f64"])
+    ap.add_argument("--rounding", default="rne", choices=["rne", "sr"])
+    ap.add_argument("--flags", type=lambda v: int(v, 0), default=0, help="lbm_params.flags (LBM_FLAG_*)")
     ap.add_argument("--lattice", default="d2q9", choices=["d2q9", "d3q19"],
                     help="d3q19: time only the 3-D extension on an n3^3 sphere packing")
     ap.add_argument("--n3", type=int, default=384)
@@ -175,9 +177,13 @@ def kernel_name(args, tile=(32, 4)) -> str:
     bundle 1, collision 2)."""
     t = {"f32": "float", "f64": "double", "f16s": "__half", "bf16s": "__nv_bfloat16"}[args.storage]
     lay = {"stream": 0, "bundle": 1, "collision": 2}[args.layout]
+    pairs = (args.storage in ("f16s", "bf16s") and args.layout == "bundle" and args.nx % 2 == 0
+             and not (getattr(args, "flags", 0) & 0x20))
     if args.algo == "lptl":
-        return f"k_two_lattice<{t}, {lay}, true>"
+        return f"k_two_lattice_pair<{t}, {lay}, true>" if pairs else f"k_two_lattice<{t}, {lay}, true>"
     if args.algo == "nptl":
+        if pairs and tile[0] % 2 == 0:
+            return f"k_two_lattice_pair<{t}, {lay}, false>"
         if args.layout == "collision" and tile[0] % 32 == 0:
             return f"k_two_lattice_aos<{t}>"
         return f"k_two_lattice<{t}, {lay}, false>"
@@ -329,7 +335,7 @@ def run_ours(args):
     tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else (32, 4)
     mask = G.porous_discs(nx, ny, seed=3)
     kw = dict(force=(1e-6, 0.0), bc=(lbm.PERIODIC,) * 4, layout=args.layout, algo=args.algo,
-              storage=args.storage, tile=tile)
+              storage=args.storage, rounding=args.rounding, seed=7, tile=tile, flags=args.flags)
     stream = torch.cuda.Stream()
     lat = lbm.Lattice(nx, ny, 0.9, mask, stream=stream, **kw)
     info = lat.info()
@@ -410,9 +416,11 @@ def variants(args, mask, torch, world):
                      ("f32_stream_npol_32x8", dict(storage="f32", algo="npol", tile=(32, 8))),
                      ("f32_stream_nsol_32x8", dict(storage="f32", algo="nsol", tile=(32, 8))),
                      ("f32_bundle_aa_128x1", dict(storage="f32", algo="aa", layout="bundle", tile=(128, 1))),
-                     ("f16s_rne_bundle_nptl_64x4", dict(storage="f16s", layout="bundle", tile=(64, 4))),
-                     ("bf16s_rne_bundle_nptl_64x4", dict(storage="bf16s", layout="bundle", tile=(64, 4))),
-                     ("f16s_sr_bundle_nptl_64x4", dict(storage="f16s", layout="bundle", tile=(64, 4),
+                     ("f16s_rne_bundle_nptl_32x8", dict(storage="f16s", layout="bundle", tile=(32, 8))),
+                     ("f16s_rne_bundle_nptl_32x8_one_node_per_thread",
+                      dict(storage="f16s", layout="bundle", tile=(32, 8), flags=0x20)),
+                     ("bf16s_rne_bundle_nptl_32x8", dict(storage="bf16s", layout="bundle", tile=(32, 8))),
+                     ("f16s_sr_bundle_nptl_32x8", dict(storage="f16s", layout="bundle", tile=(32, 8),
                                                        rounding="sr", seed=7)),
                      ("f16s_rne_stream_npol_32x8", dict(storage="f16s", algo="npol", tile=(32, 8))),
                      ("bf16s_rne_stream_npol_32x8", dict(storage="bf16s", algo="npol", tile=(32, 8)))]:
@@ -503,7 +511,11 @@ def d3q19(args, torch):
                           ("f16s_rne_bundle_nptl_128x1x1_porous", "porous", dict(storage="f16s", layout="bundle")),
                           ("f32_bundle_aa_128x1x1_porous", "porous", dict(storage="f32", layout="bundle", algo="aa")),
                           ("f32_stream_npol_32x8x2_porous", "porous", dict(storage="f32", layout="stream", algo="npol",
-                                                                          tile=(32, 8, 2)))]:
+                                                                          tile=(32, 8, 2))),
+                          ("f32_bundle_nsol_32x4x4_porous", "porous", dict(storage="f32", layout="bundle", algo="nsol",
+                                                                          tile=(32, 4, 4))),
+                          ("f32_stream_nsol_32x4x4_porous", "porous", dict(storage="f32", layout="stream", algo="nsol",
+                                                                          tile=(32, 4, 4)))]:
         m = porous if geo == "porous" else np.zeros_like(porous)
         stream = torch.cuda.Stream()
         kw = dict(kw)
