@@ -71,35 +71,43 @@ __host__ __device__ __forceinline__ uint32_t step_key(uint64_t seed, uint32_t t)
 __host__ __device__ __forceinline__ uint32_t node_key(uint32_t skey, uint32_t n) {
     return mix32(n ^ skey);
 }
+// Random word of population i of a node: the node's hashed key with a
+// per-direction constant folded in, multiplied by an odd constant (a
+// multiplicative hash); the stochastic rounding below uses its top bits.
 __host__ __device__ __forceinline__ uint32_t pop_rand(uint32_t nkey, int i) {
-    return mix32(nkey + (uint32_t)i * 0x9E3779B9U);
+    return (nkey ^ ((uint32_t)i * 0x9E3779B9U)) * 0x85EBCA6BU;
 }
 
 // ------------------------------------------------------------ codecs
-// Stochastic rounding: with lo the value rounded toward zero and ulp the gap
-// to the next magnitude, round away from zero iff u * ulp < |x| - |lo| for
-// u = (r >> 8) * 2^-24. Every product and difference here is exact.
+// Stochastic rounding of an FP32 value x to 16 bits: away from zero with
+// probability (|x| - |lo|) / ulp, lo the value rounded toward zero and ulp
+// the gap to the next magnitude. The 16-bit value keeps the top of x's bit
+// pattern and drops its low d bits, where ulp = 2^d FP32 ulps at x: BF16
+// d = 16; FP16 d = 13 in its normal range (|x| >= 2^-14) and d = 126 - the
+// FP32 exponent field (14 ... 23) below it, down to |x| = 2^-24. A uniform
+// random integer below 2^d (the top d bits of r) is added to the pattern and
+// the low d bits of the sum cleared: the kept part increments exactly when
+// the dropped bits plus the draw carry, i.e. with that probability (a carry
+// out of the mantissa gives the next power of two, which both formats hold). Below
+// 2^-24 the FP16 value is 0 or 2^-24: away iff (r >> 8) 2^-48 < |x|, exact in
+// FP32. Non-finite and out-of-range values round to nearest.
 __device__ __forceinline__ __half sr_half(float x, uint32_t r) {
-    __half lo = __float2half_rz(x);
-    float alo = fabsf(__half2float(lo));
-    float ax = fabsf(x);
-    if (!(ax < 65504.0f) || ax == alo) return __float2half_rn(x);
-    unsigned short mag = __half_as_ushort(lo) & 0x7FFFu;
-    float ulp = __half2float(__ushort_as_half((unsigned short)(mag + 1))) - alo;
-    float u = __fmul_rn(__fmul_rn((float)(r >> 8), ulp), 0x1p-24f);
-    if (u < __fsub_rn(ax, alo)) mag = (unsigned short)(mag + 1);
-    return __ushort_as_half((unsigned short)(mag | (x < 0.0f ? 0x8000u : 0u)));
+    const float ax = fabsf(x);
+    if (!(ax < 65504.0f)) return __float2half_rn(x);
+    const uint32_t b = __float_as_uint(x);
+    if (ax < 0x1p-24f) {
+        const bool away = __fmul_rn((float)(r >> 8), 0x1p-48f) < ax;
+        return __ushort_as_half((unsigned short)(((b >> 16) & 0x8000u) | (away ? 1u : 0u)));
+    }
+    const int d = max(13, 126 - (int)((b >> 23) & 0xFFu));
+    // clear the dropped bits: after a carry into the exponent the FP16 ulp
+    // below 2^-14 stays 2^-24, so the leftover bits would not all drop
+    const uint32_t kept = (b + (r >> (32 - d))) & ~((1u << d) - 1u);
+    return __float2half_rz(__uint_as_float(kept));
 }
 __device__ __forceinline__ __nv_bfloat16 sr_bf16(float x, uint32_t r) {
-    __nv_bfloat16 lo = __float2bfloat16_rz(x);
-    float alo = fabsf(__bfloat162float(lo));
-    float ax = fabsf(x);
-    if (!(ax < 3.0e38f) || ax == alo) return __float2bfloat16_rn(x);
-    unsigned short mag = __bfloat16_as_ushort(lo) & 0x7FFFu;
-    float ulp = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mag + 1))) - alo;
-    float u = __fmul_rn(__fmul_rn((float)(r >> 8), ulp), 0x1p-24f);
-    if (u < __fsub_rn(ax, alo)) mag = (unsigned short)(mag + 1);
-    return __ushort_as_bfloat16((unsigned short)(mag | (x < 0.0f ? 0x8000u : 0u)));
+    if (!(fabsf(x) < 3.0e38f)) return __float2bfloat16_rn(x);
+    return __ushort_as_bfloat16((unsigned short)((__float_as_uint(x) + (r >> 16)) >> 16));
 }
 
 template <class S> struct Codec;

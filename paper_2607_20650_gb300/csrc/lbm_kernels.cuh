@@ -912,14 +912,15 @@ __global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : 4) k_npo
 // with slot i of x + c_i when both are fluid (no exchange = bounce-back).
 // Values that enter through domain edges or from other tiles (buffer grid)
 // are substituted afterwards.
-// smem_raw: 9 * tx * ty compute values followed by tx * ty flag bytes.
+// Two block barriers: after the staging (and the substitutions, read from
+// the lattice and the buffer grid), and after the exchanges.
+// smem_raw: 9 * tx * ty compute values.
 template <class S, int L>
 __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int lx, int ly, int lane,
                                           unsigned char *smem_raw) {
     using C = typename Codec<S>::C;
     const int T = a.tx * a.ty;
     C *sm = reinterpret_cast<C *>(smem_raw);
-    uint8_t *fl = smem_raw + sizeof(C) * 9 * T;
     const int nx = a.geo.nx, ny = a.geo.ny;
     const int x0 = bx * a.tx, y0 = by * a.ty;
     const int x1 = min(x0 + a.tx, nx) - 1, y1 = min(y0 + a.ty, ny) - 1;
@@ -937,14 +938,15 @@ __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int 
     const unsigned F = __ballot_sync(__activemask(), fluid);
     (void)F;
     const bool zero_fill = false;   // measured: NSOL is 2 % faster without the sector zero fill
-    if (member) fl[tid] = fluid ? 1 : 0;
     if (fluid) {
 #pragma unroll
         for (int s = 0; s < 9; ++s) sm[s * T + tid] = ldp<S, L>(lat, a.N, n, s);
     }
     const C dnb = (fluid && x == 0 && a.geo.bw == INLET_EQ_NEUMANN) ? neighbour_drho<S, L>(a, lat, n, 1) : C(0);
-    __syncthreads();
-    // Substitutions for pulls the in-tile exchange does not cover.
+    // Substitutions for pulls the in-tile exchange does not cover, read
+    // before the first barrier: the lattice holds the previous state until
+    // the stores after the last barrier, and other tiles' values come from
+    // the buffer grid.
     C fix[9];
     unsigned fixmask = 0;
     const bool dom_inner = x > 0 && x < nx - 1 && y > 0 && y < ny - 1;
@@ -977,19 +979,20 @@ __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int 
             fixmask |= 1u << i;
             if (kind != PULL_NODE) continue;  // inlet unknown
             if (in_tile)
-                fix[i] = sm[opp(j) * T + (ys - y0) * a.tx + (xs - x0)];
+                fix[i] = ldp<S, L>(lat, a.N, (uint32_t)ys * (uint32_t)nx + (uint32_t)xs, opp(j));
             else
                 fix[i] = halo_read(a, xs, ys, j, bx);
         }
     }
     __syncthreads();
     if (fluid) {
+        // partner x + c_i fluid <=> the pull of direction 8-i from it does not bounce
 #pragma unroll
         for (int i = 5; i < 9; ++i) {
             const int px = lx + cx(i), py = ly + cy(i);
             if (px >= 0 && px < a.tx && py < a.ty && x0 + px <= x1 && y0 + py <= y1) {
                 const int pt = py * a.tx + px;
-                if (fl[pt]) {
+                if (!((lk >> link_bit(opp(i))) & 1u)) {
                     C t = sm[opp(i) * T + tid];
                     sm[opp(i) * T + tid] = sm[i * T + pt];
                     sm[i * T + pt] = t;
@@ -1013,8 +1016,11 @@ __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int 
     }
 }
 
+#ifndef LBM_NSOL_MINB
+#define LBM_NSOL_MINB 4
+#endif
 template <class S, int L>
-__global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : 4) k_nsol(const Step<S> a) {
+__global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : LBM_NSOL_MINB) k_nsol(const Step<S> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     nsol_tile<S, L>(a, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y,
                     (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u), smem_raw);
@@ -1582,7 +1588,7 @@ cudaError_t step_layout(const HostArgs &h, const Step<S> &a, int phase, cudaStre
             break;
         case NPOL: k_npol<S, L><<<grid, tile, 0, st>>>(a); break;
         case NSOL: {
-            const size_t sm = sizeof(C) * 9 * h.tile_x * h.tile_y + h.tile_x * h.tile_y;
+            const size_t sm = sizeof(C) * 9 * h.tile_x * h.tile_y;
             k_nsol<S, L><<<grid, tile, sm, st>>>(a);
             break;
         }

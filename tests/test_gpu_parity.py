@@ -229,25 +229,40 @@ def test_codec_round_to_nearest_even_matches_numpy():
 
 @pytest.mark.parametrize("storage", ["f16s", "bf16s"])
 def test_codec_stochastic_rounding_is_unbiased_and_keyed(storage):
+    """Each value rounds to one of its two 16-bit neighbours, away from zero
+    with probability (|x| - |lo|) / ulp: checked for values in the FP16
+    normal range, in its subnormal range (2.5e-5 < 2^-14, 9.1e-8 just above
+    2^-24, 3.7e-8 below it), negative ones and a large one. The draws depend on the keys only (same update index, same
+    bits; another index, other draws), and the decisions of different
+    directions of one node are uncorrelated."""
     K = 9 * 200000
-    val = np.float32(1.0e-3 + 3.3e-7)
-    x = np.full(K, val, dtype=np.float32)
-    d_in = torch.from_numpy(x).cuda()
-    out = torch.empty(K, dtype=torch.int16, device="cuda")
-    b1, b2, b3 = (torch.empty_like(d_in) for _ in range(3))
     s = lbm.current_stream()
-    lbm.lbm_quantize(storage, "sr", 42, 5, d_in, out, b1, K, s)
-    lbm.lbm_quantize(storage, "sr", 42, 5, d_in, out, b2, K, s)
-    lbm.lbm_quantize(storage, "sr", 42, 6, d_in, out, b3, K, s)
-    torch.cuda.synchronize()
-    v1, v2, v3 = (b.cpu().numpy().astype(np.float64) for b in (b1, b2, b3))
-    assert np.array_equal(v1, v2)                    # same keys, same bits
-    assert not np.array_equal(v1, v3)                # another update index, other draws
-    lo, hi = np.unique(v1)[[0, -1]]
-    assert len(np.unique(v1)) == 2 and lo < val < hi  # only the two neighbours
-    p = (float(val) - lo) / (hi - lo)
-    frac = np.mean(v1 == hi)
-    assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / K) + 2 ** -24
+    for val in (np.float32(1.0e-3 + 3.3e-7), np.float32(-2.5e-5 - 1.3e-9), np.float32(0.3 + 1.1e-7),
+                np.float32(-7.1e-2 - 2.9e-9), np.float32(9.1e-8), np.float32(-3.7e-8)):
+        x = np.full(K, val, dtype=np.float32)
+        d_in = torch.from_numpy(x).cuda()
+        out = torch.empty(K, dtype=torch.int16, device="cuda")
+        b1, b2, b3 = (torch.empty_like(d_in) for _ in range(3))
+        lbm.lbm_quantize(storage, "sr", 42, 5, d_in, out, b1, K, s)
+        lbm.lbm_quantize(storage, "sr", 42, 5, d_in, out, b2, K, s)
+        lbm.lbm_quantize(storage, "sr", 42, 6, d_in, out, b3, K, s)
+        torch.cuda.synchronize()
+        v1, v2, v3 = (b.cpu().numpy().astype(np.float64) for b in (b1, b2, b3))
+        assert np.array_equal(v1, v2)                    # same keys, same bits
+        assert not np.array_equal(v1, v3)                # another update index, other draws
+        vals = np.unique(v1)
+        assert len(vals) == 2, (val, vals)               # only the two neighbours
+        near, far = (vals[1], vals[0]) if val < 0 else (vals[0], vals[1])
+        assert abs(near) < abs(float(val)) < abs(far)
+        p = (abs(float(val)) - abs(near)) / (abs(far) - abs(near))
+        up = (v1 == far)
+        frac = np.mean(up)
+        assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / K) + 2 ** -24, (val, frac, p)
+        # directions of one node (k = 9 n + i): decisions of i and i + 1 uncorrelated
+        d = up.reshape(-1, 9).astype(np.float64)
+        for i in range(8):
+            c = np.corrcoef(d[:, i], d[:, i + 1])[0, 1]
+            assert abs(c) < 5 / math.sqrt(d.shape[0]), (val, i, c)
 
 
 def test_neumann_inlet_rejected_for_aa_and_thin_one_lattice_tiles():
