@@ -633,11 +633,16 @@ def e2e(args, mask, torch, world=1):
         import torch.distributed as dist
         dist.barrier()
     t = time.perf_counter()
-    h = lbm.lbm_create(p, host_mask, ws, nbytes, stream)
+    h = lbm.lbm_create(p, host_mask, ws, nbytes, stream)       # synchronous
+    t1 = time.perf_counter()
     lbm.lbm_step(h, k, True)
+    lbm.lbm_sync(h)
+    t2 = time.perf_counter()
     lib = lbm.load()
     st = lib.lbm_read_moments(h, rho.ctypes.data, ux.ctypes.data, uy.ctypes.data)
     dt = time.perf_counter() - t
+    parts = {"create_and_init_ms": (t1 - t) * 1e3, "updates_ms": (t2 - t1) * 1e3,
+             "read_moments_ms": (t + dt - t2) * 1e3}
     lbm.lbm_destroy(h)
     assert st == 0
     del ws
@@ -646,7 +651,7 @@ def e2e(args, mask, torch, world=1):
         dt = max_over_ranks(dt, "cuda")
     return {"value": N * k * world / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": N * world / k,
             "d2h_bytes_per_step": 3 * 8 * N * world / k, "steps": k, "replicas": world,
-            "host_buffers": "page-locked",
+            "host_buffers": "page-locked", "parts": parts,
             "region": "lbm_create(host mask) + init + K updates + lbm_read_moments(host f64)"}
 
 
