@@ -250,6 +250,43 @@ lbm_status lbm_quantize(int32_t storage, int32_t rounding, uint64_t seed, int64_
 lbm_status lbm_mass_f32_noalloc(const float *d_h, const uint8_t *d_solid, int64_t N, double *out,
                                 void *cuda_stream);
 
+/* ---------------------------------------------------------------- masks
+ * Host-side generator of the benchmark families' solid masks (Sec. 4:
+ * Hagen-Poiseuille channel, obstacles, porous media, a wing at an angle of
+ * attack) for callers that do not build masks themselves. No GPU work. The
+ * mask is row-major, mask[y nx + x] (3-D: mask[(z ny + y) nx + x]), 1 =
+ * solid, caller-owned (nx * ny bytes), overwritten (lbm_mask_disc: ORed
+ * into). Seeded generators draw from splitmix64 streams (Steele, Lea & Flood,
+ * 2014) seeded with seed ^ mix(stream * gamma + gamma), doubles (x >> 11)
+ * 2^-53: the same masks as the package's Python input generator. LBM_EINVAL
+ * on a NULL mask, nx * ny >= 2^32 or out-of-range parameters.            */
+/* Solid rows y = 0 and y = ny - 1. */
+lbm_status lbm_mask_channel_walls(int32_t nx, int32_t ny, uint8_t *mask);
+/* Nodes with (x - xc)^2 + (y - yc)^2 <= r^2 (integer node coordinates) set
+ * to 1; periodic != 0 wraps the disc around the domain, else clips it. */
+lbm_status lbm_mask_disc(int32_t nx, int32_t ny, double xc, double yc, double r, int32_t periodic,
+                         uint8_t *mask);
+/* Random overlapping discs on a periodic domain (stream 1: three uniforms
+ * per disc, centre (u nx, v ny), radius rmin + (rmax - rmin) w, batches of
+ * 256) until at least solid_fraction of the nodes are solid. The 134M-node
+ * porous workload: 16384 x 8192, seed 3, radii 8-32, fraction 0.4. */
+lbm_status lbm_mask_porous_discs(int32_t nx, int32_t ny, uint64_t seed, double rmin, double rmax,
+                                 double solid_fraction, uint8_t *mask);
+/* NACA 4-digit airfoil (camber m at chord fraction p, thickness t: 2412 is
+ * 0.02, 0.4, 0.12) of the given chord in nodes, from the closed-form
+ * thickness (closed trailing edge) and camber-line equations with n_points
+ * cosine-spaced points per side, leading edge at (nx/4, ny/2), rotated
+ * nose-up by aoa_deg about the quarter chord; nodes inside the outline
+ * (even-odd rule) are solid. Transcendental functions come from the C
+ * library, so a node within rounding distance of the outline may differ
+ * from another implementation's. */
+lbm_status lbm_mask_naca4(int32_t nx, int32_t ny, double chord, double m, double p, double t,
+                          double aoa_deg, int32_t n_points, uint8_t *mask);
+/* Random overlapping spheres on a periodic box (stream 5: four uniforms per
+ * sphere, batches of 256) until at least solid_fraction is solid. */
+lbm_status lbm3_mask_porous_spheres(int32_t nx, int32_t ny, int32_t nz, uint64_t seed, double rmin,
+                                    double rmax, double solid_fraction, uint8_t *mask);
+
 /* ---------------------------------------------------------------- batches
  * Many independent lattices advanced together, one persistent launch per
  * update over a packed list of tiles of every case, captured into CUDA

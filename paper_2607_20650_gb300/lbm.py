@@ -110,6 +110,11 @@ SIGNATURES = {
     "lbm_layout_index": (_i64, [_i32, _i64, _i64, _i32]),
     "lbm_quantize": (_i32, [_i32, _i32, _u64, _i64, _vp, _vp, _vp, _i64, _vp]),
     "lbm_mass_f32_noalloc": (_i32, [_vp, _vp, _i64, _P(_dbl), _vp]),
+    "lbm_mask_channel_walls": (_i32, [_i32, _i32, _vp]),
+    "lbm_mask_disc": (_i32, [_i32, _i32, _dbl, _dbl, _dbl, _i32, _vp]),
+    "lbm_mask_porous_discs": (_i32, [_i32, _i32, _u64, _dbl, _dbl, _dbl, _vp]),
+    "lbm_mask_naca4": (_i32, [_i32, _i32, _dbl, _dbl, _dbl, _dbl, _dbl, _i32, _vp]),
+    "lbm3_mask_porous_spheres": (_i32, [_i32, _i32, _i32, _u64, _dbl, _dbl, _dbl, _vp]),
     "lbm_tune": (_i32, [_P(lbm_params), _vp, _vp, _sz, _vp, _P(lbm_tuning)]),
     "lbm_tune_workspace_bytes": (_i32, [_P(lbm_params), _P(_sz)]),
     "lbm_batch_plan": (_i32, [_i32, _P(lbm_params), _P(lbm_tuning)]),
@@ -300,6 +305,42 @@ def lbm_quantize(storage, rounding, seed, t, d_in, d_out, d_back, count, stream)
                                ROUNDINGS[rounding] if isinstance(rounding, str) else rounding,
                                int(seed), int(t), _ptr(d_in), _ptr(d_out), _ptr(d_back),
                                int(count), stream), "lbm_quantize")
+
+
+def lbm_mask_channel_walls(nx: int, ny: int) -> np.ndarray:
+    m = np.empty((ny, nx), np.uint8)
+    _check(load().lbm_mask_channel_walls(nx, ny, m.ctypes.data), "lbm_mask_channel_walls")
+    return m
+
+
+def lbm_mask_disc(nx: int, ny: int, xc: float, yc: float, r: float, periodic: bool = False,
+                  out: np.ndarray | None = None) -> np.ndarray:
+    m = np.zeros((ny, nx), np.uint8) if out is None else out
+    _check(load().lbm_mask_disc(nx, ny, xc, yc, r, int(periodic), m.ctypes.data), "lbm_mask_disc")
+    return m
+
+
+def lbm_mask_porous_discs(nx: int, ny: int, seed: int, rmin: float = 8.0, rmax: float = 32.0,
+                          solid_fraction: float = 0.4) -> np.ndarray:
+    m = np.empty((ny, nx), np.uint8)
+    _check(load().lbm_mask_porous_discs(nx, ny, seed, rmin, rmax, solid_fraction, m.ctypes.data),
+           "lbm_mask_porous_discs")
+    return m
+
+
+def lbm_mask_naca4(nx: int, ny: int, chord: float, m: float = 0.02, p: float = 0.4, t: float = 0.12,
+                   aoa_deg: float = 8.0, n_points: int = 2048) -> np.ndarray:
+    out = np.empty((ny, nx), np.uint8)
+    _check(load().lbm_mask_naca4(nx, ny, chord, m, p, t, aoa_deg, n_points, out.ctypes.data), "lbm_mask_naca4")
+    return out
+
+
+def lbm3_mask_porous_spheres(nx: int, ny: int, nz: int, seed: int, rmin: float = 4.0, rmax: float = 12.0,
+                             solid_fraction: float = 0.3) -> np.ndarray:
+    m = np.empty((nz, ny, nx), np.uint8)
+    _check(load().lbm3_mask_porous_spheres(nx, ny, nz, seed, rmin, rmax, solid_fraction, m.ctypes.data),
+           "lbm3_mask_porous_spheres")
+    return m
 
 
 def lbm_mass_f32_noalloc(d_h, d_solid, N: int, stream: int) -> float:

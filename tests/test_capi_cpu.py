@@ -257,3 +257,36 @@ def test_flag_constants_match_header():
     assert {"LBM_FLAG_NO_GRAPH", "LBM_FLAG_NO_PREFETCH", "LBM_FLAG_WIDE_OFFSETS"} <= set(flags)
     for name, value in flags.items():
         assert getattr(lbm, name) == int(value, 16), name
+
+
+# ---------------------------------------------------------------- host mask generator
+
+def test_c_mask_generator_matches_the_python_input_generator(lib):
+    """The C ABI's host mask generator and the package's Python input
+    generator draw the same splitmix64 streams and apply the same
+    double-precision tests, so the seeded masks agree bit for bit."""
+    from paper_2607_20650_gb300 import geometry as G
+    for nx, ny, seed in ((300, 170, 21), (512, 256, 3), (97, 61, 5)):
+        assert np.array_equal(lbm.lbm_mask_porous_discs(nx, ny, seed, 4.0, 9.0, 0.3),
+                              G.porous_discs(nx, ny, seed, rmin=4, rmax=9, solid_fraction=0.3))
+    assert np.array_equal(lbm.lbm_mask_porous_discs(1024, 512, 3), G.porous_discs(1024, 512, 3))
+    assert np.array_equal(lbm.lbm_mask_channel_walls(256, 64), G.channel_walls(256, 64))
+    for periodic in (False, True):
+        assert np.array_equal(lbm.lbm_mask_disc(96, 40, 3.5, 20.0, 6.5, periodic),
+                              G.disc(96, 40, 3.5, 20.0, 6.5, periodic=periodic))
+    assert np.array_equal(lbm.lbm3_mask_porous_spheres(40, 36, 30, 3, 2.0, 5.0, 0.25),
+                          G.porous_spheres(40, 36, 30, 3, 2.0, 5.0, 0.25))
+    # the wing: transcendental functions of two libraries may differ in the
+    # last place, which can move a node lying on the outline
+    c = lbm.lbm_mask_naca4(2048, 1024, 256.0)
+    p = G.naca_wing(2048, 1024, 256.0)
+    assert int(p.sum()) > 0.06 * 256 * 256 * 0.12 and np.count_nonzero(c != p) <= 4
+
+
+def test_c_mask_generator_rejects_bad_arguments(lib):
+    for call in (lambda: lbm.lbm_mask_porous_discs(0, 8, 1), lambda: lbm.lbm_mask_porous_discs(8, 8, 1, 5.0, 4.0),
+                 lambda: lbm.lbm_mask_porous_discs(8, 8, 1, 1.0, 2.0, 1.0),
+                 lambda: lbm.lbm_mask_naca4(64, 32, -1.0), lambda: lbm.lbm3_mask_porous_spheres(4, 4, 0, 1)):
+        with pytest.raises(lbm.LbmError) as e:
+            call()
+        assert e.value.status == lbm.LBM_EINVAL
