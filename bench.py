@@ -10,9 +10,11 @@ of 32 x 4 nodes, two lattices): the fastest two-lattice combination measured
 on this workload. MLUPS counts every node (solid ones included), as the paper does.
 
 Also reported: the same update with FP16/BF16 shifted storage, the one-lattice
-NPOL variant, the batched ensemble of 256 channels against 256 sequential
-single-case runs, the FP64 CPU oracle on a bounded sample (cpu_baseline), and
-an end-to-end number through the C ABI with host buffers (e2e).
+NPOL, NSOL and AA variants, the batched ensemble of 256 channels against 256
+sequential single-case runs, the D3Q19 extension (a 384^3 sphere packing in
+every layout and algorithm, and a batch of 128 boxes against sequential
+runs), the FP64 CPU oracle on a bounded sample (cpu_baseline), and an
+end-to-end number through the C ABI with host buffers (e2e).
 
 Prints ONE JSON line. ``--impl reference`` times the CPU oracle instead.
 """
@@ -391,6 +393,7 @@ def run_ours(args):
         result["variants"] = variants(args, mask, torch, world)
         result["batched"] = batched(args, torch)
         result["d3q19"] = d3q19(args, torch)
+        result["batched_d3q19"] = batched3(args, torch)
     result["e2e"] = e2e(args, mask, torch, world)
     if rank == 0 and not args.no_cpu and world == 1:
         result["cpu_baseline"] = cpu_sample()
@@ -607,6 +610,59 @@ def batched(args, torch):
             "speedup": t_seq / t_batch, "tiles": info["tiles"], "grid": info["grid"],
             "chosen": chosen,
             "tuned_ns_per_node": [[round(tuning.ns_per_cell[l][a], 5) for a in range(4)] for l in range(3)]}
+
+
+def batched3(args, torch):
+    """128 independent D3Q19 boxes (seeded edges 16-96 per axis, random sphere
+    packings r 2-6 of solid fraction 0.2, periodic, tau in [0.6, 1.2],
+    g_x = 1e-6, FP32 bundle NPTL 32x4x4): one launch per update over the
+    tiles of every box (graphs of 64 updates) against the same boxes run one
+    after another as single boxes (each lbm3_step(K), graphs of 64)."""
+    from paper_2607_20650_gb300 import geometry as G, lbm
+    ncases = 128
+    r = G.SplitMix64(21, 3)
+    dims = r.integers(3 * ncases, 16, 96).reshape(ncases, 3)
+    taus = r.uniform(ncases, 0.6, 1.2)
+    kw = dict(storage="f32", layout="bundle", algo="nptl", tile=(32, 4, 4), force=(1e-6, 0.0, 0.0))
+    masks = [G.porous_spheres(int(nx), int(ny), int(nz), 100 + c, 2.0, 6.0, 0.2) for c, (nx, ny, nz) in enumerate(dims)]
+    params = [lbm.make_params3(int(nx), int(ny), int(nz), float(t), **kw) for (nx, ny, nz), t in zip(dims, taus)]
+    stream = torch.cuda.Stream()
+    b = lbm.Batch3(params, masks, stream=stream)
+    info = b.info()
+    k = 128
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.step(64).sync()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(k)
+    e1.record(stream)
+    e1.synchronize()
+    b.sync()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    b.close()
+    del b
+    singles = []
+    for (nx, ny, nz), t, m in zip(dims, taus, masks):
+        singles.append(lbm.Lattice3(int(nx), int(ny), int(nz), float(t), m, stream=stream, **kw))
+    for lat in singles:
+        lbm.lbm3_step(lat.h, 64, False)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for lat in singles:
+        lbm.lbm3_step(lat.h, k, False)
+    e1.record(stream)
+    e1.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    for lat in singles:
+        lat.close()
+    del singles
+    torch.cuda.empty_cache()
+    hbm, _ = peaks()
+    gbs = info["bytes_per_update"] * k / t_batch / 1e9
+    return {"cases": ncases, "nodes": info["cells"], "fluid_nodes": info["fluid_cells"], "steps": k,
+            "work_items": info["items"], "batched_MLUPS": info["cells"] * k / t_batch / 1e6,
+            "sequential_MLUPS": info["cells"] * k / t_seq / 1e6, "speedup": t_seq / t_batch,
+            "GBps_algorithmic": gbs, "frac_of_measured_hbm": gbs / hbm}
 
 
 def e2e(args, mask, torch, world=1):

@@ -353,7 +353,9 @@ void lbm_batch_destroy(lbm_batch *B);
  * 0,0,0 = 128 x 1 x 1; tile_z <= 64), two lattices; NPOL (one lattice and a
  * buffer grid: per tile and parity, the five populations leaving each node
  * of each of the six tile faces, 2 x tiles x 10 (ty tz + tx tz + tx ty)
- * values); AA (the same tiles, one lattice, as in 2-D: populations and mass
+ * values); NSOL (one lattice, swap streaming: population i of a node kept
+ * in its slot opp(i), the tile staged in shared memory, the same buffer
+ * grid as NPOL); AA (the same tiles, one lattice, as in 2-D: populations and mass
  * accessible after an even number of updates only, LBM_EINVAL otherwise;
  * needs 32-bit offset tables, i.e. roughly 19 N < 2^31, LBM_EUNSUPPORTED
  * otherwise). All produce the same bits at equal storage. Faces per axis: PERIODIC or WALL
@@ -420,6 +422,48 @@ lbm_status lbm3_force(lbm3_lattice *L, const uint8_t *d_body, double out[3]);
 lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out);
 void lbm3_destroy(lbm3_lattice *L);
 int64_t lbm3_layout_index(int32_t layout, int64_t N, int64_t n, int32_t i);
+
+/* ---------------------------------------------------------------- D3Q19 batches
+ * Many independent boxes advanced together: one launch per update over a
+ * packed list of work items of every case (a tile for NPTL, NPOL and NSOL,
+ * 256 consecutive nodes for LPTL), captured into CUDA graphs of 64 updates.
+ * Per case: its own size, tau, force, faces, inlet/outlet, rounding, seed and
+ * mask. Shared by every case (LBM_EINVAL otherwise): storage, layout,
+ * algorithm (LPTL, NPTL, NPOL or NSOL; AA: LBM_EUNSUPPORTED) and, for the
+ * tiled algorithms, the tile. Every case must fit the 32-bit offset tables
+ * (roughly 19 N < 2^31, no LBM_FLAG_WIDE_OFFSETS; LBM_EUNSUPPORTED
+ * otherwise). Results per case are bit-identical to a single-box run of the
+ * same parameters, stochastic rounding included (the batch's update counter
+ * starts at 0 like a box's).
+ * Workspace: lbm3_batch_workspace_bytes of 256-byte aligned device memory,
+ * the caller's, as is the stream. A divergence in any case is reported by
+ * lbm3_batch_sync and the read calls as LBM_EDIVERGED.                    */
+typedef struct lbm3_batch lbm3_batch;
+
+lbm_status lbm3_batch_workspace_bytes(int32_t ncases, const lbm3_params *params, size_t *bytes);
+/* params, masks_host: ncases entries; mask c holds nx ny nz bytes of case c
+ * (nonzero = solid, host, read during the call). Initial state of every
+ * case: rho = 1, v = 0. */
+lbm_status lbm3_batch_create(int32_t ncases, const lbm3_params *params, const uint8_t *const *masks_host,
+                             void *d_workspace, size_t bytes, void *cuda_stream, lbm3_batch **out);
+/* Equilibrium of case c from host arrays (NULL: rho 1 / v 0); only before
+ * the first lbm3_batch_step (LBM_EINVAL afterwards). Synchronous. */
+lbm_status lbm3_batch_init(lbm3_batch *B, int32_t c, const double *rho, const double *ux, const double *uy,
+                           const double *uz);
+/* Enqueue nsteps updates of every case; with want_moments the last one
+ * writes rho, v of every case. */
+lbm_status lbm3_batch_step(lbm3_batch *B, int64_t nsteps, uint32_t want_moments);
+lbm_status lbm3_batch_sync(lbm3_batch *B);
+/* Case c, as lbm3_read_moments / lbm3_read_populations / lbm3_mass. */
+lbm_status lbm3_batch_read_moments(lbm3_batch *B, int32_t c, double *rho, double *ux, double *uy, double *uz);
+lbm_status lbm3_batch_read_populations(lbm3_batch *B, int32_t c, void *host, int32_t as);
+lbm_status lbm3_batch_mass(lbm3_batch *B, int32_t c, double *out);
+/* Work items per update, total nodes, total fluid nodes and algorithmic
+ * bytes per update (the sum of the cases' lbm3_get_info figures); any
+ * pointer may be NULL. */
+lbm_status lbm3_batch_get_info(lbm3_batch *B, int64_t *items, int64_t *cells, int64_t *fluid_cells,
+                               double *bytes_per_update);
+void lbm3_batch_destroy(lbm3_batch *B);
 
 #ifdef __cplusplus
 }

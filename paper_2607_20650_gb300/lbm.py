@@ -140,6 +140,16 @@ SIGNATURES = {
     "lbm3_get_info": (_i32, [_vp, _P(lbm_info)]),
     "lbm3_destroy": (None, [_vp]),
     "lbm3_layout_index": (_i64, [_i32, _i64, _i64, _i32]),
+    "lbm3_batch_workspace_bytes": (_i32, [_i32, _P(lbm3_params), _P(_sz)]),
+    "lbm3_batch_create": (_i32, [_i32, _P(lbm3_params), _P(_vp), _vp, _sz, _vp, _P(_vp)]),
+    "lbm3_batch_init": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
+    "lbm3_batch_step": (_i32, [_vp, _i64, _u32]),
+    "lbm3_batch_sync": (_i32, [_vp]),
+    "lbm3_batch_read_moments": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
+    "lbm3_batch_read_populations": (_i32, [_vp, _i32, _vp, _i32]),
+    "lbm3_batch_mass": (_i32, [_vp, _i32, _P(_dbl)]),
+    "lbm3_batch_get_info": (_i32, [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_dbl)]),
+    "lbm3_batch_destroy": (None, [_vp]),
 }
 
 _lib = None
@@ -539,6 +549,74 @@ def lbm3_layout_index(layout, N: int, n: int, i: int) -> int:
     return int(load().lbm3_layout_index(lay, int(N), int(n), int(i)))
 
 
+def _param3_array(params):
+    arr = (lbm3_params * len(params))()
+    for k, p in enumerate(params):
+        arr[k] = p
+    return arr
+
+
+def lbm3_batch_workspace_bytes(params: list) -> int:
+    b = ctypes.c_size_t()
+    _check(load().lbm3_batch_workspace_bytes(len(params), _param3_array(params), ctypes.byref(b)),
+           "lbm3_batch_workspace_bytes")
+    return b.value
+
+
+def lbm3_batch_create(params: list, masks: list, workspace, nbytes: int, stream: int):
+    arr = _param3_array(params)
+    ms = [np.ascontiguousarray(m, dtype=np.uint8).reshape(-1) for m in masks]
+    ptrs = (ctypes.c_void_p * len(ms))(*[m.ctypes.data for m in ms])
+    h = ctypes.c_void_p()
+    _check(load().lbm3_batch_create(len(params), arr, ptrs, _ptr(workspace), nbytes, stream,
+                                    ctypes.byref(h)), "lbm3_batch_create")
+    return h, ms
+
+
+def lbm3_batch_init(h, c: int, rho=None, ux=None, uy=None, uz=None):
+    arrs = [_f64(a) for a in (rho, ux, uy, uz)]
+    _check(load().lbm3_batch_init(h, int(c), *[_ptr(a) for a in arrs]), "lbm3_batch_init")
+
+
+def lbm3_batch_step(h, nsteps: int, want_moments: bool = False):
+    _check(load().lbm3_batch_step(h, int(nsteps), 1 if want_moments else 0), "lbm3_batch_step")
+
+
+def lbm3_batch_sync(h):
+    _check(load().lbm3_batch_sync(h), "lbm3_batch_sync")
+
+
+def lbm3_batch_read_moments(h, c: int, N: int):
+    out = [np.empty(N) for _ in range(4)]
+    _check(load().lbm3_batch_read_moments(h, int(c), *[a.ctypes.data for a in out]),
+           "lbm3_batch_read_moments")
+    return out
+
+
+def lbm3_batch_read_populations(h, c: int, N: int, as_: str = "f64") -> np.ndarray:
+    out = np.empty((19, N), dtype=np.float64 if as_ == "f64" else np.float32)
+    _check(load().lbm3_batch_read_populations(h, int(c), out.ctypes.data, STORAGES[as_]),
+           "lbm3_batch_read_populations")
+    return out
+
+
+def lbm3_batch_mass(h, c: int) -> float:
+    out = ctypes.c_double()
+    _check(load().lbm3_batch_mass(h, int(c), ctypes.byref(out)), "lbm3_batch_mass")
+    return out.value
+
+
+def lbm3_batch_get_info(h) -> dict:
+    it, c, f, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    _check(load().lbm3_batch_get_info(h, ctypes.byref(it), ctypes.byref(c), ctypes.byref(f), ctypes.byref(b)),
+           "lbm3_batch_get_info")
+    return {"items": it.value, "cells": c.value, "fluid_cells": f.value, "bytes_per_update": b.value}
+
+
+def lbm3_batch_destroy(h):
+    load().lbm3_batch_destroy(h)
+
+
 def _torch():
     import torch
     return torch
@@ -704,6 +782,55 @@ class Lattice3:
     def close(self):
         if getattr(self, "h", None):
             lbm3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch3:
+    """Independent D3Q19 boxes advanced by one launch per update."""
+
+    def __init__(self, params: list, masks: list, stream=None):
+        torch = _torch()
+        self.params = list(params)
+        self.N = [p.nx * p.ny * p.nz for p in self.params]
+        nbytes = lbm3_batch_workspace_bytes(self.params)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.torch_stream = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = self.torch_stream.cuda_stream
+        self.h, self._masks = lbm3_batch_create(self.params, masks, self.workspace, nbytes, self.stream)
+
+    def init(self, c, rho=None, ux=None, uy=None, uz=None):
+        lbm3_batch_init(self.h, c, rho, ux, uy, uz)
+        return self
+
+    def step(self, n: int, moments: bool = False):
+        lbm3_batch_step(self.h, n, moments)
+        return self
+
+    def sync(self):
+        lbm3_batch_sync(self.h)
+        return self
+
+    def moments(self, c):
+        return lbm3_batch_read_moments(self.h, c, self.N[c])
+
+    def populations(self, c, as_: str = "f64"):
+        return lbm3_batch_read_populations(self.h, c, self.N[c], as_)
+
+    def mass(self, c) -> float:
+        return lbm3_batch_mass(self.h, c)
+
+    def info(self) -> dict:
+        return lbm3_batch_get_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm3_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

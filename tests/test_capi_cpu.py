@@ -249,6 +249,32 @@ def test_d3q19_inlet_outflow_params(lib):
         assert e.value.status == lbm.LBM_EUNSUPPORTED
 
 
+def test_d3q19_batch_plan_checked_without_gpu(lib):
+    a = lbm.make_params3(24, 16, 8, 0.8, algo="nptl", storage="f32", tile=(8, 4, 2))
+    b = lbm.make_params3(40, 8, 12, 0.7, algo="nptl", storage="f32", tile=(8, 4, 2), force=(1e-6, 0, 0))
+    total = lbm.lbm3_batch_workspace_bytes([a, b])
+    assert total >= lbm.lbm3_workspace_bytes(a) + lbm.lbm3_workspace_bytes(b)
+    # one record per case and one (case, item) pair per tile on top of the boxes
+    assert total <= lbm.lbm3_workspace_bytes(a) + lbm.lbm3_workspace_bytes(b) + 64 * 1024
+    for algo in ("lptl", "npol", "nsol"):
+        assert lbm.lbm3_batch_workspace_bytes([lbm.make_params3(24, 16, 8, 0.8, algo=algo, tile=(8, 4, 2))]) > 0
+    bad = [
+        ([a, lbm.make_params3(24, 16, 8, 0.8, algo="nptl", storage="f16s", tile=(8, 4, 2))], lbm.LBM_EINVAL),
+        ([a, lbm.make_params3(24, 16, 8, 0.8, algo="nptl", storage="f32", tile=(8, 2, 4))], lbm.LBM_EINVAL),
+        ([a, lbm.make_params3(24, 16, 8, 0.8, algo="lptl", storage="f32")], lbm.LBM_EINVAL),
+        ([a, lbm.make_params3(24, 16, 8, 0.8, algo="nptl", storage="f32", layout="bundle",
+                              tile=(8, 4, 2))], lbm.LBM_EINVAL),
+        ([lbm.make_params3(24, 16, 8, 0.8, algo="aa", tile=(8, 4, 2))], lbm.LBM_EUNSUPPORTED),
+        ([lbm.make_params3(24, 16, 8, 0.8, algo="nptl", tile=(8, 4, 2), flags=lbm.LBM_FLAG_WIDE_OFFSETS)],
+         lbm.LBM_EUNSUPPORTED),
+        ([], lbm.LBM_EINVAL),
+    ]
+    for params, status in bad:
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm3_batch_workspace_bytes(params)
+        assert e.value.status == status
+
+
 def test_flag_constants_match_header():
     """Every LBM_FLAG_* of include/lbm.h has the same value in the binding."""
     import re
