@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--geo3", default="porous", choices=["porous", "fluid"])
     ap.add_argument("--batch-only", action="store_true",
                     help="time only the 256-channel batched ensemble (profiling)")
+    ap.add_argument("--batch3-only", action="store_true",
+                    help="time only the batch of 512 D3Q19 boxes (profiling)")
     ap.add_argument("--ref-seconds", type=float, default=120.0,
                     help="--impl reference: CPU seconds for the warm-up and timed steps together")
     return ap.parse_args()
@@ -417,8 +419,9 @@ def variants(args, mask, torch, world):
                      ("f32_stream_lptl", dict(storage="f32", algo="lptl")),
                      ("f32_collision_nptl_64x4", dict(storage="f32", layout="collision", tile=(64, 4))),
                      ("f32_stream_npol_32x8", dict(storage="f32", algo="npol", tile=(32, 8))),
-                     ("f32_stream_nsol_32x8", dict(storage="f32", algo="nsol", tile=(32, 8))),
-                     ("f32_bundle_aa_128x1", dict(storage="f32", algo="aa", layout="bundle", tile=(128, 1))),
+                     ("f32_bundle_npol_64x4", dict(storage="f32", algo="npol", layout="bundle", tile=(64, 4))),
+                     ("f32_bundle_nsol_32x8", dict(storage="f32", algo="nsol", layout="bundle", tile=(32, 8))),
+                     ("f32_bundle_aa_64x2", dict(storage="f32", algo="aa", layout="bundle", tile=(64, 2))),
                      ("f16s_rne_bundle_nptl_32x8", dict(storage="f16s", layout="bundle", tile=(32, 8))),
                      ("f16s_rne_bundle_nptl_32x8_one_node_per_thread",
                       dict(storage="f16s", layout="bundle", tile=(32, 8), flags=0x20)),
@@ -513,8 +516,8 @@ def d3q19(args, torch):
                           ("f32_collision_nptl_128x1x1_porous", "porous", dict(storage="f32", layout="collision")),
                           ("f16s_rne_bundle_nptl_128x1x1_porous", "porous", dict(storage="f16s", layout="bundle")),
                           ("f32_bundle_aa_128x1x1_porous", "porous", dict(storage="f32", layout="bundle", algo="aa")),
-                          ("f32_stream_npol_32x8x2_porous", "porous", dict(storage="f32", layout="stream", algo="npol",
-                                                                          tile=(32, 8, 2))),
+                          ("f32_stream_npol_16x8x4_porous", "porous", dict(storage="f32", layout="stream", algo="npol",
+                                                                          tile=(16, 8, 4))),
                           ("f32_bundle_nsol_32x4x4_porous", "porous", dict(storage="f32", layout="bundle", algo="nsol",
                                                                           tile=(32, 4, 4))),
                           ("f32_stream_nsol_32x4x4_porous", "porous", dict(storage="f32", layout="stream", algo="nsol",
@@ -612,19 +615,19 @@ def batched(args, torch):
             "tuned_ns_per_node": [[round(tuning.ns_per_cell[l][a], 5) for a in range(4)] for l in range(3)]}
 
 
-def batched3(args, torch):
-    """128 independent D3Q19 boxes (seeded edges 16-96 per axis, random sphere
-    packings r 2-6 of solid fraction 0.2, periodic, tau in [0.6, 1.2],
-    g_x = 1e-6, FP32 bundle NPTL 32x4x4): one launch per update over the
-    tiles of every box (graphs of 64 updates) against the same boxes run one
-    after another as single boxes (each lbm3_step(K), graphs of 64)."""
+def batched3(args, torch, ncases: int = 512, edges=(12, 48), algo: str = "lptl", tile=(0, 0, 0)):
+    """512 independent D3Q19 boxes (seeded edges 12-48 per axis, random
+    sphere packings r 2-5 of solid fraction 0.2, periodic, tau in
+    [0.6, 1.2], g_x = 1e-6, FP32 bundle layout, LPTL): one launch per update
+    over the work items of every box (graphs of 64 updates) against the same
+    boxes run one after another as single boxes (each lbm3_step(K), graphs
+    of 64)."""
     from paper_2607_20650_gb300 import geometry as G, lbm
-    ncases = 128
     r = G.SplitMix64(21, 3)
-    dims = r.integers(3 * ncases, 16, 96).reshape(ncases, 3)
+    dims = r.integers(3 * ncases, edges[0], edges[1]).reshape(ncases, 3)
     taus = r.uniform(ncases, 0.6, 1.2)
-    kw = dict(storage="f32", layout="bundle", algo="nptl", tile=(32, 4, 4), force=(1e-6, 0.0, 0.0))
-    masks = [G.porous_spheres(int(nx), int(ny), int(nz), 100 + c, 2.0, 6.0, 0.2) for c, (nx, ny, nz) in enumerate(dims)]
+    kw = dict(storage="f32", layout="bundle", algo=algo, tile=tuple(tile), force=(1e-6, 0.0, 0.0))
+    masks = [G.porous_spheres(int(nx), int(ny), int(nz), 100 + c, 2.0, 5.0, 0.2) for c, (nx, ny, nz) in enumerate(dims)]
     params = [lbm.make_params3(int(nx), int(ny), int(nz), float(t), **kw) for (nx, ny, nz), t in zip(dims, taus)]
     stream = torch.cuda.Stream()
     b = lbm.Batch3(params, masks, stream=stream)
@@ -659,7 +662,8 @@ def batched3(args, torch):
     torch.cuda.empty_cache()
     hbm, _ = peaks()
     gbs = info["bytes_per_update"] * k / t_batch / 1e9
-    return {"cases": ncases, "nodes": info["cells"], "fluid_nodes": info["fluid_cells"], "steps": k,
+    return {"cases": ncases, "edges": list(edges), "algo": algo, "tile": list(tile),
+            "nodes": info["cells"], "fluid_nodes": info["fluid_cells"], "steps": k,
             "work_items": info["items"], "batched_MLUPS": info["cells"] * k / t_batch / 1e6,
             "sequential_MLUPS": info["cells"] * k / t_seq / 1e6, "speedup": t_seq / t_batch,
             "GBps_algorithmic": gbs, "frac_of_measured_hbm": gbs / hbm}
@@ -726,6 +730,16 @@ def main():
         print(json.dumps({"metric": "batched D2Q9 BGK MLUPS (256 channels)", "value": b["batched_MLUPS"],
                           "unit": "MLUPS", "n_gpus": 1, "steps": b["steps"], "higher_is_better": True,
                           "config": {"workload": "256 seeded channels, 37.1M nodes, FP32"}, "batched": b}))
+    elif args.batch3_only:
+        import torch
+        from paper_2607_20650_gb300 import build, lbm
+        build.build()
+        lbm.load()
+        b = batched3(args, torch)
+        print(json.dumps({"metric": "batched D3Q19 BGK MLUPS (512 boxes)", "value": b["batched_MLUPS"],
+                          "unit": "MLUPS", "n_gpus": 1, "steps": b["steps"], "higher_is_better": True,
+                          "config": {"workload": "512 seeded boxes of 12-48 nodes per edge, 13.8M nodes, FP32"},
+                          "batched_d3q19": b}))
     else:
         run_ours(args)
 
