@@ -974,17 +974,20 @@ struct Case3 {
     int pad;
 };
 
-// Resident 512-thread blocks the register budget is set for: the arguments
-// are read from shared memory here, and the single-lattice bound of three
-// blocks made the two-lattice body spill about 200 bytes.
+// Register budget: threads per block and resident blocks. The arguments are
+// read from shared memory here, which takes registers: the single-box bound
+// (three 512-thread blocks, 40 registers) made the two-lattice body spill
+// about 200 bytes. LPTL items are 256 nodes: five blocks (48 registers, a
+// few spilled bytes) measured 6 % faster than four (64).
+__host__ __device__ constexpr int batch3_threads(int algo) { return algo == LBM_LPTL ? 256 : 512; }
 __host__ __device__ constexpr int batch3_min_blocks(int algo, int elem) {
-    return (algo == LBM_LPTL || algo == LBM_NPTL) ? 2 : (elem == 8 ? 1 : 2);
+    return algo == LBM_LPTL ? 5 : (algo == LBM_NPTL ? 2 : (elem == 8 ? 1 : 2));
 }
 
 // src: update parity; toff: offset added to the update counter (stochastic
 // rounding keys); mom: store the moments.
 template <class S, int L, int ALGO, bool OFF32>
-__global__ void __launch_bounds__(512, batch3_min_blocks(ALGO, sizeof(S)))
+__global__ void __launch_bounds__(batch3_threads(ALGO), batch3_min_blocks(ALGO, sizeof(S)))
     k3_batch(const Case3<S> *cases, const uint2 *items, int src, int toff, int mom) {
     __shared__ __align__(16) unsigned char raw[sizeof(Step3<S>)];
     Step3<S> &a = *reinterpret_cast<Step3<S> *>(raw);
