@@ -428,6 +428,8 @@ def variants(args, mask, torch, world):
                      ("bf16s_rne_bundle_nptl_32x8", dict(storage="bf16s", layout="bundle", tile=(32, 8))),
                      ("f16s_sr_bundle_nptl_32x8", dict(storage="f16s", layout="bundle", tile=(32, 8),
                                                        rounding="sr", seed=7)),
+                     ("bf16s_sr_bundle_nptl_32x8", dict(storage="bf16s", layout="bundle", tile=(32, 8),
+                                                        rounding="sr", seed=7)),
                      ("f16s_rne_stream_npol_32x8", dict(storage="f16s", algo="npol", tile=(32, 8))),
                      ("bf16s_rne_stream_npol_32x8", dict(storage="bf16s", algo="npol", tile=(32, 8)))]:
         kw = dict(kw)

@@ -79,35 +79,35 @@ __host__ __device__ __forceinline__ uint32_t pop_rand(uint32_t nkey, int i) {
 }
 
 // ------------------------------------------------------------ codecs
-// Stochastic rounding of an FP32 value x to 16 bits: away from zero with
-// probability (|x| - |lo|) / ulp, lo the value rounded toward zero and ulp
-// the gap to the next magnitude. The 16-bit value keeps the top of x's bit
-// pattern and drops its low d bits, where ulp = 2^d FP32 ulps at x: BF16
-// d = 16; FP16 d = 13 in its normal range (|x| >= 2^-14) and d = 126 - the
-// FP32 exponent field (14 ... 23) below it, down to |x| = 2^-24. A uniform
-// random integer below 2^d (the top d bits of r) is added to the pattern and
-// the low d bits of the sum cleared: the kept part increments exactly when
-// the dropped bits plus the draw carry, i.e. with that probability (a carry
-// out of the mantissa gives the next power of two, which both formats hold). Below
-// 2^-24 the FP16 value is 0 or 2^-24: away iff (r >> 8) 2^-48 < |x|, exact in
-// FP32. Non-finite and out-of-range values round to nearest.
+// Stochastic rounding of FP32 values to 16 bits with the stochastic-rounding
+// conversion of the sm_100 family (cvt.rs): a random integer, the top bits of
+// the value's random word r (13 for FP16, 16 for BF16), is added to the top
+// bits the conversion drops and the sum truncated, so the kept part
+// increments exactly when those dropped bits plus the draw carry: away from
+// zero with probability (|x| - |lo|) / ulp, lo the value rounded toward zero
+// and ulp the gap to the next magnitude. BF16 drops 16 bits and FP16 13 in
+// its normal range (|x| >= 2^-14), where this is exact; below 2^-14 FP16
+// drops more than 13 bits and the probability is the dropped fraction cut to
+// 13 bits (at most 2^-13 ulp low). The packed forms round two values: hi to
+// the upper half (its draw in bits 28..16 for FP16, 31..16 for BF16), lo to
+// the lower half (bits 12..0, 15..0), each exactly as the one-value form.
+__device__ __forceinline__ uint32_t sr_half2(float hi, float lo, uint32_t r_hi, uint32_t r_lo) {
+    const uint32_t draw = ((r_hi >> 19) << 16) | (r_lo >> 19);
+    uint32_t d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(draw));
+    return d;
+}
+__device__ __forceinline__ uint32_t sr_bf162(float hi, float lo, uint32_t r_hi, uint32_t r_lo) {
+    const uint32_t draw = (r_hi & 0xFFFF0000u) | (r_lo >> 16);
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(draw));
+    return d;
+}
 __device__ __forceinline__ __half sr_half(float x, uint32_t r) {
-    const float ax = fabsf(x);
-    if (!(ax < 65504.0f)) return __float2half_rn(x);
-    const uint32_t b = __float_as_uint(x);
-    if (ax < 0x1p-24f) {
-        const bool away = __fmul_rn((float)(r >> 8), 0x1p-48f) < ax;
-        return __ushort_as_half((unsigned short)(((b >> 16) & 0x8000u) | (away ? 1u : 0u)));
-    }
-    const int d = max(13, 126 - (int)((b >> 23) & 0xFFu));
-    // clear the dropped bits: after a carry into the exponent the FP16 ulp
-    // below 2^-14 stays 2^-24, so the leftover bits would not all drop
-    const uint32_t kept = (b + (r >> (32 - d))) & ~((1u << d) - 1u);
-    return __float2half_rz(__uint_as_float(kept));
+    return __ushort_as_half((unsigned short)(sr_half2(0.0f, x, 0u, r) & 0xFFFFu));
 }
 __device__ __forceinline__ __nv_bfloat16 sr_bf16(float x, uint32_t r) {
-    if (!(fabsf(x) < 3.0e38f)) return __float2bfloat16_rn(x);
-    return __ushort_as_bfloat16((unsigned short)((__float_as_uint(x) + (r >> 16)) >> 16));
+    return __ushort_as_bfloat16((unsigned short)(sr_bf162(0.0f, x, 0u, r) & 0xFFFFu));
 }
 
 template <class S> struct Codec;

@@ -548,13 +548,6 @@ __device__ __forceinline__ uint32_t pack_rne(float lo, float hi) {
     return r;
 }
 
-template <class S>
-__device__ __forceinline__ uint32_t bits16(S v) {
-    unsigned short u;
-    memcpy(&u, &v, 2);
-    return u;
-}
-
 // Encoded 16-bit pair words for the nine directions: word i holds direction i
 // of node a (low half) and node b (high half). A node with keep = false
 // contributes +0.
@@ -570,15 +563,21 @@ __device__ __forceinline__ void encode_pair(const Step<S> &a, uint32_t n, const 
             w[i] = pack_rne<S>(ka ? lo : 0.0f, kb ? hi : 0.0f);
         }
     } else {
+        // one packed stochastic conversion per direction: node a in the low
+        // half, node b in the high half, each with its own draw (a solid
+        // node's lane converts +0, which no draw changes)
         const uint32_t sk = step_key(a.seed, (uint32_t)(*a.tctr + a.toff));
         const uint32_t nka = node_key(sk, n), nkb = node_key(sk, n + 1);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             float lo, hi;
             up2(g[i], lo, hi);
-            const uint32_t ea = ka ? bits16(Codec<S>::enc(lo, true, pop_rand(nka, i))) : 0u;
-            const uint32_t eb = kb ? bits16(Codec<S>::enc(hi, true, pop_rand(nkb, i))) : 0u;
-            w[i] = ea | (eb << 16);
+            lo = ka ? lo : 0.0f;
+            hi = kb ? hi : 0.0f;
+            if constexpr (std::is_same<S, __half>::value)
+                w[i] = sr_half2(hi, lo, pop_rand(nkb, i), pop_rand(nka, i));
+            else
+                w[i] = sr_bf162(hi, lo, pop_rand(nkb, i), pop_rand(nka, i));
         }
     }
 }
