@@ -420,7 +420,9 @@ def variants(args, mask, torch, world):
                      ("f32_collision_nptl_64x4", dict(storage="f32", layout="collision", tile=(64, 4))),
                      ("f32_stream_npol_32x8", dict(storage="f32", algo="npol", tile=(32, 8))),
                      ("f32_bundle_npol_64x4", dict(storage="f32", algo="npol", layout="bundle", tile=(64, 4))),
-                     ("f32_bundle_nsol_32x8", dict(storage="f32", algo="nsol", layout="bundle", tile=(32, 8))),
+                     ("f32_bundle_nsol_64x4", dict(storage="f32", algo="nsol", layout="bundle", tile=(64, 4))),
+                     ("f32_bundle_nsol_64x4_no_tma", dict(storage="f32", algo="nsol", layout="bundle", tile=(64, 4),
+                                                          flags=0x40)),
                      ("f32_bundle_aa_64x2", dict(storage="f32", algo="aa", layout="bundle", tile=(64, 2))),
                      ("f16s_rne_bundle_nptl_32x8", dict(storage="f16s", layout="bundle", tile=(32, 8))),
                      ("f16s_rne_bundle_nptl_32x8_one_node_per_thread",

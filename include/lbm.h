@@ -122,6 +122,11 @@ typedef enum {
                                     the layout is bundle and tile_x is even: two
                                     adjacent nodes per thread with packed FP32
                                     arithmetic; the results are bit-identical) */
+#define LBM_FLAG_NO_TMA 0x40u  /* NSOL, F32 storage: stage each tile with per-thread loads
+                                  (default when the layout is stream or bundle, nx and
+                                  tile_x are multiples of 4 and the tile's rows fit one
+                                  tensor copy: one tensor-memory-access copy of the tile's
+                                  populations into shared memory per block; bit-identical) */
 
 typedef struct lbm_params {
     int32_t nx, ny;          /* lattice size; nx*ny < 2^32 */
@@ -203,7 +208,9 @@ typedef struct lbm_info {
     int64_t steps;                 /* updates done since lbm_init */
     int32_t tile_x, tile_y;        /* tile used (LPTL: block size, 1) */
     int32_t aux;                   /* lbm_get_info: L2 prefetch distance (LPTL: nodes, NPTL
-                                      and AA: rows; 0 = off); lbm3_get_info: see there */
+                                      and AA: rows; 0 = off); NSOL: 1 when tiles are staged
+                                      by tensor copies (LBM_FLAG_NO_TMA); lbm3_get_info: see
+                                      there */
     double bytes_per_update;       /* algorithmic DRAM bytes of one update */
     size_t workspace_bytes;
 } lbm_info;

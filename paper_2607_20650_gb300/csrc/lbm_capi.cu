@@ -1,6 +1,7 @@
 // C ABI of liblbm.so (declared in include/lbm.h): parameter checks, the
 // workspace layout, update scheduling with cached CUDA graphs, host-side
 // layout conversion for checkpoints, and the FP64 reductions.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -210,6 +211,51 @@ static uint32_t prefetch_distance(const lbm_params *p, int64_t N, size_t elem, i
     return rows < p->ny ? (uint32_t)rows : 0;
 }
 
+// NSOL with FP32 storage stages each tile by one tensor copy (TMA) when the
+// tile's rows are whole 16-byte units in a tensor the copy can describe:
+// stream layout as a (nx, ny, 9) tensor, box (tx, ty, 9); bundle layout as
+// (3 nx, ny, 3), box (3 tx, ty, 3). The copy's x coordinate (x0 or 3 x0) times
+// 4 bytes is then a multiple of 16 for every tile, the row strides are
+// multiples of 16 bytes, and tiles past the lattice edge read zeros. The
+// encoder is the driver's, reached through the runtime; without it (or on any
+// failure) the kernel stages with per-thread loads.
+static void setup_tma(const lbm_params *p, const Plan &pl, HostArgs *h) {
+    h->tma = 0;
+    if (p->algo != LBM_NSOL || p->storage != LBM_F32 || (p->flags & LBM_FLAG_NO_TMA)) return;
+    if (p->layout != LBM_LAYOUT_STREAM && p->layout != LBM_LAYOUT_BUNDLE) return;
+    const bool bundle = p->layout == LBM_LAYOUT_BUNDLE;
+    const int64_t row = bundle ? 3 * (int64_t)pl.tx : pl.tx;
+    if (pl.tx % 4 || p->nx % 4 || row > 256 || pl.ty > 256 || ((uintptr_t)h->pop[0]) % 16) return;
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            (void)cudaGetLastError();
+            fn = nullptr;
+        }
+        return (Encode)fn;
+    }();
+    if (!encode) return;
+    const cuuint64_t N = (cuuint64_t)pl.N, nx = (cuuint64_t)p->nx;
+    const cuuint64_t dims[3] = {bundle ? 3 * nx : nx, (cuuint64_t)p->ny, bundle ? 3u : 9u};
+    const cuuint64_t strides[2] = {dims[0] * 4, (bundle ? 3 * N : N) * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)row, (cuuint32_t)pl.ty, bundle ? 3u : 9u};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    static_assert(sizeof(CUtensorMap) == sizeof(TmaDesc), "tensor map size");
+    CUtensorMap m;
+    if (encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->pop[0], dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return;
+    memcpy(h->tmap.bytes, &m, sizeof(m));
+    h->tma = 1;
+}
+
 void lbm_fill_args(const lbm_params *p, const Plan &pl, char *ws, const Ops *ops, HostArgs *h) {
     memset(h, 0, sizeof(*h));
     h->nx = p->nx;
@@ -248,6 +294,7 @@ void lbm_fill_args(const lbm_params *p, const Plan &pl, char *ws, const Ops *ops
     h->mom = ws + pl.mom;
     h->err = (unsigned int *)(ws + pl.misc);
     h->tctr = (long long *)(ws + pl.misc + 64);
+    setup_tma(p, pl, h);
 }
 
 extern "C" lbm_status lbm_create(const lbm_params *p, const uint8_t *mask_host, void *d_workspace,
@@ -429,6 +476,8 @@ static lbm_status check_err(lbm_lattice *L) {
     CK(cudaMemcpy(&flag, L->err, sizeof(flag), cudaMemcpyDeviceToHost));
     if (flag) {
         CK(cudaMemset(L->err, 0, sizeof(unsigned int)));
+        if (flag & 2u)
+            return lbm_fail(LBM_ECUDA, "a tile's tensor copy did not complete within the wait limit");
         return lbm_fail(LBM_EDIVERGED, "non-finite density after %lld updates", (long long)L->steps);
     }
     return LBM_OK;
@@ -736,7 +785,7 @@ extern "C" lbm_status lbm_get_info(lbm_lattice *L, lbm_info *out) {
     if (L->pl.halo_grid) bytes += 2.0 * (double)L->pl.halo_parity_elems * elem;  // buffer grid read + write
     out->bytes_per_update = bytes;
     out->workspace_bytes = L->pl.total;
-    out->aux = (int32_t)L->h.pf;
+    out->aux = L->p.algo == LBM_NSOL ? (int32_t)L->h.tma : (int32_t)L->h.pf;
     return LBM_OK;
 }
 

@@ -8,6 +8,12 @@
 
 namespace lbm {
 
+// An opaque tensor-map descriptor for the tensor copies (the 128-byte,
+// 64-byte aligned object the driver encodes), passed to kernels by value.
+struct alignas(64) TmaDesc {
+    unsigned char bytes[128];
+};
+
 // Everything a kernel launch needs, in host types.
 struct HostArgs {
     int nx, ny;
@@ -28,6 +34,8 @@ struct HostArgs {
     void *mom;                 // 3N compute-type values
     unsigned int *err;
     long long *tctr;           // device update counter (stochastic rounding keys)
+    int tma;                   // NSOL, FP32: the tile is staged by one tensor copy (tmap)
+    TmaDesc tmap;
 };
 
 // One update: which lattice is the source, the halo parity that is read,

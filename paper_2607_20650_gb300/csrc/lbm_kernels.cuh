@@ -904,6 +904,39 @@ __global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : 4) k_npo
                     (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u));
 }
 
+// Tensor copy (TMA) of a tile into shared memory with an mbarrier that
+// counts the bytes: one thread initialises the barrier, announces the bytes
+// and issues the copy; every thread then waits on the barrier's phase 0 with
+// an iteration limit.
+constexpr int kTmaSpin = 1 << 20;
+
+__device__ __forceinline__ void tma_issue_3d(const TmaDesc *tm, void *dst, uint64_t *bar, int c0, int c1, int c2,
+                                             uint32_t bytes) {
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar), d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(d),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(b)
+        : "memory");
+}
+
+__device__ __forceinline__ bool tma_wait(uint64_t *bar) {
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int it = 0; it < kTmaSpin; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(b)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // ------------------------------------------------------------ NSOL
 // One lattice, swap streaming: populations are stored in opposite slots
 // (slot s of node x holds f*_{8-s}(x)). Tiles are staged in shared memory;
@@ -914,12 +947,25 @@ __global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : 4) k_npo
 // Two block barriers: after the staging (and the substitutions, read from
 // the lattice and the buffer grid), and after the exchanges.
 // smem_raw: 9 * tx * ty compute values.
-template <class S, int L>
+// TMA: the tile's populations arrive by one tensor copy (FP32 storage, stream
+// or bundle layout; tm is the kernel's tensor-map parameter) and keep the
+// bundle interleave in shared memory; otherwise every fluid node stages its
+// own nine values.
+template <class S, int L, bool TMA = false>
 __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int lx, int ly, int lane,
-                                          unsigned char *smem_raw) {
+                                          unsigned char *smem_raw, const TmaDesc *tm = nullptr) {
     using C = typename Codec<S>::C;
     const int T = a.tx * a.ty;
     C *sm = reinterpret_cast<C *>(smem_raw);
+    // slot of direction s of tile node t among the staged values
+    auto si = [T](int s, int t) { return (TMA && L == BUNDLE) ? (s / 3) * 3 * T + 3 * t + s % 3 : s * T + t; };
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + sizeof(C) * 9 * T);
+    if constexpr (TMA) {
+        if (lx == 0 && ly == 0)
+            tma_issue_3d(tm, sm, bar, L == BUNDLE ? 3 * bx * a.tx : bx * a.tx, by * a.ty, 0,
+                         (uint32_t)(sizeof(C) * 9 * T));
+        __syncthreads();   // the barrier is initialised before anyone waits on it
+    }
     const int nx = a.geo.nx, ny = a.geo.ny;
     const int x0 = bx * a.tx, y0 = by * a.ty;
     const int x1 = min(x0 + a.tx, nx) - 1, y1 = min(y0 + a.ty, ny) - 1;
@@ -937,9 +983,9 @@ __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int 
     const unsigned F = __ballot_sync(__activemask(), fluid);
     (void)F;
     const bool zero_fill = false;   // measured: NSOL is 2 % faster without the sector zero fill
-    if (fluid) {
+    if (!TMA && fluid) {
 #pragma unroll
-        for (int s = 0; s < 9; ++s) sm[s * T + tid] = ldp<S, L>(lat, a.N, n, s);
+        for (int s = 0; s < 9; ++s) sm[si(s, tid)] = ldp<S, L>(lat, a.N, n, s);
     }
     const C dnb = (fluid && x == 0 && a.geo.bw == INLET_EQ_NEUMANN) ? neighbour_drho<S, L>(a, lat, n, 1) : C(0);
     // Substitutions for pulls the in-tile exchange does not cover, read
@@ -983,7 +1029,17 @@ __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int 
                 fix[i] = halo_read(a, xs, ys, j, bx);
         }
     }
-    __syncthreads();
+    if constexpr (TMA) {
+        bool done = tma_wait(bar);
+        if (!__syncthreads_and(done)) {
+            // let a late copy land before the block's shared memory is released
+            if (!done) done = tma_wait(bar);
+            if (lx == 0 && ly == 0) atomicOr(a.err, 2u);
+            return;
+        }
+    } else {
+        __syncthreads();
+    }
     if (fluid) {
         // partner x + c_i fluid <=> the pull of direction 8-i from it does not bounce
 #pragma unroll
@@ -992,9 +1048,9 @@ __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int 
             if (px >= 0 && px < a.tx && py < a.ty && x0 + px <= x1 && y0 + py <= y1) {
                 const int pt = py * a.tx + px;
                 if (!((lk >> link_bit(opp(i))) & 1u)) {
-                    C t = sm[opp(i) * T + tid];
-                    sm[opp(i) * T + tid] = sm[i * T + pt];
-                    sm[i * T + pt] = t;
+                    C t = sm[si(opp(i), tid)];
+                    sm[si(opp(i), tid)] = sm[si(i, pt)];
+                    sm[si(i, pt)] = t;
                 }
             }
         }
@@ -1003,7 +1059,7 @@ __device__ __forceinline__ void nsol_tile(const Step<S> &a, int bx, int by, int 
     if (fluid) {
         C g[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = ((fixmask >> i) & 1u) ? fix[i] : sm[i * T + tid];
+        for (int i = 0; i < 9; ++i) g[i] = ((fixmask >> i) & 1u) ? fix[i] : sm[si(i, tid)];
         S e[9];
         collide_encode(a, (uint32_t)x, n, g, e, dnb);
 #pragma unroll
@@ -1023,6 +1079,16 @@ __global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : LBM_NSOL
     extern __shared__ __align__(16) unsigned char smem_raw[];
     nsol_tile<S, L>(a, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y,
                     (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u), smem_raw);
+}
+
+// NSOL with the tile staged by a tensor copy; shared memory: the tile's
+// 9 T values, then the copy's mbarrier.
+template <class S, int L>
+__global__ void __launch_bounds__(kMaxTileThreads, LBM_NSOL_MINB)
+    k_nsol_tma(const Step<S> a, const __grid_constant__ TmaDesc tm) {
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    nsol_tile<S, L, true>(a, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y,
+                          (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u), smem_tma, &tm);
 }
 
 // ------------------------------------------------------------ AA pattern
@@ -1588,6 +1654,12 @@ cudaError_t step_layout(const HostArgs &h, const Step<S> &a, int phase, cudaStre
         case NPOL: k_npol<S, L><<<grid, tile, 0, st>>>(a); break;
         case NSOL: {
             const size_t sm = sizeof(C) * 9 * h.tile_x * h.tile_y;
+            if constexpr (std::is_same<S, float>::value && L != COLLISION) {
+                if (h.tma) {
+                    k_nsol_tma<S, L><<<grid, tile, sm + 16, st>>>(a, h.tmap);
+                    break;
+                }
+            }
             k_nsol<S, L><<<grid, tile, sm, st>>>(a);
             break;
         }

@@ -27,6 +27,7 @@ LBM_FLAG_NO_STAGING = 4
 LBM_FLAG_WIDE_OFFSETS = 8
 LBM_FLAG_NO_PREFETCH = 16
 LBM_FLAG_NO_PAIRS = 32
+LBM_FLAG_NO_TMA = 64
 LBM_AUTO = -1
 
 
@@ -297,6 +298,7 @@ def lbm_get_info(h) -> dict:
     i = lbm_info()
     _check(load().lbm_get_info(h, ctypes.byref(i)), "lbm_get_info")
     out = {f: getattr(i, f) for f, _ in lbm_info._fields_ if f != "aux"}
+    out["aux"] = int(i.aux)   # NSOL: 1 = tiles staged by tensor copies; else the prefetch distance
     out["prefetch_distance"] = int(i.aux)
     return out
 
