@@ -219,13 +219,8 @@ static uint32_t prefetch_distance(const lbm_params *p, int64_t N, size_t elem, i
 // multiples of 16 bytes, and tiles past the lattice edge read zeros. The
 // encoder is the driver's, reached through the runtime; without it (or on any
 // failure) the kernel stages with per-thread loads.
-static void setup_tma(const lbm_params *p, const Plan &pl, HostArgs *h) {
-    h->tma = 0;
-    if (p->algo != LBM_NSOL || p->storage != LBM_F32 || (p->flags & LBM_FLAG_NO_TMA)) return;
-    if (p->layout != LBM_LAYOUT_STREAM && p->layout != LBM_LAYOUT_BUNDLE) return;
-    const bool bundle = p->layout == LBM_LAYOUT_BUNDLE;
-    const int64_t row = bundle ? 3 * (int64_t)pl.tx : pl.tx;
-    if (pl.tx % 4 || p->nx % 4 || row > 256 || pl.ty > 256 || ((uintptr_t)h->pop[0]) % 16) return;
+bool lbm_encode_f32_tensor_map(TmaDesc *out, int rank, void *base, const uint64_t *dims,
+                                const uint64_t *strides, const uint32_t *box) {
     using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -240,20 +235,37 @@ static void setup_tma(const lbm_params *p, const Plan &pl, HostArgs *h) {
         }
         return (Encode)fn;
     }();
-    if (!encode) return;
-    const cuuint64_t N = (cuuint64_t)pl.N, nx = (cuuint64_t)p->nx;
-    const cuuint64_t dims[3] = {bundle ? 3 * nx : nx, (cuuint64_t)p->ny, bundle ? 3u : 9u};
-    const cuuint64_t strides[2] = {dims[0] * 4, (bundle ? 3 * N : N) * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)row, (cuuint32_t)pl.ty, bundle ? 3u : 9u};
-    const cuuint32_t estr[3] = {1, 1, 1};
+    if (!encode || rank < 1 || rank > 5 || ((uintptr_t)base) % 16) return false;
+    cuuint64_t d[5], st[4];
+    cuuint32_t bx[5], es[5];
+    for (int k = 0; k < rank; ++k) {
+        d[k] = dims[k];
+        bx[k] = box[k];
+        es[k] = 1;
+        if (k + 1 < rank) st[k] = strides[k];
+    }
     static_assert(sizeof(CUtensorMap) == sizeof(TmaDesc), "tensor map size");
     CUtensorMap m;
-    if (encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->pop[0], dims, strides, box, estr,
+    if (encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, base, d, st, bx, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return;
-    memcpy(h->tmap.bytes, &m, sizeof(m));
-    h->tma = 1;
+        return false;
+    memcpy(out->bytes, &m, sizeof(m));
+    return true;
+}
+
+static void setup_tma(const lbm_params *p, const Plan &pl, HostArgs *h) {
+    h->tma = 0;
+    if (p->algo != LBM_NSOL || p->storage != LBM_F32 || (p->flags & LBM_FLAG_NO_TMA)) return;
+    if (p->layout != LBM_LAYOUT_STREAM && p->layout != LBM_LAYOUT_BUNDLE) return;
+    const bool bundle = p->layout == LBM_LAYOUT_BUNDLE;
+    const int64_t row = bundle ? 3 * (int64_t)pl.tx : pl.tx;
+    if (pl.tx % 4 || p->nx % 4 || row > 256 || pl.ty > 256) return;
+    const uint64_t N = (uint64_t)pl.N, nx = (uint64_t)p->nx;
+    const uint64_t dims[3] = {bundle ? 3 * nx : nx, (uint64_t)p->ny, bundle ? 3u : 9u};
+    const uint64_t strides[2] = {dims[0] * 4, (bundle ? 3 * N : N) * 4};
+    const uint32_t box[3] = {(uint32_t)row, (uint32_t)pl.ty, bundle ? 3u : 9u};
+    h->tma = lbm_encode_f32_tensor_map(&h->tmap, 3, h->pop[0], dims, strides, box) ? 1 : 0;
 }
 
 void lbm_fill_args(const lbm_params *p, const Plan &pl, char *ws, const Ops *ops, HostArgs *h) {

@@ -904,49 +904,6 @@ __global__ void __launch_bounds__(kMaxTileThreads, sizeof(S) == 8 ? 1 : 4) k_npo
                     (int)((threadIdx.y * blockDim.x + threadIdx.x) & 31u));
 }
 
-// Tensor copy (TMA) of a tile into shared memory with an mbarrier that
-// counts the bytes: one thread initialises the barrier, announces the bytes
-// and issues the copy; every thread then waits on the barrier's phase 0 with
-// an iteration limit.
-constexpr int kTmaSpin = 1 << 20;
-
-__device__ __forceinline__ void tma_issue_3d(const TmaDesc *tm, void *dst, uint64_t *bar, int c0, int c1, int c2,
-                                             uint32_t bytes) {
-    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar), d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(d),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(b)
-        : "memory");
-}
-
-__device__ __forceinline__ bool tma_wait(uint64_t *bar) {
-    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
-    for (int it = 0; it < kTmaSpin; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(ok)
-            : "r"(b)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-// ------------------------------------------------------------ NSOL
-// One lattice, swap streaming: populations are stored in opposite slots
-// (slot s of node x holds f*_{8-s}(x)). Tiles are staged in shared memory;
-// for each of the four positive directions i, slot 8-i of x is exchanged
-// with slot i of x + c_i when both are fluid (no exchange = bounce-back).
-// Values that enter through domain edges or from other tiles (buffer grid)
-// are substituted afterwards.
-// Two block barriers: after the staging (and the substitutions, read from
-// the lattice and the buffer grid), and after the exchanges.
-// smem_raw: 9 * tx * ty compute values.
 // TMA: the tile's populations arrive by one tensor copy (FP32 storage, stream
 // or bundle layout; tm is the kernel's tensor-map parameter) and keep the
 // bundle interleave in shared memory; otherwise every fluid node stages its
