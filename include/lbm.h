@@ -387,7 +387,7 @@ typedef struct lbm3_params {
                                                   or LBM_AA */
     uint64_t seed;
     int32_t tile_x, tile_y, tile_z;
-    uint32_t flags;          /* LBM_FLAG_NO_GRAPH, LBM_FLAG_WIDE_OFFSETS */
+    uint32_t flags;          /* LBM_FLAG_NO_GRAPH, LBM_FLAG_WIDE_OFFSETS, LBM_FLAG_NO_PAIRS */
     int32_t bc_x_east;       /* east x face after an inlet west face: LBM_BC_OUTFLOW_ZG,
                                 LBM_BC_WALL or LBM_BC_OUTLET_PRESSURE (ignored otherwise:
                                 both x faces are bc_x) */
@@ -424,8 +424,11 @@ lbm_status lbm3_mass(lbm3_lattice *L, double *out);
  * Synchronous; AA: after an even number of updates only. */
 lbm_status lbm3_force(lbm3_lattice *L, const uint8_t *d_body, double out[3]);
 /* cells, fluid_cells, steps, tile (tile_y = tile_y * tile_z), bytes per
- * update; aux = 1 when pulls use 64-bit addressing (large lattices or
- * LBM_FLAG_WIDE_OFFSETS), 0 with the 32-bit offset tables. */
+ * update; aux bit 0: pulls use 64-bit addressing (large lattices or
+ * LBM_FLAG_WIDE_OFFSETS; clear with the 32-bit offset tables); bit 1: LPTL
+ * or NPTL with 16-bit storage update two x-adjacent nodes per thread
+ * (stream or bundle layout, nx and tile_x even, 32-bit offset tables, no
+ * LBM_FLAG_NO_PAIRS; bit-identical to one node per thread). */
 lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out);
 void lbm3_destroy(lbm3_lattice *L);
 int64_t lbm3_layout_index(int32_t layout, int64_t N, int64_t n, int32_t i);

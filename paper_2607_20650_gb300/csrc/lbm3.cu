@@ -479,6 +479,11 @@ extern "C" lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out) {
     if (L->pl.halo_parity)   // NPOL/NSOL buffer grid: one parity read, the other written
         out->bytes_per_update += 2.0 * (double)L->pl.halo_parity * (double)L->pl.elem;
     out->workspace_bytes = L->pl.total;
-    out->aux = L->off32 ? 0 : 1;   // 1: the 64-bit addressing path
+    // bit 0: the 64-bit addressing path; bit 1: two nodes per thread (16-bit storage)
+    const bool pairs = (L->p.storage == LBM_F16S || L->p.storage == LBM_BF16S) && L->off32 &&
+                       (L->p.layout == LBM_LAYOUT_BUNDLE || L->p.layout == LBM_LAYOUT_STREAM) &&
+                       L->p.nx % 2 == 0 && !(L->p.flags & LBM_FLAG_NO_PAIRS) &&
+                       (L->p.algo == LBM_LPTL || (L->p.algo == LBM_NPTL && L->pl.tx % 2 == 0));
+    out->aux = (L->off32 ? 0 : 1) | (pairs ? 2 : 0);
     return LBM_OK;
 }

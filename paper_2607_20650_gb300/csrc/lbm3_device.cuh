@@ -120,5 +120,92 @@ __device__ __forceinline__ void collide3(const Consts3<C> &k, C *g, C &drho, C &
     }
 }
 
+// The FP32 constants of Consts3<float>, each duplicated into both lanes of a
+// packed pair, with the signs collide3_2 folds in.
+struct Consts3x2 {
+    f2 nomega, nw[3], nwl[3], kw[3];
+    f2 hf[3], f[3], cF[Q];
+    f2 c45, c3, c9, cm3, cm15, cm1;
+};
+
+inline Consts3x2 make_consts3x2(const Consts3<float> &k) {
+    Consts3x2 q;
+    q.nomega = dup2(-k.omega);
+    const float w[3] = {k.w0, k.w1, k.w2}, wl[3] = {k.wl0, k.wl1, k.wl2}, kw[3] = {k.kw0, k.kw1, k.kw2};
+    for (int s = 0; s < 3; ++s) {
+        q.nw[s] = dup2(-w[s]);
+        q.nwl[s] = dup2(-wl[s]);
+        q.kw[s] = dup2(kw[s]);
+        q.hf[s] = dup2(k.hf[s]);
+        q.f[s] = dup2(k.f[s]);
+    }
+    for (int i = 0; i < Q; ++i) q.cF[i] = dup2(k.cF[i]);
+    q.c45 = dup2(4.5f);
+    q.c3 = dup2(3.0f);
+    q.c9 = dup2(9.0f);
+    q.cm3 = dup2(-3.0f);
+    q.cm15 = dup2(-1.5f);
+    q.cm1 = dup2(-1.0f);
+    return q;
+}
+
+// collide3 on two nodes at once (packed FP32 pairs, fma.rn.f32x2 and
+// friends): the same rounded operations lane by lane, so each lane equals
+// the scalar collide3 bit for bit. The relaxation is written without
+// negated operands, t' = fma(-w, P, g) = -fma(w, P, -g) and o =
+// fma(-omega, t'', g), which IEEE rounding makes exact; a negative first
+// term of a sum is an exact product with -1.
+__device__ __forceinline__ void collide3_2(const Consts3x2 &q, int force, f2 *g, f2 &drho, f2 &ux, f2 &uy,
+                                           f2 &uz) {
+    f2 r = g[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) r = add2(r, g[i]);
+    drho = r;
+    f2 j[3];
+    bool started[3] = {false, false, false};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int c[3] = {cx(i), cy(i), cz(i)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!c[a]) continue;
+            if (!started[a]) {
+                j[a] = c[a] > 0 ? g[i] : mul2(g[i], q.cm1);
+                started[a] = true;
+            } else {
+                j[a] = c[a] > 0 ? add2(j[a], g[i]) : sub2(j[a], g[i]);
+            }
+        }
+    }
+    ux = add2(j[0], q.hf[0]);
+    uy = add2(j[1], q.hf[1]);
+    uz = add2(j[2], q.hf[2]);
+    const f2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
+    const f2 base = fma2(q.cm15, usq, drho);
+    const f2 m3uF = mul2(q.cm3, fma2(ux, q.f[0], fma2(uy, q.f[1], mul2(uz, q.f[2]))));
+    const f2 u[3] = {ux, uy, uz};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int c[3] = {cx(i), cy(i), cz(i)};
+        f2 cu = 0;
+        bool any = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!c[a]) continue;
+            if (!any) cu = c[a] > 0 ? u[a] : mul2(u[a], q.cm1);
+            else cu = c[a] > 0 ? add2(cu, u[a]) : sub2(cu, u[a]);
+            any = true;
+        }
+        const int s = sq(i);
+        const f2 P = any ? fma2(cu, fma2(q.c45, cu, q.c3), base) : base;
+        f2 t = fma2(q.nw[s], P, g[i]);
+        t = fma2(q.nwl[s], P, t);
+        f2 o = fma2(q.nomega, t, g[i]);
+        if (force && any) o = fma2(q.kw[s], fma2(q.cF[i], fma2(q.c9, cu, q.c3), m3uF), o);
+        else if (force) o = fma2(q.kw[0], m3uF, o);
+        g[i] = o;
+    }
+}
+
 }  // namespace d3
 }  // namespace lbm

@@ -15,6 +15,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lbm.h"
 #include "lbm3_device.cuh"
 #include "lbm_internal.h"
@@ -85,6 +87,7 @@ struct Step3 {
     // Zou-He: U_x/3, (U_x + U_y)/6, (U_x - U_y)/6, (U_x + U_z)/6, (U_x - U_z)/6,
     // -U_y/3, -U_z/3, rho_out - 1
     C zh[8];
+    Consts3x2 k2;   // FP32 arithmetic: k duplicated for the packed node pairs
 };
 
 // Storage slot of population i in the stored state.
@@ -337,6 +340,138 @@ __global__ void __launch_bounds__(512, sizeof(S) == 8 ? 2 : 3) k3_step(const Ste
         if (x >= (uint32_t)a.g.nx || y >= (uint32_t)a.g.ny || z >= (uint32_t)a.g.nz) return;
     }
     step3_node<S, L, OFF32>(a, x, y, z);
+}
+
+// Node pairs: two x-adjacent nodes (x even) per thread for 16-bit storage,
+// each pulled as step3_node pulls it, the collision on packed FP32 pairs
+// (collide3_2, bit-identical to collide3 lane by lane) and two values rounded
+// per conversion, node a in the low half and node b in the high half of each
+// 32-bit word. A solid partner's lane holds +0, which is what a solid node
+// stores, so its words are written whole.
+template <class S>
+__device__ __forceinline__ uint32_t pack3_rne(float lo, float hi) {
+    uint32_t r;
+    if constexpr (std::is_same<S, __half>::value)
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    else
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// The words of nodes n, n + 1 (n even, N even): stream layout one word per
+// direction; bundle layout one word per single-direction bundle and three per
+// three-direction bundle (the six values a0 a1 a2 b0 b1 b2 are adjacent).
+template <class S, int L>
+__device__ __forceinline__ void store3_pair(S *dst, uint32_t N, uint32_t n, const uint32_t *w) {
+    if (L == STREAM) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) *reinterpret_cast<uint32_t *>(dst + (uint32_t)i * N + n) = w[i];
+        return;
+    }
+#pragma unroll
+    for (int f = 0; f < Q; ++f) {
+        if (bundle_first(f) != f) continue;
+        if (bundle_size(f) == 1) {
+            *reinterpret_cast<uint32_t *>(dst + (uint32_t)f * N + n) = w[f];
+        } else {
+            uint32_t *q = reinterpret_cast<uint32_t *>(dst + (uint32_t)f * N + 3u * n);
+            q[0] = (w[f] & 0xFFFFu) | (w[f + 1] << 16);
+            q[1] = (w[f + 2] & 0xFFFFu) | (w[f] & 0xFFFF0000u);
+            q[2] = (w[f + 1] >> 16) | (w[f + 2] & 0xFFFF0000u);
+        }
+    }
+}
+
+template <class S, int L>
+__device__ __forceinline__ void step3_pair(const Step3<S> &a, uint32_t x, uint32_t y, uint32_t z, uint32_t n) {
+    const uint2 lk2 = *reinterpret_cast<const uint2 *>(a.links + n);   // n even: 8-byte aligned
+    const bool fa = lk2.x != SOLID, fb = lk2.y != SOLID;
+    if (!fa && !fb) return;
+    float ga[Q], gb[Q];
+    if (fa) {
+        pull3<S, L, true>(a, x, y, z, n, lk2.x, ga);
+        faces3(a, x, ga);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) ga[i] = 0.0f;
+    }
+    if (fb) {
+        pull3<S, L, true>(a, x + 1u, y, z, n + 1u, lk2.y, gb);
+        faces3(a, x + 1u, gb);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) gb[i] = 0.0f;
+    }
+    f2 g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = pk2(ga[i], gb[i]);
+    f2 drho, ux, uy, uz;
+    collide3_2(a.k2, a.k.force, g, drho, ux, uy, uz);
+    float da, db;
+    up2(drho, da, db);
+    if ((fa && !isfinite(da)) || (fb && !isfinite(db))) atomicOr(a.err, 1u);
+    if (a.mom) {
+        float r[2], u[3][2];
+        up2(add2(dup2(1.0f), drho), r[0], r[1]);
+        up2(ux, u[0][0], u[0][1]);
+        up2(uy, u[1][0], u[1][1]);
+        up2(uz, u[2][0], u[2][1]);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (!(k ? fb : fa)) continue;
+            a.mom[n + k] = r[k];
+            a.mom[a.N + n + k] = u[0][k];
+            a.mom[2 * (size_t)a.N + n + k] = u[1][k];
+            a.mom[3 * (size_t)a.N + n + k] = u[2][k];
+        }
+    }
+    uint32_t w[Q];
+    if (!a.sr) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float lo, hi;
+            up2(g[i], lo, hi);
+            w[i] = pack3_rne<S>(fa ? lo : 0.0f, fb ? hi : 0.0f);
+        }
+    } else {
+        const uint32_t sk = step_key(a.seed, (uint32_t)(*a.tctr + a.toff));
+        const uint32_t nka = node_key(sk, n), nkb = node_key(sk, n + 1u);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float lo, hi;
+            up2(g[i], lo, hi);
+            lo = fa ? lo : 0.0f;
+            hi = fb ? hi : 0.0f;
+            if constexpr (std::is_same<S, __half>::value)
+                w[i] = sr_half2(hi, lo, pop_rand(nkb, i), pop_rand(nka, i));
+            else
+                w[i] = sr_bf162(hi, lo, pop_rand(nkb, i), pop_rand(nka, i));
+        }
+    }
+    store3_pair<S, L>(a.dst, a.N, n, w);
+}
+
+#ifndef LBM3_PAIR_MINB
+#define LBM3_PAIR_MINB 4
+#endif
+// LINEAR: pairs over n (LPTL, 2 x blockDim nodes per block); otherwise tiles
+// of tx x ty x tz nodes with blocks of tx/2 x ty x tz threads (NPTL).
+template <class S, int L, bool LINEAR>
+__global__ void __launch_bounds__(256, LBM3_PAIR_MINB) k3_step_pair(const Step3<S> a) {
+    uint32_t x, y, z, n;
+    if (LINEAR) {
+        const uint64_t n64 = 2ull * ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x);
+        if (n64 >= a.N) return;
+        n = (uint32_t)n64;
+        node_xyz(a, n, x, y, z);
+    } else {
+        x = blockIdx.x * a.tx + 2u * threadIdx.x;
+        y = blockIdx.y * a.ty + threadIdx.y;
+        z = blockIdx.z * a.tz + threadIdx.z;
+        if (x >= (uint32_t)a.g.nx || y >= (uint32_t)a.g.ny || z >= (uint32_t)a.g.nz) return;
+        n = (z * (uint32_t)a.g.ny + y) * (uint32_t)a.g.nx + x;
+    }
+    step3_pair<S, L>(a, x, y, z, n);
 }
 
 // AA pattern on one array. Even updates (PHASE 0) start from the canonical

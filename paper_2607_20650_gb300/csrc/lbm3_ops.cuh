@@ -97,7 +97,32 @@ Step3<S> make3(const lbm3_lattice *L, int src, int toff, int mom) {
     a.nxy_magic = magic3((uint64_t)p.nx * (uint64_t)p.ny);
     // measured: +7 % for the stream layout on a porous box, -3 % for the bundle layout
     a.zero_fill = (p.layout != LBM_LAYOUT_BUNDLE && (p.algo == LBM_LPTL || L->pl.tx % 32 == 0)) ? 1 : 0;
+    if constexpr (std::is_same<C, float>::value) a.k2 = make_consts3x2(a.k);
     return a;
+}
+
+// Node pairs (k3_step_pair): 16-bit storage, stream or bundle layout, the
+// 32-bit offset tables, nx even (and tile_x even for NPTL), unless
+// LBM_FLAG_NO_PAIRS asks for one node per thread.
+template <class S>
+bool pairs3_ok(const lbm3_lattice *L) {
+    const lbm3_params &p = L->p;
+    return sizeof(S) == 2 && L->off32 && (p.layout == LBM_LAYOUT_BUNDLE || p.layout == LBM_LAYOUT_STREAM) &&
+           p.nx % 2 == 0 && !(p.flags & LBM_FLAG_NO_PAIRS) && (p.algo == LBM_LPTL || L->pl.tx % 2 == 0);
+}
+
+template <class S, bool LINEAR>
+void launch_pair3(const lbm3_lattice *L, const Step3<S> &a, cudaStream_t st) {
+    dim3 g, b;
+    if (LINEAR) {
+        b = dim3(128);
+        g = dim3((unsigned)((L->pl.N / 2 + 127) / 128));
+    } else {
+        b = dim3(L->pl.tx / 2, L->pl.ty, L->pl.tz);
+        g = dim3(L->pl.ntx, L->pl.nty, L->pl.ntz);
+    }
+    if (L->p.layout == LBM_LAYOUT_STREAM) k3_step_pair<S, STREAM, LINEAR><<<g, b, 0, st>>>(a);
+    else k3_step_pair<S, BUNDLE, LINEAR><<<g, b, 0, st>>>(a);
 }
 
 template <class S, bool LINEAR, bool OFF32>
@@ -190,6 +215,11 @@ cudaError_t step3(const lbm3_lattice *L, cudaStream_t st, int src, int toff, int
     } else if (L->p.algo == LBM_AA) {
         if (src == 0) launch_aa<S, 0>(L, a, st);
         else launch_aa<S, 1>(L, a, st);
+    } else if ((L->p.algo == LBM_LPTL || L->p.algo == LBM_NPTL) && pairs3_ok<S>(L)) {
+        if constexpr (sizeof(S) == 2) {
+            if (L->p.algo == LBM_LPTL) launch_pair3<S, true>(L, a, st);
+            else launch_pair3<S, false>(L, a, st);
+        }
     } else if (L->p.algo == LBM_LPTL) {
         const dim3 g((unsigned)((L->pl.N + L->block_1d - 1) / L->block_1d)), b(L->block_1d);
         if (L->off32) launch3k<S, true, true>(L, a, g, b, st);

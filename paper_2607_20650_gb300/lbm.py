@@ -538,7 +538,8 @@ def lbm3_get_info(h) -> dict:
     i = lbm_info()
     _check(load().lbm3_get_info(h, ctypes.byref(i)), "lbm3_get_info")
     out = {f: getattr(i, f) for f, _ in lbm_info._fields_ if f != "aux"}
-    out["wide_addressing"] = bool(i.aux)
+    out["wide_addressing"] = bool(i.aux & 1)
+    out["node_pairs"] = bool(i.aux & 2)
     return out
 
 

@@ -757,3 +757,59 @@ def test_nsol_mass_and_force_match_oracle3():
     f_gpu, f_ref = lat.force(body), ref.force(spec.mask)
     assert np.max(np.abs(f_gpu - f_ref)) <= 1e-11 * np.max(np.abs(f_ref))
     lat.close()
+
+
+def _even_specs():
+    out = {}
+    nx, ny, nz = 36, 21, 13
+    out["porous"] = Spec3(nx, ny, nz, 0.7, G.porous_spheres(nx, ny, nz, 5, 2.0, 5.0, 0.25), (P, P, P),
+                          force=(1e-5, 2e-6, -1e-6))
+    nx, ny, nz = 44, 19, 11
+    out["duct"] = Spec3(nx, ny, nz, 0.9, G.ball(nx, ny, nz, 12.0, 9.0, 5.0, 3.5), (P, W, W),
+                        force=(1e-5, 0.0, 0.0), seed=2)
+    nx, ny, nz = 34, 5, 3
+    m = np.zeros((nz, ny, nx), np.uint8)
+    m[1, 2, 7] = 1
+    m[1, 2, 8] = 1
+    out["ragged"] = Spec3(nx, ny, nz, 0.6, m, (W, P, W), seed=3)
+    return out
+
+
+EVEN = _even_specs()
+
+
+@pytest.mark.parametrize("case", list(EVEN))
+@pytest.mark.parametrize("layout", ["bundle", "stream"])
+@pytest.mark.parametrize("storage,rounding", [("f16s", "rne"), ("f16s", "sr"), ("bf16s", "rne"), ("bf16s", "sr")])
+@pytest.mark.parametrize("algo,tile", [("lptl", (0, 0, 0)), ("nptl", (8, 4, 2)), ("nptl", (16, 2, 3))])
+def test_node_pairs_bit_identical3(case, layout, storage, rounding, algo, tile):
+    """D3Q19 with 16-bit storage: two x-adjacent nodes per thread with the
+    collision on packed FP32 pairs give the bits of one node per thread
+    (LBM_FLAG_NO_PAIRS), states and moments, on odd and even tiles, ragged
+    edges, walls and solid pairs."""
+    spec = EVEN[case]
+    kw = dict(layout=layout, algo=algo, storage=storage, rounding=rounding, seed=13, tile=tile)
+    a = spec.gpu(**kw)
+    b = spec.gpu(flags=lbm.LBM_FLAG_NO_PAIRS, **kw)
+    assert a.info()["node_pairs"] and not b.info()["node_pairs"]
+    a.step(29, moments=True).sync()
+    b.step(29, moments=True).sync()
+    assert np.array_equal(a.populations("f32"), b.populations("f32"))
+    assert all(np.array_equal(u, v) for u, v in zip(a.moments(), b.moments()))
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("algo", ["lptl", "nptl"])
+def test_node_pairs_with_inlet_outlet_faces3(algo):
+    """Pairs on the Zou-He channel (inlet, pressure outlet, walls; nx = 42):
+    bit-identical to one node per thread, FP16 with stochastic rounding."""
+    kw = dict(layout="bundle", algo=algo, storage="f16s", rounding="sr", seed=3, tile=(8, 2, 2))
+    _, a, _ = _zou_he3(**kw)
+    _, b, _ = _zou_he3(flags=lbm.LBM_FLAG_NO_PAIRS, **kw)
+    assert a.info()["node_pairs"]
+    a.step(40, moments=True).sync()
+    b.step(40, moments=True).sync()
+    assert np.array_equal(a.populations("f32"), b.populations("f32"))
+    a.close()
+    b.close()
