@@ -217,7 +217,7 @@ static uint32_t prefetch_distance(const lbm_params *p, int64_t N, size_t elem, i
 // (3 nx, ny, 3), box (3 tx, ty, 3). The copy's x coordinate (x0 or 3 x0) times
 // 4 bytes is then a multiple of 16 for every tile, the row strides are
 // multiples of 16 bytes, and tiles past the lattice edge read zeros. The
-// encoder is the driver's, reached through the runtime; without it (or on any
+// encoder is the CUDA driver's, reached through the runtime; without it (or on any
 // failure) the kernel stages with per-thread loads.
 bool lbm_encode_f32_tensor_map(TmaDesc *out, int rank, void *base, const uint64_t *dims,
                                 const uint64_t *strides, const uint32_t *box) {

@@ -47,7 +47,7 @@ struct lbm_lattice {
 lbm_status lbm_fail(lbm_status s, const char *fmt, ...);
 // Tensor map (TMA descriptor) of an FP32 tensor of `rank` dimensions (dims
 // innermost first, byte strides of dimensions 1 .. rank-1, copy box); false
-// when the driver's encoder is unavailable or rejects the description.
+// when the CUDA driver's encoder is unavailable or rejects the description.
 bool lbm_encode_f32_tensor_map(lbm::TmaDesc *out, int rank, void *base, const uint64_t *dims,
                                const uint64_t *strides, const uint32_t *box);
 lbm_status lbm_cuda_fail(cudaError_t e, const char *where);

@@ -9,7 +9,7 @@
 namespace lbm {
 
 // An opaque tensor-map descriptor for the tensor copies (the 128-byte,
-// 64-byte aligned object the driver encodes), passed to kernels by value.
+// 64-byte aligned object the CUDA driver encodes), passed to kernels by value.
 struct alignas(64) TmaDesc {
     unsigned char bytes[128];
 };
