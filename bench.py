@@ -520,6 +520,8 @@ def d3q19(args, torch):
                           ("f32_collision_nptl_128x1x1_porous", "porous", dict(storage="f32", layout="collision")),
                           ("f16s_rne_bundle_nptl_128x1x1_porous", "porous", dict(storage="f16s", layout="bundle")),
                           ("f16s_rne_stream_nptl_128x1x1_porous", "porous", dict(storage="f16s", layout="stream")),
+                          ("f16s_rne_bundle_lptl_porous", "porous", dict(storage="f16s", layout="bundle", algo="lptl",
+                                                                         tile=(0, 0, 0))),
                           ("f32_bundle_aa_128x1x1_porous", "porous", dict(storage="f32", layout="bundle", algo="aa")),
                           ("f32_stream_npol_16x8x4_porous", "porous", dict(storage="f32", layout="stream", algo="npol",
                                                                           tile=(16, 8, 4))),

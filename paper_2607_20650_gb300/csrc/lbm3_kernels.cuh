@@ -382,29 +382,56 @@ __device__ __forceinline__ void store3_pair(S *dst, uint32_t N, uint32_t n, cons
     }
 }
 
+// Pulls of a pair (pull3 of both nodes, direction by direction, into packed
+// pairs): node a = (x, y, z) with x even, node b = (x + 1, y, z); only node a
+// can lie on the west face and only node b on the east one. A solid node's
+// lane is +0.
+template <class S, int L>
+__device__ __forceinline__ void pull3_pair(const Step3<S> &a, uint32_t x, uint32_t y, uint32_t z, uint32_t n,
+                                           uint32_t lka, uint32_t lkb, bool fa, bool fb, f2 *g) {
+    const uint32_t nx = (uint32_t)a.g.nx, ny = (uint32_t)a.g.ny, nz = (uint32_t)a.g.nz;
+    const S *__restrict__ src = a.src;
+    const int N = (int)a.N, nxy = (int)(nx * ny);
+    const int xlo = x == 0 ? a.xlo_corr : 0, xhi = x + 1u == nx - 1 ? a.xhi_corr : 0;
+    const int ylo = y == 0 ? nxy : 0, yhi = y == ny - 1 ? -nxy : 0;
+    const int zlo = z == 0 ? N : 0, zhi = z == nz - 1 ? -N : 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const S *ba = src + mult3<L>(i) * n, *bb = ba + mult3<L>(i);
+        int oa, ob;
+        if (i == REST) {
+            oa = ob = a.os[i];
+        } else {
+            const int wyz = (cy(i) > 0 ? ylo : cy(i) < 0 ? yhi : 0) + (cz(i) > 0 ? zlo : cz(i) < 0 ? zhi : 0);
+            const int wa = (cx(i) > 0 ? xlo : 0) + wyz, wb = (cx(i) < 0 ? xhi : 0) + wyz;
+            oa = ((lka >> bit(i)) & 1u) ? a.ob[i] : a.op[i] + (int)mult3<L>(i) * wa;
+            ob = ((lkb >> bit(i)) & 1u) ? a.ob[i] : a.op[i] + (int)mult3<L>(i) * wb;
+        }
+        const float va = fa ? Codec<S>::dec(ba[oa]) : 0.0f;
+        const float vb = fb ? Codec<S>::dec(bb[ob]) : 0.0f;
+        g[i] = pk2(va, vb);
+    }
+}
+
 template <class S, int L>
 __device__ __forceinline__ void step3_pair(const Step3<S> &a, uint32_t x, uint32_t y, uint32_t z, uint32_t n) {
     const uint2 lk2 = *reinterpret_cast<const uint2 *>(a.links + n);   // n even: 8-byte aligned
     const bool fa = lk2.x != SOLID, fb = lk2.y != SOLID;
     if (!fa && !fb) return;
-    float ga[Q], gb[Q];
-    if (fa) {
-        pull3<S, L, true>(a, x, y, z, n, lk2.x, ga);
-        faces3(a, x, ga);
-    } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) ga[i] = 0.0f;
-    }
-    if (fb) {
-        pull3<S, L, true>(a, x + 1u, y, z, n + 1u, lk2.y, gb);
-        faces3(a, x + 1u, gb);
-    } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) gb[i] = 0.0f;
-    }
     f2 g[Q];
+    pull3_pair<S, L>(a, x, y, z, n, lk2.x, lk2.y, fa, fb, g);
+    // inlet / outlet planes (x = 0 holds node a, x = nx - 1 node b): the
+    // substitutions of one node, on its lane
+    const bool west = a.inlet && x == 0 && fa, east = a.outlet && x + 1u == (uint32_t)a.g.nx - 1 && fb;
+    if (west || east) {
+        float ga[Q], gb[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = pk2(ga[i], gb[i]);
+        for (int i = 0; i < Q; ++i) up2(g[i], ga[i], gb[i]);
+        if (west) faces3(a, x, ga);
+        if (east) faces3(a, x + 1u, gb);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = pk2(ga[i], gb[i]);
+    }
     f2 drho, ux, uy, uz;
     collide3_2(a.k2, a.k.force, g, drho, ux, uy, uz);
     float da, db;
