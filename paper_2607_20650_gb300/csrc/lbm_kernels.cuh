@@ -638,22 +638,32 @@ __device__ __forceinline__ void pair_update(const Step<S> &a, uint32_t x, uint32
         else if (L == STREAM) store_zero<S, L>(a.dst, a.N, n + 1u, a.off32);
         return;
     }
-    float ga[9], gb[9];
-    if (fa) {
-        pull_interior<S, L>(a.src, n, nx, a.N, lka, ga);
-    } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) ga[i] = 0.0f;
-    }
-    if (fb) {
-        pull_interior<S, L>(a.src, n + 1u, nx, a.N, lkb, gb);
-    } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) gb[i] = 0.0f;
-    }
+    // both nodes' pulls, direction by direction, into packed pairs (node b's
+    // values sit one record after node a's; a solid node's lane is +0)
     f2 g[9];
+    {
+        const S *own = a.src + lay_mul<L>() * n;
+        const S *rs = own + (ptrdiff_t)lay_mul<L>() * nx;  // row y+1: source of c_y = -1
+        const S *rn = own - (ptrdiff_t)lay_mul<L>() * nx;  // row y-1: source of c_y = +1
+        constexpr ptrdiff_t m = lay_mul<L>();
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = pk2(ga[i], gb[i]);
+        for (int i = 0; i < 9; ++i) {
+            const S *pa, *pb;
+            if (i == 4) {
+                pa = own + (ptrdiff_t)lay_base<L>(a.N, 4);
+                pb = pa + m;
+            } else {
+                const S *row = cy(i) < 0 ? rs : (cy(i) > 0 ? rn : own);
+                const S *pp = row + ((ptrdiff_t)lay_base<L>(a.N, i) - m * cx(i));
+                const S *po = own + (ptrdiff_t)lay_base<L>(a.N, opp(i));
+                pa = ((lka >> link_bit(i)) & 1u) ? po : pp;
+                pb = (((lkb >> link_bit(i)) & 1u) ? po : pp) + m;
+            }
+            const float va = fa ? Codec<S>::dec(ld_src(pa)) : 0.0f;
+            const float vb = fb ? Codec<S>::dec(ld_src(pb)) : 0.0f;
+            g[i] = pk2(va, vb);
+        }
+    }
     f2 drho2, ux2, uy2;
     collide2(a.k2, a.k.force, g, drho2, ux2, uy2);
     float da, db;
