@@ -311,13 +311,11 @@ __device__ __forceinline__ void step3_node(const Step3<S> &a, uint32_t x, uint32
     const uint32_t n = (z * ny + y) * nx + x;
     const uint32_t lk = a.links[n];
     const bool f = lk != SOLID;
-#ifndef LBM3_NO_ZERO_FILL
     if (a.zero_fill) {
         const int lane = (int)(((threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x) & 31u);
         const unsigned F = __ballot_sync(__activemask(), f);
         if (!f && shares3<S, L>(F, lane)) zero3<S, L>(a, n);
     }
-#endif
     if (!f) return;
     C g[Q];
     pull3<S, L, OFF32>(a, x, y, z, n, lk, g);
