@@ -13,7 +13,8 @@ Also reported: the same update with FP16/BF16 shifted storage, the one-lattice
 NPOL, NSOL and AA variants, the batched ensemble of 256 channels against 256
 sequential single-case runs, the D3Q19 extension (a 384^3 sphere packing in
 every layout and algorithm, and a batch of 128 boxes against sequential
-runs), the FP64 CPU oracle on a bounded sample (cpu_baseline), and an
+runs), the headline lattice split into 2 and 4 x-slabs exchanging their
+faces after every update (slabs), the FP64 CPU oracle on a bounded sample (cpu_baseline), and an
 end-to-end number through the C ABI with host buffers (e2e).
 
 Prints ONE JSON line. ``--impl reference`` times the CPU oracle instead.
@@ -393,6 +394,7 @@ def run_ours(args):
 
     if not args.no_variants:
         result["variants"] = variants(args, mask, torch, world)
+        result["slabs"] = slab_split(args, mask, torch, tile)
         result["batched"] = batched(args, torch)
         result["d3q19"] = d3q19(args, torch)
         result["batched_d3q19"] = batched3(args, torch)
@@ -451,6 +453,40 @@ def variants(args, mask, torch, world):
                      "workspace_GB": info["workspace_bytes"] / 1e9, "steps": k}
         lat.close()
         del lat
+        torch.cuda.empty_cache()
+    return out
+
+
+def slab_split(args, mask, torch, tile):
+    """The headline lattice split into 2 and 4 x-slabs on this GPU, the
+    crossing populations of every face exchanged on the device after every
+    update (the domain split of a multi-GPU run with its transport inside one
+    process): the cost of the split against the undivided lattice."""
+    from paper_2607_20650_gb300 import lbm
+    from paper_2607_20650_gb300 import slabs as S
+    nx, ny = args.nx, args.ny
+    k = min(args.steps, 200)
+    out = {}
+    for parts in (2, 4):
+        dec = S.Decomposition(nx, ny, 0.9, mask, parts=parts, force=(1e-6, 0.0), bc=(lbm.PERIODIC,) * 4,
+                              layout="bundle", algo="nptl", storage="f32", tile=tile)
+        dec.init()
+        dec.step(args.warmup).sync()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        dec.step(k)
+        e1.record(s)
+        e1.synchronize()
+        dec.sync()
+        dt = e0.elapsed_time(e1) / 1e3
+        out[f"f32_bundle_nptl_{tile[0]}x{tile[1]}_{parts}_slabs"] = {
+            "MLUPS": nx * ny * k / dt / 1e6, "ms_per_step": dt / k * 1e3, "steps": k,
+            "slab_columns": [sl.nx for sl in dec.slabs], "messages_per_update": len(dec.msgs),
+            "bytes_per_message": 3 * ny * 4, "launches_per_update": 2 * parts + 2 * len(dec.msgs)}
+        dec.close()
+        del dec
         torch.cuda.empty_cache()
     return out
 

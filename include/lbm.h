@@ -203,6 +203,29 @@ lbm_status lbm_force(lbm_lattice *L, const uint8_t *d_body, double out[2]);
 lbm_status lbm_read_populations(lbm_lattice *L, void *host, int32_t as);
 lbm_status lbm_write_populations(lbm_lattice *L, const void *host, int32_t as);
 
+/* Face exchange between x-slabs of one lattice (the domain split behind the
+ * multi-GPU extension of Sec. 6). A slab holds whole columns of the lattice
+ * plus one ghost column on each face it shares with another slab; the pull
+ * update (Eq. (1)) of the column next to a ghost column reads from it only the
+ * three populations that cross the face, the directions with c_ix = sense
+ * (sense = +1: SE, E, NE; -1: SW, W, NW, in that order, Fig. 2). After every
+ * update, pack those three values of the sender's boundary column and unpack
+ * them into the receiver's ghost column; the slabs' interiors then evolve
+ * bit for bit like the undivided lattice (same storage, layout, algorithm;
+ * with LBM_ROUND_SR the draws are keyed on each slab's own node index).
+ *   x      column of this lattice, 0 <= x < nx
+ *   sense  +1 or -1 (which three directions)
+ *   d_buf  device buffer of 3 * ny stored values (8, 4, 2, 2 bytes each for
+ *          F64, F32, F16S, BF16S), caller-owned; value k * ny + y is
+ *          direction k of node (x, y), bits as stored.
+ * lbm_face_pack copies the column of the current state into d_buf;
+ * lbm_face_unpack copies d_buf into it (NPOL / NSOL: then refreshes the
+ * buffer grid from the lattice). Both enqueue on the lattice's stream and
+ * return at once. LBM_EINVAL: NULL argument, x or sense out of range, or the
+ * AA algorithm (its stored state alternates between two forms). */
+lbm_status lbm_face_pack(lbm_lattice *L, int32_t x, int32_t sense, void *d_buf);
+lbm_status lbm_face_unpack(lbm_lattice *L, int32_t x, int32_t sense, const void *d_buf);
+
 typedef struct lbm_info {
     int64_t cells, fluid_cells;
     int64_t steps;                 /* updates done since lbm_init */

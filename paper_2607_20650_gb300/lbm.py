@@ -105,6 +105,8 @@ SIGNATURES = {
     "lbm_force": (_i32, [_vp, _vp, _P(_dbl)]),
     "lbm_read_populations": (_i32, [_vp, _vp, _i32]),
     "lbm_write_populations": (_i32, [_vp, _vp, _i32]),
+    "lbm_face_pack": (_i32, [_vp, _i32, _i32, _vp]),
+    "lbm_face_unpack": (_i32, [_vp, _i32, _i32, _vp]),
     "lbm_get_info": (_i32, [_vp, _P(lbm_info)]),
     "lbm_destroy": (None, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, []),
@@ -292,6 +294,16 @@ def lbm_write_populations(h, pops: np.ndarray):
     as_ = "f64" if a.dtype == np.float64 else "f32"
     a = a.astype(np.float64 if as_ == "f64" else np.float32, copy=False)
     _check(load().lbm_write_populations(h, a.ctypes.data, STORAGES[as_]), "lbm_write_populations")
+
+
+def lbm_face_pack(h, x: int, sense: int, d_buf):
+    """Three populations crossing the face x -> x + sense of column x into
+    d_buf (device, 3 * ny stored values)."""
+    _check(load().lbm_face_pack(h, int(x), int(sense), _ptr(d_buf)), "lbm_face_pack")
+
+
+def lbm_face_unpack(h, x: int, sense: int, d_buf):
+    _check(load().lbm_face_unpack(h, int(x), int(sense), _ptr(d_buf)), "lbm_face_unpack")
 
 
 def lbm_get_info(h) -> dict:
@@ -666,6 +678,12 @@ class Lattice:
 
     def write_populations(self, pops):
         lbm_write_populations(self.h, pops)
+
+    def face_pack(self, x: int, sense: int, buf):
+        lbm_face_pack(self.h, x, sense, buf)
+
+    def face_unpack(self, x: int, sense: int, buf):
+        lbm_face_unpack(self.h, x, sense, buf)
 
     def mass(self) -> float:
         return lbm_mass(self.h)

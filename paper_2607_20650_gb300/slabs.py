@@ -1,0 +1,286 @@
+"""One D2Q9 lattice split into x-slabs with a face exchange after every
+update: the domain decomposition behind the multi-GPU extension the paper
+names as future work (Sec. 6).
+
+Each slab owns a run of whole columns and adds one ghost column on every face
+it shares with another slab. The pull update (Eq. 1) of a slab's boundary
+column reads, from the ghost column beside it, only the three populations
+that cross that face; after every update the owner of the neighbouring column
+sends exactly those (``lbm_face_pack``) and the slab writes them into its
+ghost column (``lbm_face_unpack``). Solid padding columns beyond a ghost
+column can round a slab's row length up to a multiple of 32 nodes, so that
+its rows keep the memory-line alignment of the undivided lattice's. With the
+ghost columns' solid mask taken from the neighbour, every interior node sees
+the same sources, the same link
+classification and the same edge treatment as in the undivided lattice, so
+the interiors evolve bit for bit like it (LPTL, NPTL, NPOL, NSOL; every
+layout and storage; stochastic rounding keys its draws on each slab's own
+node index, so it gives other, equally distributed, draws). The ghost
+columns' own updates are never read and are overwritten by the next exchange.
+
+Two transports carry a face's message:
+ * slabs held by the same process exchange on the device (pack into a device
+   buffer, unpack from it; one stream, so no synchronisation);
+ * slabs held by different processes exchange through page-locked host
+   buffers over a ``torch.distributed`` process group (one slab per rank,
+   slab index = rank): device -> host copy, point-to-point send/recv with the
+   face's two neighbours, host -> device copy, unpack.
+
+Every step of the update and of the exchange runs in the library's kernels;
+this module only plans the split and moves the messages.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import lbm
+
+ELEM_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
+EAST_GOING, WEST_GOING = 1, -1   # sense: c_ix of the three exchanged directions
+
+
+@dataclass(frozen=True)
+class Slab:
+    """Columns [x0, x1) of the lattice, plus a ghost column on the west
+    (gw = 1) and / or east (ge = 1) face, and pw / pe solid padding columns
+    outside the ghost columns that round the slab's row length up to the
+    alignment asked for. Local columns, west to east: pw padding, gw ghost,
+    the interior, ge ghost, pe padding."""
+    index: int
+    x0: int
+    x1: int
+    gw: int
+    ge: int
+    pw: int = 0
+    pe: int = 0
+
+    @property
+    def width(self) -> int:
+        return self.x1 - self.x0
+
+    @property
+    def nx(self) -> int:
+        """Columns of the slab's own lattice, ghosts and padding included."""
+        return self.pw + self.gw + self.width + self.ge + self.pe
+
+    @property
+    def first(self) -> int:
+        """Local column of the first interior column."""
+        return self.pw + self.gw
+
+    @property
+    def interior(self) -> slice:
+        return slice(self.first, self.first + self.width)
+
+    @property
+    def west_ghost(self) -> int:
+        return self.pw
+
+    @property
+    def east_ghost(self) -> int:
+        return self.first + self.width
+
+    def columns(self, nx: int) -> np.ndarray:
+        """Lattice column held by each ghost and interior column of the slab
+        (ghosts wrap on a periodic lattice)."""
+        return np.arange(self.x0 - self.gw, self.x1 + self.ge) % nx
+
+    def local(self, a: np.ndarray, nx: int, pad_value) -> np.ndarray:
+        """The slab's columns of a lattice array (ny x nx, y-major), padding
+        columns filled with pad_value."""
+        a = np.asarray(a).reshape(-1, nx)
+        out = np.full((a.shape[0], self.nx), pad_value, a.dtype)
+        out[:, self.pw:self.nx - self.pe] = a[:, self.columns(nx)]
+        return out
+
+    def edges(self, bc) -> tuple:
+        """(west, east, south, north) of the slab's lattice: the lattice's own
+        x edge where the slab has no ghost column, a wall beyond a ghost or a
+        padding column (only the ghost's own update, never read, sees it)."""
+        return (lbm.WALL if (self.gw or self.pw) else bc[0], lbm.WALL if (self.ge or self.pe) else bc[1],
+                bc[2], bc[3])
+
+
+def split(nx: int, parts: int, periodic_x: bool, align: int = 1) -> list[Slab]:
+    """Columns split into `parts` runs whose widths differ by at most one.
+    Every slab holds at least two columns, so the column next to an inlet or
+    outlet edge (read by the Neumann inlet) is never a ghost. With align > 1
+    a slab with a ghost column gets solid padding beyond it (east if it has
+    an east ghost, else west) so that its row length is a multiple of align:
+    rows then start on the same memory-line boundary as an undivided
+    lattice's."""
+    if parts < 1 or 2 * parts > nx:
+        raise ValueError(f"cannot split {nx} columns into {parts} slabs of at least 2 columns")
+    if align < 1:
+        raise ValueError("align must be >= 1")
+    base, extra = divmod(nx, parts)
+    wrap = periodic_x and parts > 1
+    out, x = [], 0
+    for s in range(parts):
+        w = base + (1 if s < extra else 0)
+        gw, ge = 1 if (s > 0 or wrap) else 0, 1 if (s < parts - 1 or wrap) else 0
+        pad = (-(gw + w + ge)) % align if (gw or ge) else 0
+        out.append(Slab(s, x, x + w, gw, ge, 0 if ge else pad, pad if ge else 0))
+        x += w
+    return out
+
+
+def faces(parts: int, periodic_x: bool) -> list[tuple[int, int]]:
+    """Shared faces as (west slab, east slab) pairs."""
+    f = [(s, s + 1) for s in range(parts - 1)]
+    if periodic_x and parts > 1:
+        f.append((parts - 1, 0))
+    return f
+
+
+def messages(slabs: list[Slab], periodic_x: bool) -> list[tuple[int, int, int, int, int]]:
+    """Per update, every message as (sender, column in sender, receiver,
+    column in receiver, sense): across each face the west slab's last
+    interior column sends its east-going populations into the east slab's
+    west ghost, and the east slab's first interior column sends its
+    west-going populations into the west slab's east ghost."""
+    out = []
+    for w, e in faces(len(slabs), periodic_x):
+        sw, se = slabs[w], slabs[e]
+        out.append((w, sw.east_ghost - 1, e, se.west_ghost, EAST_GOING))
+        out.append((e, se.first, w, sw.east_ghost, WEST_GOING))
+    return out
+
+
+def _tag(sense: int) -> int:
+    return 0 if sense == EAST_GOING else 1
+
+
+def exchange_host(sends: list, recvs: list, group=None):
+    """Point-to-point exchange of host buffers over a torch.distributed group:
+    sends / recvs are lists of (peer, sense, tensor), peer = the other slab's
+    index = its rank in `group` (default: the world). Messages between the
+    same two ranks are told apart by their sense (two of them when two slabs
+    share both faces of a periodic lattice). All receives are posted before
+    the sends, and every request is waited for."""
+    import torch.distributed as dist
+    g = (lambda r: r) if group is None else (lambda r: dist.get_global_rank(group, r))
+    reqs = [dist.irecv(t, src=g(peer), group=group, tag=_tag(sense)) for peer, sense, t in recvs]
+    reqs += [dist.isend(t, dst=g(peer), group=group, tag=_tag(sense)) for peer, sense, t in sends]
+    for r in reqs:
+        r.wait()
+
+
+class Decomposition:
+    """A lattice of nx x ny nodes split into `parts` x-slabs.
+
+    owned: slab indices held by this process, one lattice each on the current
+    device (default: all). When some slabs live elsewhere, slab s is held by
+    rank s of `group` (a torch.distributed process group, default the world)
+    and their faces exchange through host memory. align: row length of
+    every slab's lattice rounded up to a multiple of this many nodes with
+    solid padding (1 = none). Other keyword arguments are those of
+    ``lbm.Lattice`` (bc, layout, algo, storage, force, ...)."""
+
+    def __init__(self, nx, ny, tau, mask=None, *, parts=2, owned=None, group=None, bc=(lbm.PERIODIC,) * 4,
+                 align=32, **kw):
+        import torch
+        algo = kw.get("algo", "nptl")
+        if (lbm.ALGOS[algo] if isinstance(algo, str) else int(algo)) == lbm.ALGOS["aa"]:
+            raise ValueError("the AA pattern stores two forms of the state in turn; slabs need one")
+        self.nx, self.ny = int(nx), int(ny)
+        self.periodic_x = bc[0] == lbm.PERIODIC and bc[1] == lbm.PERIODIC
+        self.slabs = split(self.nx, int(parts), self.periodic_x, int(align))
+        self.owned = list(range(len(self.slabs))) if owned is None else sorted(int(s) for s in owned)
+        self.group = group
+        storage = kw.get("storage", "f32")
+        storage = storage if isinstance(storage, str) else {v: k for k, v in lbm.STORAGES.items()}[storage]
+        self.elem = ELEM_BYTES[storage]
+        m = np.zeros((self.ny, self.nx), np.uint8) if mask is None else \
+            np.asarray(mask, np.uint8).reshape(self.ny, self.nx)
+        self.lat = {}
+        for s in self.owned:
+            sl = self.slabs[s]
+            self.lat[s] = lbm.Lattice(sl.nx, self.ny, tau, sl.local(m, self.nx, 1), bc=sl.edges(bc), **kw)
+        self.msgs = messages(self.slabs, self.periodic_x)
+        nb = 3 * self.ny * self.elem
+        dev = lambda: torch.empty(nb, dtype=torch.uint8, device="cuda")  # noqa: E731
+        host = lambda: torch.empty(nb, dtype=torch.uint8, pin_memory=True)  # noqa: E731
+        self.dbuf = [dev() for _ in self.msgs]
+        self.hbuf = {k: host() for k, (src, _, dst, _, _) in enumerate(self.msgs)
+                     if (src in self.lat) != (dst in self.lat)}
+
+    def _field(self, a, sl: Slab):
+        if a is None:
+            return None
+        return sl.local(np.asarray(a, np.float64), self.nx, 0.0).reshape(-1)
+
+    def init(self, rho=None, ux=None, uy=None):
+        """Equilibrium from the lattice's fields (N values each, y-major);
+        every slab, ghost columns included, starts from the same state as the
+        undivided lattice, so the first update needs no exchange."""
+        for s, lat in self.lat.items():
+            sl = self.slabs[s]
+            lat.init(self._field(rho, sl), self._field(ux, sl), self._field(uy, sl))
+        return self
+
+    def exchange(self):
+        import torch
+        sends, recvs, unpack = [], [], []
+        for k, (src, xs, dst, xd, sense) in enumerate(self.msgs):
+            if src in self.lat:
+                self.lat[src].face_pack(xs, sense, self.dbuf[k])
+                if dst not in self.lat:
+                    self.hbuf[k].copy_(self.dbuf[k], non_blocking=True)
+                    sends.append((dst, sense, self.hbuf[k]))
+            if dst in self.lat:
+                if src not in self.lat:
+                    recvs.append((src, sense, self.hbuf[k]))
+                unpack.append(k)
+        if sends or recvs:
+            torch.cuda.current_stream().synchronize()
+            for lat in self.lat.values():
+                lat.sync()
+            exchange_host(sends, recvs, self.group)
+            for k in unpack:
+                if self.msgs[k][0] not in self.lat:
+                    self.dbuf[k].copy_(self.hbuf[k], non_blocking=True)
+        for k in unpack:
+            _, _, dst, xd, sense = self.msgs[k]
+            self.lat[dst].face_unpack(xd, sense, self.dbuf[k])
+
+    def step(self, n: int = 1, moments: bool = False):
+        for t in range(int(n)):
+            last = moments and t == n - 1
+            for lat in self.lat.values():
+                lat.step(1, moments=last)
+            self.exchange()
+        return self
+
+    def sync(self):
+        for lat in self.lat.values():
+            lat.sync()
+        return self
+
+    def _assemble(self, parts: dict, lead: int | None):
+        shape = (self.ny, self.nx) if lead is None else (lead, self.ny, self.nx)
+        out = None
+        for s, a in parts.items():
+            sl = self.slabs[s]
+            a = a.reshape(shape[:-1] + (sl.nx,))[..., sl.interior]
+            if out is None:
+                out = np.zeros(shape, a.dtype)
+            out[..., sl.x0:sl.x1] = a
+        return out.reshape(shape[:-2] + (-1,))
+
+    def moments(self):
+        """(rho, ux, uy) of the owned slabs' interior columns, placed in
+        lattice-sized arrays (columns of slabs held elsewhere stay 0)."""
+        got = {s: lat.moments() for s, lat in self.lat.items()}
+        return tuple(self._assemble({s: m[c] for s, m in got.items()}, None) for c in range(3))
+
+    def populations(self, as_: str = "f64") -> np.ndarray:
+        """(9, N) state of the owned slabs' interior columns (others 0)."""
+        return self._assemble({s: lat.populations(as_) for s, lat in self.lat.items()}, 9)
+
+    def close(self):
+        for lat in self.lat.values():
+            lat.close()
+        self.lat = {}
