@@ -25,8 +25,9 @@
  *    and freed by lbm_destroy / lbm_batch_destroy.
  *  - Errors: every call returns an lbm_status; nothing throws or exits.
  *    lbm_last_error() returns a thread-local message for the last failure.
- *  - Nothing in this library spins on the device; the only waits are host
- *    waits, and lbm_wait bounds them.
+ *  - The one device-side wait is NSOL's wait for its tile's tensor copy,
+ *    bounded (LBM_ECUDA at the next check if it runs out); host waits are
+ *    bounded by lbm_wait.
  */
 #ifndef LBM_H
 #define LBM_H
@@ -225,6 +226,21 @@ lbm_status lbm_write_populations(lbm_lattice *L, const void *host, int32_t as);
  * AA algorithm (its stored state alternates between two forms). */
 lbm_status lbm_face_pack(lbm_lattice *L, int32_t x, int32_t sense, void *d_buf);
 lbm_status lbm_face_unpack(lbm_lattice *L, int32_t x, int32_t sense, const void *d_buf);
+
+/* Every message of an exchange between lattices held by one process, in one
+ * launch: message k copies the three populations crossing x -> x + sense[k]
+ * of column xs[k] of src[k] into column xd[k] of dst[k] (what
+ * lbm_face_pack of src[k] followed by lbm_face_unpack of dst[k] does, with
+ * no buffer in between), then the buffer grid of every NPOL / NSOL receiver
+ * is refreshed once. All arrays are host arrays of `count` entries,
+ * 0 <= count <= 64; every lattice must have the same ny, storage, layout
+ * and algorithm. Enqueued on cuda_stream (cudaStream_t as void*): the
+ * caller orders it after the updates of every lattice involved, e.g. by
+ * keeping them all on that stream. LBM_EINVAL: as lbm_face_pack, a count
+ * out of range, or lattices that differ. */
+lbm_status lbm_face_exchange(int32_t count, lbm_lattice *const *src, const int32_t *xs,
+                             lbm_lattice *const *dst, const int32_t *xd, const int32_t *sense,
+                             void *cuda_stream);
 
 typedef struct lbm_info {
     int64_t cells, fluid_cells;

@@ -11,9 +11,10 @@
 //
 // lbm_face_pack copies the three populations of one column of the current
 // state into a dense buffer (the message), lbm_face_unpack writes a buffer
-// into one column. The values are moved as stored (bit copies of the storage
-// type), so the exchange is exact for every storage type and rounding mode.
-// Both enqueue one small kernel on the lattice's stream.
+// into one column; lbm_face_exchange does both for every message between
+// lattices of one process in one launch (no intermediate buffer). The values
+// are moved as stored (bit copies of the storage type), so the exchange is
+// exact for every storage type and rounding mode.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -22,6 +23,8 @@
 #include "lbm_capi_internal.h"
 
 namespace {
+
+constexpr int kMaxFaceMessages = 64;
 
 // Element offsets of the three exchanged populations of node (x, y) are
 // base[k] + (y * nx + x) * stride in every layout: the layouts of Fig. 2 are
@@ -80,7 +83,100 @@ lbm_status face_map(lbm_lattice *L, int32_t x, int32_t sense, const void *buf, F
     return LBM_OK;
 }
 
+// Direct column-to-ghost copies of up to kCopiesPerLaunch messages between
+// lattices of one process (same storage, layout, ny): message blockIdx.y.
+constexpr int kCopiesPerLaunch = 16;
+
+struct FaceCopy {
+    const void *src;
+    void *dst;
+    int64_t sbase[3], dbase[3];
+    int64_t snx, dnx;
+    int32_t xs, xd;
+};
+
+struct FaceCopies {
+    FaceCopy m[kCopiesPerLaunch];
+    int64_t stride;
+    int32_t ny;
+};
+
+template <class E>
+__global__ void k_face_copy(const FaceCopies c) {
+    const FaceCopy &m = c.m[blockIdx.y];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * (int64_t)c.ny) return;
+    const int k = (int)(t / c.ny);
+    const int64_t y = t - (int64_t)k * c.ny;
+    const E v = ((const E *)m.src)[m.sbase[k] + (y * m.snx + m.xs) * c.stride];
+    ((E *)m.dst)[m.dbase[k] + (y * m.dnx + m.xd) * c.stride] = v;
+}
+
+cudaError_t launch_face_copy(size_t elem, const FaceCopies &c, int count, cudaStream_t st) {
+    const unsigned threads = 256;
+    const dim3 grid((unsigned)((3 * (int64_t)c.ny + threads - 1) / threads), (unsigned)count);
+    switch (elem) {
+        case 8: k_face_copy<uint64_t><<<grid, threads, 0, st>>>(c); break;
+        case 4: k_face_copy<uint32_t><<<grid, threads, 0, st>>>(c); break;
+        default: k_face_copy<uint16_t><<<grid, threads, 0, st>>>(c); break;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+extern "C" lbm_status lbm_face_exchange(int32_t count, lbm_lattice *const *src, const int32_t *xs,
+                                        lbm_lattice *const *dst, const int32_t *xd, const int32_t *sense,
+                                        void *cuda_stream) {
+    if (count < 0 || count > kMaxFaceMessages) return lbm_fail(LBM_EINVAL, "count %d outside [0, %d]", count,
+                                                                kMaxFaceMessages);
+    if (count == 0) return LBM_OK;
+    if (!src || !xs || !dst || !xd || !sense) return lbm_fail(LBM_EINVAL, "NULL argument");
+    FaceMap ms[kMaxFaceMessages], md[kMaxFaceMessages];
+    for (int k = 0; k < count; ++k) {
+        lbm_status s = face_map(src[k], xs[k], sense[k], src[k], &ms[k]);
+        if (s == LBM_OK) s = face_map(dst[k], xd[k], sense[k], dst[k], &md[k]);
+        if (s != LBM_OK) return s;
+        const lbm_lattice *a = src[k], *b = dst[k], *r = src[0];
+        if (a->p.storage != r->p.storage || b->p.storage != r->p.storage || a->p.layout != r->p.layout ||
+            b->p.layout != r->p.layout || a->p.algo != r->p.algo || b->p.algo != r->p.algo ||
+            a->p.ny != r->p.ny || b->p.ny != r->p.ny)
+            return lbm_fail(LBM_EINVAL, "message %d: lattices differ in storage, layout, algorithm or ny", k);
+    }
+    const cudaStream_t st = (cudaStream_t)cuda_stream;
+    for (int k0 = 0; k0 < count; k0 += kCopiesPerLaunch) {
+        const int n = count - k0 < kCopiesPerLaunch ? count - k0 : kCopiesPerLaunch;
+        FaceCopies c{};
+        c.stride = ms[k0].stride;
+        c.ny = src[0]->p.ny;
+        for (int j = 0; j < n; ++j) {
+            const int k = k0 + j;
+            FaceCopy &m = c.m[j];
+            m.src = src[k]->h.pop[src[k]->cur];
+            m.dst = dst[k]->h.pop[dst[k]->cur];
+            for (int d = 0; d < 3; ++d) {
+                m.sbase[d] = ms[k].base[d];
+                m.dbase[d] = md[k].base[d];
+            }
+            m.snx = ms[k].nx;
+            m.dnx = md[k].nx;
+            m.xs = ms[k].x;
+            m.xd = md[k].x;
+        }
+        cudaError_t e = launch_face_copy(src[0]->ops->elem, c, n, st);
+        if (e != cudaSuccess) return lbm_cuda_fail(e, "face exchange");
+    }
+    // Buffer grids of the receivers (NPOL / NSOL), once each.
+    for (int k = 0; k < count; ++k) {
+        bool seen = false;
+        for (int j = 0; j < k; ++j) seen = seen || dst[j] == dst[k];
+        lbm_lattice *L = dst[k];
+        if (seen || !L->pl.halo_grid) continue;
+        cudaError_t e = L->ops->publish(L->h, L->cur, (int)(L->steps & 1), st);
+        if (e != cudaSuccess) return lbm_cuda_fail(e, "buffer grid refresh after face exchange");
+    }
+    return LBM_OK;
+}
 
 extern "C" lbm_status lbm_face_pack(lbm_lattice *L, int32_t x, int32_t sense, void *d_buf) {
     FaceMap m;

@@ -107,6 +107,7 @@ SIGNATURES = {
     "lbm_write_populations": (_i32, [_vp, _vp, _i32]),
     "lbm_face_pack": (_i32, [_vp, _i32, _i32, _vp]),
     "lbm_face_unpack": (_i32, [_vp, _i32, _i32, _vp]),
+    "lbm_face_exchange": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "lbm_get_info": (_i32, [_vp, _P(lbm_info)]),
     "lbm_destroy": (None, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, []),
@@ -304,6 +305,16 @@ def lbm_face_pack(h, x: int, sense: int, d_buf):
 
 def lbm_face_unpack(h, x: int, sense: int, d_buf):
     _check(load().lbm_face_unpack(h, int(x), int(sense), _ptr(d_buf)), "lbm_face_unpack")
+
+
+def lbm_face_exchange(src: list, xs: list, dst: list, xd: list, sense: list, stream: int):
+    """One launch for every message between lattices of this process:
+    column xs[k] of src[k] -> column xd[k] of dst[k] (handles)."""
+    n = len(src)
+    hs = (ctypes.c_void_p * max(n, 1))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in src])
+    hd = (ctypes.c_void_p * max(n, 1))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in dst])
+    a, b, c = [(ctypes.c_int32 * max(n, 1))(*map(int, v)) for v in (xs, xd, sense)]
+    _check(load().lbm_face_exchange(n, hs, a, hd, b, c, stream), "lbm_face_exchange")
 
 
 def lbm_get_info(h) -> dict:

@@ -19,8 +19,9 @@ node index, so it gives other, equally distributed, draws). The ghost
 columns' own updates are never read and are overwritten by the next exchange.
 
 Two transports carry a face's message:
- * slabs held by the same process exchange on the device (pack into a device
-   buffer, unpack from it; one stream, so no synchronisation);
+ * slabs held by the same process exchange on the device, every message of
+   an update in one launch (``lbm_face_exchange``: column to ghost column,
+   no buffer; one stream, so no synchronisation);
  * slabs held by different processes exchange through page-locked host
    buffers over a ``torch.distributed`` process group (one slab per rank,
    slab index = rank): device -> host copy, point-to-point send/recv with the
@@ -223,8 +224,15 @@ class Decomposition:
 
     def exchange(self):
         import torch
+        local = [m for m in self.msgs if m[0] in self.lat and m[2] in self.lat]
+        if local:
+            src, xs, dst, xd, sense = zip(*local)
+            lbm.lbm_face_exchange([self.lat[s].h for s in src], xs, [self.lat[d].h for d in dst], xd, sense,
+                                  self.lat[src[0]].stream)
         sends, recvs, unpack = [], [], []
         for k, (src, xs, dst, xd, sense) in enumerate(self.msgs):
+            if src in self.lat and dst in self.lat:
+                continue
             if src in self.lat:
                 self.lat[src].face_pack(xs, sense, self.dbuf[k])
                 if dst not in self.lat:

@@ -153,6 +153,53 @@ def test_stochastic_rounding_slabs_draw_their_own_keys():
     dec.close()
 
 
+@pytest.mark.parametrize("algo,layout,storage", [("nptl", "bundle", "f32"), ("npol", "stream", "f16s"),
+                                                  ("nsol", "collision", "f64")])
+def test_many_slabs_exchange_in_several_launches(algo, layout, storage):
+    """Nine slabs of a periodic lattice: 18 messages per update, more than
+    one launch of the one-launch exchange takes."""
+    T = 17
+    name = "porous_periodic"
+    kw = dict(algo=algo, layout=layout, storage=storage, tile=(8, 4))
+    ref = _reference(name, T, **kw)
+    nx, ny, mask, bc, extra = CASES[name]
+    dec = S.Decomposition(nx, ny, 0.7, mask, parts=9, bc=bc, align=4, **extra, **kw)
+    assert len(dec.msgs) == 18
+    dec.init(*_fields(nx, ny, mask))
+    dec.step(T, moments=True).sync()
+    _check_equal(dec, ref)
+    dec.close()
+
+
+def test_one_launch_exchange_equals_pack_then_unpack():
+    nx, ny = 40, 12
+    for storage, layout, algo in [("f32", "stream", "nptl"), ("bf16s", "bundle", "nsol")]:
+        lats = []
+        for seed in range(4):
+            lat = lbm.Lattice(nx, ny, 0.8, None, storage=storage, layout=layout, algo=algo, force=(1e-4 * seed, 0.0))
+            lat.init(*_fields(nx, ny, np.zeros(nx * ny)))
+            lat.step(2 + seed).sync()
+            lats.append(lat)
+        a0, a1, b0, b1 = lats
+        b0.write_populations(a0.populations("f64"))
+        b1.write_populations(a1.populations("f64"))
+        assert np.array_equal(b0.populations("f64"), a0.populations("f64"))
+        before = a1.populations("f64")
+        msgs = [(5, 0, 1), (nx - 2, nx - 1, -1), (17, 3, 1)]
+        lbm.lbm_face_exchange([a0.h] * 3, [m[0] for m in msgs], [a1.h] * 3, [m[1] for m in msgs],
+                              [m[2] for m in msgs], a0.stream)
+        assert not np.array_equal(a1.populations("f64"), before)
+        buf = torch.zeros(3 * ny * S.ELEM_BYTES[storage], dtype=torch.uint8, device="cuda")
+        for xs, xd, sense in msgs:
+            b0.face_pack(xs, sense, buf)
+            b1.face_unpack(xd, sense, buf)
+        for lat in lats:
+            lat.sync()
+        assert np.array_equal(a1.populations("f64"), b1.populations("f64"))
+        for lat in lats:
+            lat.close()
+
+
 def test_face_exchange_rejects_bad_arguments():
     nx, ny = 32, 16
     buf = torch.zeros(3 * ny * 4, dtype=torch.uint8, device="cuda")
@@ -167,6 +214,20 @@ def test_face_exchange_rejects_bad_arguments():
     with pytest.raises(lbm.LbmError):
         lbm.lbm_face_pack(lat.h, 3, 1, None)
     lat.close()
+    other = lbm.Lattice(nx, ny, 0.8, None, algo="nptl")
+    other_ny = lbm.Lattice(nx, ny + 2, 0.8, None, algo="nptl")
+    other_st = lbm.Lattice(nx, ny, 0.8, None, algo="nptl", storage="f16s")
+    for dst in (other_ny, other_st):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_face_exchange([other.h], [3], [dst.h], [0], [1], other.stream)
+        assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_face_exchange([other.h] * 65, [3] * 65, [other.h] * 65, [0] * 65, [1] * 65, other.stream)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_face_exchange([other.h], [nx], [other.h], [0], [1], other.stream)
+    lbm.lbm_face_exchange([], [], [], [], [], other.stream)
+    for x in (other, other_ny, other_st):
+        x.close()
     aa = lbm.Lattice(nx, ny, 0.8, None, algo="aa")
     aa.init()
     with pytest.raises(lbm.LbmError) as e:
