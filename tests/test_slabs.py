@@ -57,6 +57,20 @@ def test_split_rejects_slabs_narrower_than_two_columns():
         S.split(5, 0, True)
 
 
+def test_layout_offsets_are_affine_in_the_node_index():
+    """The face kernels address population slot i of node n as
+    base(i) + n * stride in all three layouts (Fig. 2)."""
+    from paper_2607_20650_gb300 import build, lbm
+    build.build()
+    for N in (6, 35):
+        for name in ("stream", "bundle", "collision"):
+            stride = lbm.lbm_layout_index(name, N, 1, 0) - lbm.lbm_layout_index(name, N, 0, 0)
+            for i in range(9):
+                base = lbm.lbm_layout_index(name, N, 0, i)
+                assert [lbm.lbm_layout_index(name, N, n, i) for n in range(N)] == \
+                    [base + n * stride for n in range(N)], (name, i)
+
+
 # ---------------------------------------------------------------- the plan on the oracle
 
 P, W = O.PERIODIC, O.WALL
