@@ -561,12 +561,12 @@ def d3q19(args, torch):
                           ("f16s_rne_bundle_lptl_porous", "porous", dict(storage="f16s", layout="bundle", algo="lptl",
                                                                          tile=(0, 0, 0))),
                           ("f32_bundle_aa_128x1x1_porous", "porous", dict(storage="f32", layout="bundle", algo="aa")),
-                          ("f32_stream_npol_16x8x4_porous", "porous", dict(storage="f32", layout="stream", algo="npol",
-                                                                          tile=(16, 8, 4))),
-                          ("f32_bundle_nsol_32x4x4_porous", "porous", dict(storage="f32", layout="bundle", algo="nsol",
-                                                                          tile=(32, 4, 4))),
-                          ("f32_stream_nsol_32x4x4_porous", "porous", dict(storage="f32", layout="stream", algo="nsol",
-                                                                          tile=(32, 4, 4)))]:
+                          ("f32_stream_npol_8x8x8_porous", "porous", dict(storage="f32", layout="stream", algo="npol",
+                                                                         tile=(8, 8, 8))),
+                          ("f32_bundle_nsol_8x8x8_porous", "porous", dict(storage="f32", layout="bundle", algo="nsol",
+                                                                         tile=(8, 8, 8))),
+                          ("f32_stream_nsol_8x8x8_porous", "porous", dict(storage="f32", layout="stream", algo="nsol",
+                                                                         tile=(8, 8, 8)))]:
         m = porous if geo == "porous" else np.zeros_like(porous)
         stream = torch.cuda.Stream()
         kw = dict(kw)

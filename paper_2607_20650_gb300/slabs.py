@@ -204,9 +204,10 @@ class Decomposition:
         nb = 3 * self.ny * self.elem
         dev = lambda: torch.empty(nb, dtype=torch.uint8, device="cuda")  # noqa: E731
         host = lambda: torch.empty(nb, dtype=torch.uint8, pin_memory=True)  # noqa: E731
-        self.dbuf = [dev() for _ in self.msgs]
-        self.hbuf = {k: host() for k, (src, _, dst, _, _) in enumerate(self.msgs)
-                     if (src in self.lat) != (dst in self.lat)}
+        # buffers for messages to or from another process only (the others go column to column)
+        remote = [k for k, (src, _, dst, _, _) in enumerate(self.msgs) if (src in self.lat) != (dst in self.lat)]
+        self.dbuf = {k: dev() for k in remote}
+        self.hbuf = {k: host() for k in remote}
 
     def _field(self, a, sl: Slab):
         if a is None:
@@ -229,30 +230,29 @@ class Decomposition:
             src, xs, dst, xd, sense = zip(*local)
             lbm.lbm_face_exchange([self.lat[s].h for s in src], xs, [self.lat[d].h for d in dst], xd, sense,
                                   self.lat[src[0]].stream)
-        sends, recvs, unpack = [], [], []
-        for k, (src, xs, dst, xd, sense) in enumerate(self.msgs):
-            if src in self.lat and dst in self.lat:
-                continue
+        sends, recvs = [], []
+        for k in self.dbuf:  # messages to or from another process
+            src, xs, dst, xd, sense = self.msgs[k]
             if src in self.lat:
-                self.lat[src].face_pack(xs, sense, self.dbuf[k])
-                if dst not in self.lat:
+                lat = self.lat[src]
+                lat.face_pack(xs, sense, self.dbuf[k])
+                with torch.cuda.stream(lat.torch_stream):
                     self.hbuf[k].copy_(self.dbuf[k], non_blocking=True)
-                    sends.append((dst, sense, self.hbuf[k]))
+                sends.append((dst, sense, self.hbuf[k]))
+            else:
+                recvs.append((src, sense, self.hbuf[k]))
+        if not self.dbuf:
+            return
+        for lat in self.lat.values():
+            lat.sync()  # packed messages in host memory, receivers' updates done
+        exchange_host(sends, recvs, self.group)
+        for k in self.dbuf:
+            src, xs, dst, xd, sense = self.msgs[k]
             if dst in self.lat:
-                if src not in self.lat:
-                    recvs.append((src, sense, self.hbuf[k]))
-                unpack.append(k)
-        if sends or recvs:
-            torch.cuda.current_stream().synchronize()
-            for lat in self.lat.values():
-                lat.sync()
-            exchange_host(sends, recvs, self.group)
-            for k in unpack:
-                if self.msgs[k][0] not in self.lat:
+                lat = self.lat[dst]
+                with torch.cuda.stream(lat.torch_stream):
                     self.dbuf[k].copy_(self.hbuf[k], non_blocking=True)
-        for k in unpack:
-            _, _, dst, xd, sense = self.msgs[k]
-            self.lat[dst].face_unpack(xd, sense, self.dbuf[k])
+                lat.face_unpack(xd, sense, self.dbuf[k])
 
     def step(self, n: int = 1, moments: bool = False):
         for t in range(int(n)):
