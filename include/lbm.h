@@ -472,6 +472,22 @@ lbm_status lbm3_get_info(lbm3_lattice *L, lbm_info *out);
 void lbm3_destroy(lbm3_lattice *L);
 int64_t lbm3_layout_index(int32_t layout, int64_t N, int64_t n, int32_t i);
 
+/* Face exchange between x-slabs of a D3Q19 box, as lbm_face_pack /
+ * lbm_face_unpack / lbm_face_exchange in 2-D: a slab holds whole x-planes
+ * plus a ghost plane on each face it shares with another; after every update
+ * the five populations with c_x = sense (in direction order) of the sender's
+ * boundary plane x go into the receiver's ghost plane. d_buf: device buffer
+ * of 5 * ny * nz stored values, value k * (ny nz) + (z ny + y) = direction k
+ * of node (x, y, z), bits as stored. Same rules, errors and stream use as
+ * the 2-D calls (AA refused; NPOL / NSOL receivers refresh their buffer
+ * grid); every lattice of one lbm3_face_exchange has the same ny * nz,
+ * storage, layout and algorithm. */
+lbm_status lbm3_face_pack(lbm3_lattice *L, int32_t x, int32_t sense, void *d_buf);
+lbm_status lbm3_face_unpack(lbm3_lattice *L, int32_t x, int32_t sense, const void *d_buf);
+lbm_status lbm3_face_exchange(int32_t count, lbm3_lattice *const *src, const int32_t *xs,
+                              lbm3_lattice *const *dst, const int32_t *xd, const int32_t *sense,
+                              void *cuda_stream);
+
 /* ---------------------------------------------------------------- D3Q19 batches
  * Many independent boxes advanced together: one launch per update over a
  * packed list of work items of every case (a tile for NPTL, NPOL and NSOL,

@@ -144,6 +144,9 @@ SIGNATURES = {
     "lbm3_get_info": (_i32, [_vp, _P(lbm_info)]),
     "lbm3_destroy": (None, [_vp]),
     "lbm3_layout_index": (_i64, [_i32, _i64, _i64, _i32]),
+    "lbm3_face_pack": (_i32, [_vp, _i32, _i32, _vp]),
+    "lbm3_face_unpack": (_i32, [_vp, _i32, _i32, _vp]),
+    "lbm3_face_exchange": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "lbm3_batch_workspace_bytes": (_i32, [_i32, _P(lbm3_params), _P(_sz)]),
     "lbm3_batch_create": (_i32, [_i32, _P(lbm3_params), _P(_vp), _vp, _sz, _vp, _P(_vp)]),
     "lbm3_batch_init": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
@@ -307,14 +310,30 @@ def lbm_face_unpack(h, x: int, sense: int, d_buf):
     _check(load().lbm_face_unpack(h, int(x), int(sense), _ptr(d_buf)), "lbm_face_unpack")
 
 
-def lbm_face_exchange(src: list, xs: list, dst: list, xd: list, sense: list, stream: int):
-    """One launch for every message between lattices of this process:
-    column xs[k] of src[k] -> column xd[k] of dst[k] (handles)."""
+def _face_exchange(fn: str, src: list, xs: list, dst: list, xd: list, sense: list, stream: int):
     n = len(src)
     hs = (ctypes.c_void_p * max(n, 1))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in src])
     hd = (ctypes.c_void_p * max(n, 1))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in dst])
     a, b, c = [(ctypes.c_int32 * max(n, 1))(*map(int, v)) for v in (xs, xd, sense)]
-    _check(load().lbm_face_exchange(n, hs, a, hd, b, c, stream), "lbm_face_exchange")
+    _check(getattr(load(), fn)(n, hs, a, hd, b, c, stream), fn)
+
+
+def lbm_face_exchange(src: list, xs: list, dst: list, xd: list, sense: list, stream: int):
+    """One launch for every message between lattices of this process:
+    column xs[k] of src[k] -> column xd[k] of dst[k] (handles)."""
+    _face_exchange("lbm_face_exchange", src, xs, dst, xd, sense, stream)
+
+
+def lbm3_face_pack(h, x: int, sense: int, d_buf):
+    _check(load().lbm3_face_pack(h, int(x), int(sense), _ptr(d_buf)), "lbm3_face_pack")
+
+
+def lbm3_face_unpack(h, x: int, sense: int, d_buf):
+    _check(load().lbm3_face_unpack(h, int(x), int(sense), _ptr(d_buf)), "lbm3_face_unpack")
+
+
+def lbm3_face_exchange(src: list, xs: list, dst: list, xd: list, sense: list, stream: int):
+    _face_exchange("lbm3_face_exchange", src, xs, dst, xd, sense, stream)
 
 
 def lbm_get_info(h) -> dict:
@@ -800,6 +819,12 @@ class Lattice3:
 
     def write_populations(self, pops):
         lbm3_write_populations(self.h, pops)
+
+    def face_pack(self, x: int, sense: int, buf):
+        lbm3_face_pack(self.h, x, sense, buf)
+
+    def face_unpack(self, x: int, sense: int, buf):
+        lbm3_face_unpack(self.h, x, sense, buf)
 
     def mass(self) -> float:
         return lbm3_mass(self.h)

@@ -169,8 +169,21 @@ def exchange_host(sends: list, recvs: list, group=None):
         r.wait()
 
 
+def edges3(sl: Slab, bc, bc_x_east: int) -> tuple:
+    """(bc_x, bc_y, bc_z, bc_x_east) of a D3Q19 slab's box: the box's own
+    x faces where the slab has no ghost plane; walls beyond ghost or padding
+    planes of a periodic or walled box; the box's inlet / outlet pair
+    otherwise, applied to the slab's end planes (a ghost or padding plane
+    there only changes that plane's own update, which is never read: the
+    inlet and outlet treatments read and write the node itself)."""
+    if not (sl.gw or sl.ge) or bc[0] not in (lbm.PERIODIC, lbm.WALL):
+        return bc[0], bc[1], bc[2], bc_x_east
+    return lbm.WALL, bc[1], bc[2], bc_x_east
+
+
 class Decomposition:
-    """A lattice of nx x ny nodes split into `parts` x-slabs.
+    """A lattice of nx x ny nodes (D2Q9), or nx x ny x nz (D3Q19, with nz),
+    split into `parts` x-slabs.
 
     owned: slab indices held by this process, one lattice each on the current
     device (default: all). When some slabs live elsewhere, slab s is held by
@@ -178,30 +191,43 @@ class Decomposition:
     and their faces exchange through host memory. align: row length of
     every slab's lattice rounded up to a multiple of this many nodes with
     solid padding (1 = none). Other keyword arguments are those of
-    ``lbm.Lattice`` (bc, layout, algo, storage, force, ...)."""
+    ``lbm.Lattice`` or ``lbm.Lattice3`` (bc, layout, algo, storage, force,
+    ...); in 3-D bc = (x, y, z) and bc_x_east as for ``lbm.Lattice3``."""
 
-    def __init__(self, nx, ny, tau, mask=None, *, parts=2, owned=None, group=None, bc=(lbm.PERIODIC,) * 4,
+    def __init__(self, nx, ny, tau, mask=None, *, nz=None, parts=2, owned=None, group=None, bc=None,
                  align=32, **kw):
         import torch
         algo = kw.get("algo", "nptl")
         if (lbm.ALGOS[algo] if isinstance(algo, str) else int(algo)) == lbm.ALGOS["aa"]:
             raise ValueError("the AA pattern stores two forms of the state in turn; slabs need one")
-        self.nx, self.ny = int(nx), int(ny)
-        self.periodic_x = bc[0] == lbm.PERIODIC and bc[1] == lbm.PERIODIC
+        self.d3 = nz is not None
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz) if self.d3 else 1
+        self.rows = self.ny * self.nz
+        if bc is None:
+            bc = (lbm.PERIODIC,) * (3 if self.d3 else 4)
+        self.periodic_x = bc[0] == lbm.PERIODIC and (self.d3 or bc[1] == lbm.PERIODIC)
         self.slabs = split(self.nx, int(parts), self.periodic_x, int(align))
         self.owned = list(range(len(self.slabs))) if owned is None else sorted(int(s) for s in owned)
         self.group = group
         storage = kw.get("storage", "f32")
         storage = storage if isinstance(storage, str) else {v: k for k, v in lbm.STORAGES.items()}[storage]
         self.elem = ELEM_BYTES[storage]
-        m = np.zeros((self.ny, self.nx), np.uint8) if mask is None else \
-            np.asarray(mask, np.uint8).reshape(self.ny, self.nx)
+        self.q = 19 if self.d3 else 9
+        m = np.zeros((self.rows, self.nx), np.uint8) if mask is None else \
+            np.asarray(mask, np.uint8).reshape(self.rows, self.nx)
+        bc_x_east = kw.pop("bc_x_east", lbm.OUTFLOW_ZG)
         self.lat = {}
         for s in self.owned:
             sl = self.slabs[s]
-            self.lat[s] = lbm.Lattice(sl.nx, self.ny, tau, sl.local(m, self.nx, 1), bc=sl.edges(bc), **kw)
+            local = sl.local(m, self.nx, 1)
+            if self.d3:
+                bx, by, bz, bxe = edges3(sl, bc, bc_x_east)
+                self.lat[s] = lbm.Lattice3(sl.nx, self.ny, self.nz, tau, local, bc=(bx, by, bz), bc_x_east=bxe,
+                                           **kw)
+            else:
+                self.lat[s] = lbm.Lattice(sl.nx, self.ny, tau, local, bc=sl.edges(bc), **kw)
         self.msgs = messages(self.slabs, self.periodic_x)
-        nb = 3 * self.ny * self.elem
+        nb = (5 if self.d3 else 3) * self.rows * self.elem
         dev = lambda: torch.empty(nb, dtype=torch.uint8, device="cuda")  # noqa: E731
         host = lambda: torch.empty(nb, dtype=torch.uint8, pin_memory=True)  # noqa: E731
         # buffers for messages to or from another process only (the others go column to column)
@@ -214,13 +240,13 @@ class Decomposition:
             return None
         return sl.local(np.asarray(a, np.float64), self.nx, 0.0).reshape(-1)
 
-    def init(self, rho=None, ux=None, uy=None):
-        """Equilibrium from the lattice's fields (N values each, y-major);
+    def init(self, rho=None, ux=None, uy=None, uz=None):
+        """Equilibrium from the lattice's fields (N values each, x fastest);
         every slab, ghost columns included, starts from the same state as the
         undivided lattice, so the first update needs no exchange."""
         for s, lat in self.lat.items():
-            sl = self.slabs[s]
-            lat.init(self._field(rho, sl), self._field(ux, sl), self._field(uy, sl))
+            f = [self._field(a, self.slabs[s]) for a in ((rho, ux, uy, uz) if self.d3 else (rho, ux, uy))]
+            lat.init(*f)
         return self
 
     def exchange(self):
@@ -228,8 +254,8 @@ class Decomposition:
         local = [m for m in self.msgs if m[0] in self.lat and m[2] in self.lat]
         if local:
             src, xs, dst, xd, sense = zip(*local)
-            lbm.lbm_face_exchange([self.lat[s].h for s in src], xs, [self.lat[d].h for d in dst], xd, sense,
-                                  self.lat[src[0]].stream)
+            fn = lbm.lbm3_face_exchange if self.d3 else lbm.lbm_face_exchange
+            fn([self.lat[s].h for s in src], xs, [self.lat[d].h for d in dst], xd, sense, self.lat[src[0]].stream)
         sends, recvs = [], []
         for k in self.dbuf:  # messages to or from another process
             src, xs, dst, xd, sense = self.msgs[k]
@@ -268,7 +294,7 @@ class Decomposition:
         return self
 
     def _assemble(self, parts: dict, lead: int | None):
-        shape = (self.ny, self.nx) if lead is None else (lead, self.ny, self.nx)
+        shape = (self.rows, self.nx) if lead is None else (lead, self.rows, self.nx)
         out = None
         for s, a in parts.items():
             sl = self.slabs[s]
@@ -279,14 +305,14 @@ class Decomposition:
         return out.reshape(shape[:-2] + (-1,))
 
     def moments(self):
-        """(rho, ux, uy) of the owned slabs' interior columns, placed in
-        lattice-sized arrays (columns of slabs held elsewhere stay 0)."""
+        """(rho, ux, uy[, uz]) of the owned slabs' interior columns, placed
+        in lattice-sized arrays (columns of slabs held elsewhere stay 0)."""
         got = {s: lat.moments() for s, lat in self.lat.items()}
-        return tuple(self._assemble({s: m[c] for s, m in got.items()}, None) for c in range(3))
+        return tuple(self._assemble({s: m[c] for s, m in got.items()}, None) for c in range(4 if self.d3 else 3))
 
     def populations(self, as_: str = "f64") -> np.ndarray:
-        """(9, N) state of the owned slabs' interior columns (others 0)."""
-        return self._assemble({s: lat.populations(as_) for s, lat in self.lat.items()}, 9)
+        """(Q, N) state of the owned slabs' interior columns (others 0)."""
+        return self._assemble({s: lat.populations(as_) for s, lat in self.lat.items()}, self.q)
 
     def close(self):
         for lat in self.lat.values():

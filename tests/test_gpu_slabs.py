@@ -331,3 +331,124 @@ def test_slabs_on_separate_processes_exchange_through_host_memory(name, parts, k
             assert np.array_equal(z["p"].reshape(9, ny, nx)[:, :, c], pops.reshape(9, ny, nx)[:, :, c])
             for k, key in enumerate(("rho", "ux", "uy")):
                 assert np.array_equal(z[key].reshape(ny, nx)[:, c], mom[k].reshape(ny, nx)[:, c])
+
+
+# ---------------------------------------------------------------- D3Q19 boxes
+
+CASES3 = {
+    # name: nx, ny, nz, mask, (bc_x, bc_y, bc_z), extra parameters
+    "spheres_periodic": (40, 12, 10, G.porous_spheres(40, 12, 10, 5, 1.5, 3.0, 0.25), (P, P, P),
+                         dict(force=(2e-5, -4e-6, 1e-6))),
+    "walls_force": (36, 10, 8, G.porous_spheres(36, 10, 8, 7, 1.5, 2.5, 0.2), (W, P, W),
+                    dict(force=(1e-5, 0.0, 3e-6))),
+    "zou_he_pressure": (44, 10, 8, G.ball(44, 10, 8, 15.0, 5.0, 4.0, 2.5), (lbm.INLET_ZOUHE, W, W),
+                        dict(bc_x_east=lbm.OUTLET_PRESSURE, u_in=(0.04, 0.0, 0.0), rho_out=0.997)),
+    "eq_outflow": (40, 10, 8, G.ball(40, 10, 8, 21.0, 5.0, 4.0, 2.0), (lbm.INLET_EQ, P, W),
+                   dict(bc_x_east=lbm.OUTFLOW_ZG, u_in=(0.03, 0.0, 0.0))),
+}
+
+
+def _fields3(nx, ny, nz, mask):
+    r = G.SplitMix64(11, 2)
+    n = nx * ny * nz
+    rho = 1.0 + r.uniform(n, -0.01, 0.01)
+    u = [r.uniform(n, -0.02, 0.02) for _ in range(3)]
+    for a in u:
+        a[np.asarray(mask).reshape(-1) > 0] = 0.0
+    return (rho, *u)
+
+
+def _reference3(name, T, **kw):
+    nx, ny, nz, mask, bc, extra = CASES3[name]
+    lat = lbm.Lattice3(nx, ny, nz, 0.75, mask, bc=bc, **extra, **kw)
+    lat.init(*_fields3(nx, ny, nz, mask))
+    lat.step(T, moments=True).sync()
+    out = lat.populations("f64"), lat.moments()
+    lat.close()
+    return out
+
+
+def _run3(name, T, parts, align, **kw):
+    nx, ny, nz, mask, bc, extra = CASES3[name]
+    dec = S.Decomposition(nx, ny, 0.75, mask, nz=nz, parts=parts, bc=bc, align=align, **extra, **kw)
+    dec.init(*_fields3(nx, ny, nz, mask))
+    dec.step(T, moments=True).sync()
+    p, m = dec.populations("f64"), dec.moments()
+    dec.close()
+    return p, m
+
+
+def _equal3(got, ref):
+    assert np.array_equal(got[0], ref[0])
+    assert len(got[1]) == 4
+    for u, v in zip(got[1], ref[1]):
+        assert np.array_equal(u, v)
+    assert np.all(np.isfinite(got[0]))
+
+
+OPEN3 = ("zou_he_pressure", "eq_outflow")
+
+
+@pytest.mark.parametrize("name", list(CASES3))
+@pytest.mark.parametrize("algo,layout,tile", [("lptl", "bundle", (0, 0, 0)), ("nptl", "stream", (16, 2, 2)),
+                                              ("nptl", "collision", (0, 0, 0)), ("npol", "stream", (8, 4, 2)),
+                                              ("npol", "bundle", (4, 4, 4)), ("nsol", "bundle", (8, 4, 2)),
+                                              ("nsol", "collision", (4, 4, 4))])
+@pytest.mark.parametrize("parts,align", [(2, 32), (3, 1)])
+def test_d3q19_slabs_equal_the_undivided_box_fp32(name, algo, layout, tile, parts, align):
+    if name in OPEN3 and algo in ("npol", "nsol"):
+        pytest.skip("inlet and outlet faces are LPTL / NPTL only")
+    T = 21
+    kw = dict(algo=algo, layout=layout, storage="f32", tile=tile)
+    _equal3(_run3(name, T, parts, align, **kw), _reference3(name, T, **kw))
+
+
+@pytest.mark.parametrize("storage", ["f64", "f16s", "bf16s"])
+@pytest.mark.parametrize("algo,layout", [("nptl", "bundle"), ("lptl", "stream"), ("nsol", "stream")])
+def test_d3q19_slabs_equal_the_undivided_box_other_storage(storage, algo, layout):
+    T = 17
+    for name in ("spheres_periodic", "zou_he_pressure"):
+        if name in OPEN3 and algo == "nsol":
+            continue
+        kw = dict(algo=algo, layout=layout, storage=storage, tile=(8, 4, 2) if algo == "nsol" else (0, 0, 0))
+        _equal3(_run3(name, T, 4, 1, **kw), _reference3(name, T, **kw))
+
+
+def test_d3q19_face_pack_moves_the_stored_bits():
+    nx, ny, nz = 12, 6, 5
+    as_type = {"f64": torch.float64, "f32": torch.float32, "f16s": torch.float16, "bf16s": torch.bfloat16}
+    for storage, layout, algo in [("f32", "bundle", "nptl"), ("f16s", "collision", "nsol"), ("f64", "stream", "npol"),
+                                  ("bf16s", "bundle", "lptl")]:
+        tile = (4, 2, 2) if algo in ("npol", "nsol") else (0, 0, 0)
+        a = lbm.Lattice3(nx, ny, nz, 0.8, None, storage=storage, layout=layout, algo=algo, tile=tile)
+        a.init(*_fields3(nx, ny, nz, np.zeros(nx * ny * nz)))
+        a.step(3).sync()
+        b = lbm.Lattice3(nx, ny, nz, 0.8, None, storage=storage, layout=layout, algo=algo, tile=tile)
+        b.init()
+        b.step(3).sync()
+        elem = S.ELEM_BYTES[storage]
+        sent = {}
+        for x, sense in [(0, 1), (nx - 1, -1), (5, 1), (5, -1)]:
+            buf = torch.zeros(5 * ny * nz * elem, dtype=torch.uint8, device="cuda")
+            a.face_pack(x, sense, buf)
+            b.face_unpack(x, sense, buf)
+            sent[(x, sense)] = buf
+        a.sync()
+        b.sync()
+        pa = a.populations("f64").reshape(19, ny * nz, nx)
+        pb = b.populations("f64").reshape(19, ny * nz, nx)
+        cx = [0, -1, 0, 1, 0, -1, 0, 1, -1, 0, 1, -1, 0, 1, 0, -1, 0, 1, 0]  # D3Q19 order, c_x of each direction
+        for (x, sense), buf in sent.items():
+            dirs = [i for i in range(19) if cx[i] == sense]
+            msg = buf.view(as_type[storage]).double().cpu().numpy().reshape(5, ny * nz)
+            assert np.array_equal(msg, pa[dirs, :, x])
+            assert np.array_equal(pa[dirs, :, x], pb[dirs, :, x])
+        a.close()
+        b.close()
+    aa = lbm.Lattice3(nx, ny, nz, 0.8, None, algo="aa")
+    aa.init()
+    buf = torch.zeros(5 * ny * nz * 4, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lbm.LbmError) as e:
+        aa.face_pack(3, 1, buf)
+    assert e.value.status == lbm.LBM_EINVAL
+    aa.close()

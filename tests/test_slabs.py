@@ -138,6 +138,64 @@ def test_slab_plan_on_the_oracle_is_bit_identical(name, parts, align):
     assert np.all(np.isfinite(full.h)) and np.abs(full.ux).max() > 1e-4
 
 
+# ---------------------------------------------------------------- the plan on the 3-D oracle
+
+def _case3(name):
+    nx, ny, nz = 20, 8, 6
+    if name == "spheres_periodic":
+        return nx, ny, nz, G.porous_spheres(nx, ny, nz, 5, 1.5, 2.5, 0.25), (P, P, P), dict(fx=2e-5, fy=-4e-6), {}
+    if name == "walls_force":
+        return nx, ny, nz, G.porous_spheres(nx, ny, nz, 7, 1.5, 2.5, 0.2), (W, P, W), dict(fx=1e-5, fz=3e-6), {}
+    if name == "zou_he_pressure":
+        return nx, ny, nz, G.ball(nx, ny, nz, 9.0, 4.0, 3.0, 2.2), (O.INLET_ZOUHE, W, W), {}, \
+            dict(bc_xe=O.OUTLET_PRESSURE, u_in=(0.04, 0.0, 0.0), rho_out=0.997)
+    return nx, ny, nz, G.ball(nx, ny, nz, 11.0, 4.0, 3.0, 2.0), (O.INLET_EQ, P, W), {}, \
+        dict(bc_xe=O.OUTFLOW_ZG, u_in=(0.03, 0.0, 0.0))
+
+
+@pytest.mark.parametrize("name,parts,align", [("spheres_periodic", 2, 1), ("spheres_periodic", 3, 8),
+                                              ("walls_force", 3, 1), ("zou_he_pressure", 2, 8),
+                                              ("zou_he_pressure", 3, 1), ("eq_outflow", 2, 1)])
+def test_slab_plan_on_the_3d_oracle_is_bit_identical(name, parts, align):
+    """D3Q19 boxes split into x-slabs with the plan's ghost planes, masks and
+    x faces, each updated by the 3-D oracle and given the five crossing
+    populations per face node after every update, equal the undivided box."""
+    nx, ny, nz, mask, bc, force, xface = _case3(name)
+    T = 18
+    rows = ny * nz
+    r = G.SplitMix64(9, 4)
+    rho = 1.0 + r.uniform(nx * rows, -0.01, 0.01)
+    u = [r.uniform(nx * rows, -0.02, 0.02) for _ in range(3)]
+    for a in u:
+        a[np.asarray(mask).reshape(-1) > 0] = 0.0
+    full = O.Lattice3(O.Case3(nx, ny, nz, 0.8, bc_x=bc[0], bc_y=bc[1], bc_z=bc[2], **force, **xface),
+                      mask, rho, *u).run(T)
+    periodic = bc[0] == P
+    sl = S.split(nx, parts, periodic, align)
+    c, _ = O.directions3()
+    lats = []
+    for s in sl:
+        bx, by, bz, bxe = S.edges3(s, bc, xface.get("bc_xe", O.OUTFLOW_ZG))
+        extra = dict(xface, bc_xe=bxe) if bx in (O.INLET_EQ, O.INLET_ZOUHE) else {}
+        case = O.Case3(s.nx, ny, nz, 0.8, bc_x=bx, bc_y=by, bc_z=bz, **force, **extra)
+        lats.append(O.Lattice3(case, s.local(mask, nx, 1), *[s.local(a, nx, 0.0) for a in (rho, *u)]))
+    for _ in range(T):
+        for lat in lats:
+            lat.run(1)
+        for src, xs, dst, xd, sense in S.messages(sl, periodic):
+            dirs = [i for i in range(19) if c[i, 0] == sense]
+            assert len(dirs) == 5
+            a = lats[src].h.reshape(19, rows, sl[src].nx)
+            b = lats[dst].h.reshape(19, rows, sl[dst].nx)
+            b[dirs, :, xd] = a[dirs, :, xs]
+    fh = full.h.reshape(19, rows, nx)
+    for s, lat in zip(sl, lats):
+        assert np.array_equal(lat.h.reshape(19, rows, s.nx)[:, :, s.interior], fh[:, :, s.x0:s.x1]), s
+        for a, b in ((lat.rho, full.rho), (lat.ux, full.ux), (lat.uz, full.uz)):
+            assert np.array_equal(a.reshape(rows, s.nx)[:, s.interior], b.reshape(rows, nx)[:, s.x0:s.x1])
+    assert np.all(np.isfinite(full.h)) and np.abs(full.ux).max() > 1e-4
+
+
 # ---------------------------------------------------------------- the transport
 
 def _free_port():
