@@ -1,22 +1,23 @@
-"""One D2Q9 lattice split into x-slabs with a face exchange after every
-update: the domain decomposition behind the multi-GPU extension the paper
-names as future work (Sec. 6).
+"""One lattice (D2Q9, or a D3Q19 box) split into x-slabs with a face
+exchange after every update: the domain decomposition behind the multi-GPU
+extension the paper names as future work (Sec. 6).
 
-Each slab owns a run of whole columns and adds one ghost column on every face
-it shares with another slab. The pull update (Eq. 1) of a slab's boundary
-column reads, from the ghost column beside it, only the three populations
-that cross that face; after every update the owner of the neighbouring column
-sends exactly those (``lbm_face_pack``) and the slab writes them into its
-ghost column (``lbm_face_unpack``). Solid padding columns beyond a ghost
-column can round a slab's row length up to a multiple of 32 nodes, so that
-its rows keep the memory-line alignment of the undivided lattice's. With the
-ghost columns' solid mask taken from the neighbour, every interior node sees
-the same sources, the same link
-classification and the same edge treatment as in the undivided lattice, so
-the interiors evolve bit for bit like it (LPTL, NPTL, NPOL, NSOL; every
-layout and storage; stochastic rounding keys its draws on each slab's own
-node index, so it gives other, equally distributed, draws). The ghost
-columns' own updates are never read and are overwritten by the next exchange.
+Each slab owns a run of whole columns (planes in 3-D) and adds one ghost
+column on every face it shares with another slab. The pull update (Eq. 1) of
+a slab's boundary column reads, from the ghost column beside it, only the
+populations that cross that face (three per node in D2Q9, five in D3Q19);
+after every update the owner of the neighbouring column sends exactly those
+(``lbm_face_pack``) and the slab writes them into its ghost column
+(``lbm_face_unpack``). Solid padding columns beyond a ghost column can round
+a slab's row length up to a multiple of 32 nodes, so that its rows keep the
+memory-line alignment of the undivided lattice's. With the ghost columns'
+solid mask taken from the neighbour, every interior node sees the same
+sources, the same link classification and the same edge treatment as in the
+undivided lattice, so the interiors evolve bit for bit like it (LPTL, NPTL,
+NPOL, NSOL; every layout and storage; stochastic rounding keys its draws on
+each slab's own node index, so it gives other, equally distributed, draws).
+The ghost columns' own updates are never read and are overwritten by the
+next exchange.
 
 Two transports carry a face's message:
  * slabs held by the same process exchange on the device, every message of
@@ -39,7 +40,7 @@ import numpy as np
 from . import lbm
 
 ELEM_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
-EAST_GOING, WEST_GOING = 1, -1   # sense: c_ix of the three exchanged directions
+EAST_GOING, WEST_GOING = 1, -1   # sense: c_ix of the exchanged directions
 
 
 @dataclass(frozen=True)
