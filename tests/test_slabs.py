@@ -71,6 +71,28 @@ def test_layout_offsets_are_affine_in_the_node_index():
                     [base + n * stride for n in range(N)], (name, i)
 
 
+def test_decomposition_rejects_what_it_cannot_split_before_any_device_work():
+    pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        S.Decomposition(32, 8, 0.8, None, parts=2, algo="aa")            # two forms of the state
+    with pytest.raises(ValueError):
+        S.Decomposition(32, 8, 0.8, None, parts=17)                      # slabs narrower than 2 columns
+    with pytest.raises(ValueError):
+        S.Decomposition(12, 8, 0.8, None, nz=4, parts=7, bc=(O.PERIODIC,) * 3)
+
+
+def test_ghost_faces_of_3d_slabs():
+    """A slab without ghosts keeps the box's x faces; ghost faces of periodic
+    or walled boxes become walls; inlet / outlet boxes keep their kinds."""
+    one = S.split(12, 1, True)[0]
+    assert S.edges3(one, (O.PERIODIC, O.WALL, O.PERIODIC), O.OUTFLOW_ZG)[:3] == (O.PERIODIC, O.WALL, O.PERIODIC)
+    for sl in S.split(12, 3, True, 4):
+        assert S.edges3(sl, (O.PERIODIC, O.PERIODIC, O.WALL), O.OUTFLOW_ZG)[:3] == (O.WALL, O.PERIODIC, O.WALL)
+    for sl in S.split(12, 3, False):
+        assert S.edges3(sl, (O.INLET_ZOUHE, O.WALL, O.WALL), O.OUTLET_PRESSURE) == \
+            (O.INLET_ZOUHE, O.WALL, O.WALL, O.OUTLET_PRESSURE)
+
+
 # ---------------------------------------------------------------- the plan on the oracle
 
 P, W = O.PERIODIC, O.WALL
