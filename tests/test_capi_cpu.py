@@ -316,3 +316,18 @@ def test_c_mask_generator_rejects_bad_arguments(lib):
         with pytest.raises(lbm.LbmError) as e:
             call()
         assert e.value.status == lbm.LBM_EINVAL
+
+
+def test_face_exchange_argument_errors_need_no_gpu(lib):
+    """The face calls check their arguments before any device work (include/lbm.h)."""
+    import ctypes
+    for fn in (lib.lbm_face_pack, lib.lbm_face_unpack, lib.lbm3_face_pack, lib.lbm3_face_unpack):
+        assert fn(None, 0, 1, None) == lbm.LBM_EINVAL
+    one = (ctypes.c_int32 * 1)(0)
+    for fn in (lib.lbm_face_exchange, lib.lbm3_face_exchange):
+        assert fn(0, None, None, None, None, None, None) == lbm.LBM_OK        # nothing to exchange
+        assert fn(-1, None, None, None, None, None, None) == lbm.LBM_EINVAL
+        assert fn(65, None, None, None, None, None, None) == lbm.LBM_EINVAL  # more than 64 messages
+        assert fn(1, None, one, None, one, one, None) == lbm.LBM_EINVAL      # NULL lattice arrays
+        hs = (ctypes.c_void_p * 1)(None)
+        assert fn(1, hs, one, hs, one, one, None) == lbm.LBM_EINVAL          # NULL lattices
